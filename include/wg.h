@@ -1,0 +1,210 @@
+/* wg.h -- C-ABI of libwg: semi-naive Datalog fixpoints (transitive closure,
+ * same-generation) on one GB300 GPU.
+ *
+ * Problem statement (paper, Sec. Background): a relation is a SET of tuples;
+ * recursive rules are applied until no new tuple is derived.  The library
+ * evaluates, over uint32 vertex ids,
+ *   TC:  T(x,y) <- E(x,y).   T(x,z) <- T(x,y), E(y,z).            (Sec. Background)
+ *   SG:  sg(x,y) <- E(p,x), E(p,y), x != y.                         (base rule)
+ *        sg(x,y) <- E(a,x), sg(a,b), E(b,y).                        (Sec. Generalization;
+ *        the paper's parent(X,P) is read as the edge P -> X)
+ * by semi-naive evaluation (Sec. Background, "Semi-Naive Evaluation", steps
+ * 1-5): each iteration joins the newest delta with E, sorts the candidates,
+ * removes duplicates and tuples already known, and merges the survivors into
+ * the full relation (Secs. Sorted-Array Pipeline and Asynchronous Fixpoint
+ * Engine).  The loop runs on the device; the host sees only the end result.
+ *
+ * Conventions for every entry point
+ *  - Return value: WG_OK (0) or a negative WG_E_* code.  Nothing aborts, traps
+ *    or exits.  wg_last_error() gives a message for the calling thread.
+ *  - "host" pointers are ordinary CPU memory (pageable or pinned); "device"
+ *    pointers are CUDA global memory of the context's device.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *    The library owns relations and query results until the matching *_free.
+ *  - Tuples are returned as packed keys (uint64_t(src) << 32) | dst in
+ *    ascending order, i.e. the lexicographic (src, dst) order the paper keeps
+ *    every relation in (Sec. Binary-Search Join).  Ids span all of uint32.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *  - Every call is stream-ordered on the context's stream.
+ */
+#ifndef WG_H
+#define WG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WG_OK 0
+#define WG_E_INVAL (-1)          /* bad argument, handle or state */
+#define WG_E_NOMEM (-2)          /* a device allocation failed */
+#define WG_E_BUDGET (-3)         /* the request does not fit the context's memory budget */
+#define WG_E_CAPACITY (-4)       /* caller buffer too small; the needed size is returned */
+#define WG_E_NOT_READY (-5)      /* the query has not finished (wg_wait timed out) */
+#define WG_E_ITER_CAP (-6)       /* max_iters iterations ran without reaching the fixpoint */
+#define WG_E_DEVICE_TIMEOUT (-7) /* a bounded device-side wait gave up; the result is void */
+#define WG_E_CUDA (-8)           /* a CUDA runtime call failed */
+
+typedef struct wg_ctx wg_ctx;
+typedef uint64_t wg_rel;   /* relation handle, 0 = none */
+typedef uint64_t wg_query; /* query handle, 0 = none */
+
+/* Device memory provider.  alloc returns a device pointer of at least `bytes`
+ * bytes (256-byte aligned) usable in stream order on `stream`, or NULL.  free
+ * releases it.  Both may be NULL in wg_init: the library then calls
+ * cudaMallocAsync / cudaFreeAsync on the context stream. */
+typedef void* (*wg_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*wg_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+enum wg_kind { WG_TC = 0, WG_SG = 1 };
+
+enum wg_loop {
+  WG_LOOP_DEVICE = 0, /* one CUDA graph per run: a conditional WHILE node holds the
+                         iteration; no host synchronisation between iterations */
+  WG_LOOP_HOST = 1    /* the host launches each iteration and reads the delta size
+                         back once per iteration (the host-driven loop of Sec.
+                         Motivation, "Stage-Wise Synchronization"), for comparison */
+};
+
+typedef struct wg_opts {
+  uint32_t max_iters;    /* iteration cap; 0 = 1<<20 */
+  uint32_t loop;         /* enum wg_loop */
+  uint32_t profile;      /* 1 = time every kernel with CUDA events (forces WG_LOOP_HOST) */
+  uint32_t reserved0;
+  uint64_t reserve_full; /* initial capacity of the full relation, tuples; 0 = auto */
+  uint64_t reserve_cand; /* initial capacity of the candidate buffers, tuples; 0 = auto */
+} wg_opts;
+
+enum wg_state { WG_PENDING = 0, WG_RUNNING = 1, WG_DONE = 2, WG_FAILED = 3 };
+
+typedef struct wg_status {
+  int32_t state;       /* enum wg_state */
+  int32_t error;       /* WG_OK or the WG_E_* code of a failed query */
+  uint64_t n_tuples;   /* size of the result relation once DONE */
+  uint32_t iterations; /* index of the first empty delta (the chain a->b->c->d gives 3) */
+  uint32_t regrows;    /* how often buffers were grown and the loop resumed */
+  uint64_t candidates; /* sum over iterations of the join output size |C| */
+  uint64_t gpu_launches; /* kernels this query launched */
+  double device_ms;    /* device time from the first launch to completion (CUDA events) */
+} wg_status;
+
+typedef struct wg_request {
+  int32_t kind;        /* enum wg_kind */
+  uint32_t reserved0;
+  wg_rel edges;
+  wg_opts opts;        /* loop and profile are ignored in batches */
+} wg_request;
+
+/* Per-kernel timing of a profiled query (opts.profile = 1).  `bytes` is the
+ * ALGORITHMIC traffic of all its launches: the bytes the method must move,
+ * counted from the relation sizes, not from hardware counters. */
+typedef struct wg_kernel_stat {
+  char name[32];
+  uint64_t launches;
+  double total_ms;
+  double bytes;
+} wg_kernel_stat;
+
+/* ---- context -------------------------------------------------------------
+ * wg_init: binds `device`, creates or adopts `cuda_stream` (a cudaStream_t;
+ * NULL = a new non-blocking stream owned by the context).  mem_budget_bytes
+ * caps the device memory the context holds at any time (0 = 90% of the free
+ * memory).  Errors: WG_E_INVAL (bad device), WG_E_CUDA. */
+int wg_init(int device, size_t mem_budget_bytes, wg_alloc_fn alloc, wg_free_fn free_fn,
+            void* user, void* cuda_stream, wg_ctx** out);
+/* Waits for the stream, releases every relation, query and buffer. */
+void wg_destroy(wg_ctx* ctx);
+/* Message of the last failing call on this thread ("" if none). */
+const char* wg_last_error(void);
+/* Device bytes currently held by the context. */
+size_t wg_mem_used(const wg_ctx* ctx);
+
+/* ---- relations -----------------------------------------------------------
+ * wg_relation_load: the edge set {(src[i], dst[i]) : i < n} from HOST arrays
+ * (copied; duplicates removed, self-loops kept).  The relation is sorted once
+ * here and never modified (Sec. Binary-Search Join: E is sorted at dataset
+ * load); a CSR index on the source is built for the join.  Vertex ids are
+ * relabelled internally to their rank among the distinct ids, which keeps
+ * the lexicographic order and picks the narrowest key width (the adaptive
+ * radix width of Sec. Buffer Routing and Adaptive Radix Sort).  n = 0 is a
+ * valid empty relation.  Errors: WG_E_INVAL (NULL arrays with n > 0, n >= 2^32),
+ * WG_E_NOMEM / WG_E_BUDGET. */
+int wg_relation_load(wg_ctx* ctx, const uint32_t* src, const uint32_t* dst, size_t n,
+                     wg_rel* out);
+/* Same, from DEVICE arrays (read in stream order, not retained). */
+int wg_relation_load_device(wg_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, size_t n,
+                            wg_rel* out);
+/* Distinct edges, distinct vertices, and bits per vertex field of a relation. */
+int wg_relation_info(wg_ctx* ctx, wg_rel rel, uint64_t* n_edges, uint32_t* n_vertices,
+                     uint32_t* field_bits);
+void wg_relation_free(wg_ctx* ctx, wg_rel rel);
+
+/* ---- single queries ------------------------------------------------------
+ * wg_tc / wg_sg: enqueue one fixpoint on the context stream and return at once.
+ * opts may be NULL (defaults).  The result is ready when wg_poll reports
+ * WG_DONE or wg_wait returns WG_OK; buffers that turn out too small are grown
+ * and the loop resumed inside wg_poll / wg_wait.  Errors: WG_E_INVAL (bad
+ * handle), WG_E_NOMEM / WG_E_BUDGET. */
+int wg_tc(wg_ctx* ctx, wg_rel edges, const wg_opts* opts, wg_query* out);
+int wg_sg(wg_ctx* ctx, wg_rel edges, const wg_opts* opts, wg_query* out);
+
+/* ---- batches and serving -------------------------------------------------
+ * wg_submit: admit n independent fixpoints (TC or SG, any mix) that run
+ * TOGETHER: every stage of every iteration is one launch over the tiles of
+ * all running queries, and the iteration loop is one CUDA graph.  Queries
+ * submitted while earlier ones run join the running set at the next
+ * iteration boundary that wg_poll / wg_wait / wg_serve_step reaches
+ * (continuous batching).  ids[i] receives the handle of reqs[i].  Admission
+ * is by device-memory budget: a request that cannot be admitted now stays
+ * queued (state WG_PENDING).  Errors: WG_E_INVAL. */
+int wg_submit(wg_ctx* ctx, const wg_request* reqs, size_t n, wg_query* ids);
+/* Advance the batch engine by at most `iters` iterations (admitting queued
+ * requests and retiring finished ones) and return without waiting for the
+ * device beyond that.  *n_running receives the number of queries in flight. */
+int wg_serve_step(wg_ctx* ctx, uint32_t iters, size_t* n_running);
+
+/* ---- completion and results ---------------------------------------------- */
+/* Non-blocking: fills *st. */
+int wg_poll(wg_ctx* ctx, wg_query q, wg_status* st);
+/* Blocks until the query is DONE/FAILED or timeout_us elapses (0 = no limit).
+ * Returns WG_OK, WG_E_NOT_READY on timeout, or the query's own error. */
+int wg_wait(wg_ctx* ctx, wg_query q, uint64_t timeout_us);
+/* Copy the result (sorted packed keys) into a HOST buffer of cap entries.
+ * *n_out = result size; WG_E_CAPACITY (nothing copied) when cap < size. */
+int wg_result_copy(wg_ctx* ctx, wg_query q, uint64_t* keys, size_t cap, size_t* n_out);
+/* Same into a DEVICE buffer (stream-ordered; synchronises the stream). */
+int wg_result_copy_device(wg_ctx* ctx, wg_query q, uint64_t* d_keys, size_t cap, size_t* n_out);
+/* Per-iteration delta sizes |Delta^0|, ..., |Delta^iterations| (last entry 0
+ * at the fixpoint) into a HOST buffer; WG_E_CAPACITY when cap is too small. */
+int wg_result_iters(wg_ctx* ctx, wg_query q, uint64_t* delta_sizes, size_t cap, size_t* n_out);
+/* Per-kernel statistics of a profiled query; WG_E_CAPACITY when cap is too small. */
+int wg_result_profile(wg_ctx* ctx, wg_query q, wg_kernel_stat* stats, size_t cap,
+                      size_t* n_out);
+void wg_query_free(wg_ctx* ctx, wg_query q);
+
+/* ---- sorted-array primitives (the stages of one iteration) ---------------
+ * Device buffers of packed keys, key_bytes = 4 (uint32) or 8 (uint64).  They
+ * run on the context stream, use context scratch, and synchronise the stream
+ * before returning sizes.
+ *
+ * wg_sort_keys: stable LSD radix sort of n keys on their low `bits` bits
+ * (1..64; higher bits must be zero), in place (Sec. Buffer Routing and
+ * Adaptive Radix Sort: histogram, prefix sum, scatter per digit). */
+int wg_sort_keys(wg_ctx* ctx, void* d_keys, size_t n, int key_bytes, uint32_t bits);
+/* wg_unique_diff: out = { c in sorted `cand` : c differs from its predecessor
+ * and c is not in sorted `full` } in input order (Sec. Fused Deduplication and
+ * Set Difference).  n_full = 0 gives plain deduplication.  `out` holds n
+ * entries; *n_out = survivors. */
+int wg_unique_diff(wg_ctx* ctx, const void* d_cand, size_t n, const void* d_full, size_t n_full,
+                   void* d_out, size_t* n_out, int key_bytes);
+/* wg_merge_disjoint: out = merge of sorted a and sorted b, which share no key
+ * (Sec. Disjoint Merge); out holds na + nb entries. */
+int wg_merge_disjoint(wg_ctx* ctx, const void* d_a, size_t na, const void* d_b, size_t nb,
+                      void* d_out, int key_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WG_H */
