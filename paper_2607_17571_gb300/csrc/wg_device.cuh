@@ -1,0 +1,264 @@
+// wg_device.cuh -- device-resident descriptors and block primitives shared by
+// the sm_103a kernels of the semi-naive fixpoint.
+//
+// Every kernel of the loop is "indirect": its grid is fixed (a persistent grid
+// sized to the SM count) and it reads how much work there is, and where, from
+// device memory written by the previous stage.  This is the CUDA counterpart of
+// the paper's indirect dispatch (Sec. Batched Indirect-Dispatch Loop): stage
+// sizes never travel to the host, so one iteration -- and the whole loop -- can
+// be captured once in a CUDA graph.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wg {
+
+constexpr int kThreads = 256;                 // every stage kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kItemsC = 16;                   // keys per thread, candidate stages
+constexpr int kTileC = kThreads * kItemsC;    // 4096 keys per candidate tile
+constexpr int kItemsD = 8;                    // delta tuples per thread, join count
+constexpr int kTileD = kThreads * kItemsD;    // 2048 delta tuples per tile
+constexpr int kTileM = 4096;                  // merge output tile
+constexpr int kRadix = 256;                   // digit buckets (digits of <= 8 bits)
+constexpr int kMaxPasses = 8;
+constexpr int kEmitWin = 2048;                // delta tuples staged in smem by emit
+constexpr int kFWin = 2048;                   // full-relation keys staged by dedup/diff
+constexpr uint32_t kSpinLimit = 1u << 22;     // polls before a lookback gives up
+
+// device error codes (mirrored to WG_E_* on the host)
+enum : uint32_t { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+// instance states
+enum : uint32_t { INST_FREE = 0, INST_ACTIVE = 1, INST_DONE = 2, INST_ITERCAP = 3 };
+enum : uint32_t { KIND_TC = 0, KIND_SG = 1 };
+
+// Control block of one engine.
+struct Ctl {
+  uint32_t abort;      // nonzero: every later kernel of this run returns at once
+  uint32_t error;      // DEV_* set by a wait that gave up
+  uint32_t epoch;      // lookback epoch, bumped once per lookback launch
+  uint32_t cont;       // loop continues (mirrors the graph conditional)
+  uint32_t launch_iters;  // iterations run in the current graph launch
+  uint32_t iter_budget;   // per-launch iteration budget
+  uint32_t n_active;
+  uint32_t pad;
+  unsigned long long need_cand;  // tuples needed in the candidate pools after an overflow
+  unsigned long long need_full;
+  unsigned long long need_res;
+};
+
+// One segment (one instance's part) of a segmented stage.
+struct Seg {
+  unsigned long long in_off, n;        // input range in the input pool
+  unsigned long long out_off;          // output offset in the output pool
+  unsigned long long aux_off, aux_n;   // auxiliary sorted range (full relation / delta)
+  unsigned long long res;              // produced count (written by the stage)
+  uint32_t tile0, ntiles;              // global tiles [tile0, tile0 + ntiles)
+  uint32_t inst, flags;                // owning instance; flags & 1: output to out2
+};
+
+// One launch's work: indirect grid, pools, lookback scratch.
+struct Stage {
+  const void* in;
+  void* out;
+  const void* aux;
+  void* out2;
+  Seg* segs;
+  struct Inst* inst;
+  Ctl* ctl;
+  unsigned long long* status;   // lookback words
+  unsigned long long* hist;     // radix digit counts [nseg][passes][kRadix]
+  unsigned long long* pos;      // join prefix sums (one per delta tuple)
+  uint32_t nseg, ntiles;
+  uint32_t ctr;                 // dynamic tile counter (zeroed by the writer)
+  uint32_t epoch;
+  uint32_t shift, dbits, pass, passes;
+};
+
+// One fixpoint instance (a query in flight).
+struct Inst {
+  const uint32_t* off;    // CSR offsets over source ranks [nv + 1]
+  const uint32_t* adj;    // destination ranks, sorted within each source [ne]
+  uint32_t nv, w;         // distinct vertices, bits per field
+  uint32_t kind, state;
+  uint32_t iter;          // index of the pass about to run (0 = base rule)
+  uint32_t max_iters;
+  unsigned long long n_delta, n_full, n_cand, n_new;
+  unsigned long long d_off, f_off, c_off;
+  unsigned long long res_off;  // final relation: pool res_pool at res_off
+  uint32_t res_pool, iters_done;
+  unsigned long long cand_total;
+  unsigned long long* log;     // |Delta^0|, |Delta^1|, ...
+  uint32_t log_cap, pad;
+};
+
+// Stage slots of an engine (one Stage record per kernel of the iteration).
+enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_HSCAN, S_UNIQ, S_MERGE, S_PASS0,
+                     S_NUM = S_PASS0 + kMaxPasses };
+
+// Device-resident state of one engine: pools, the instance table, the stage
+// records the plan kernels write, and the graph conditional handle.  Pools are
+// reached through this block only, so growing a pool never re-captures the graph.
+struct Dev {
+  Ctl ctl;
+  Stage st[S_NUM];
+  Inst* inst;
+  Seg* segD;  // join count: delta per instance
+  Seg* segE;  // join emit
+  Seg* segS;  // radix sort
+  Seg* segU;  // dedup + diff
+  Seg* segM;  // merge
+  void* D[2];  // delta / new-delta pools (swap every iteration)
+  void* C[2];  // candidate pools (radix ping-pong)
+  void* F[2];  // full relation pools (swap every iteration)
+  void* R;     // retired results (batch engines)
+  unsigned long long capC, capF, capR;
+  unsigned long long* pos;            // join prefix sums, capC entries
+  unsigned long long* status_scalar;  // lookback words of scalar scans
+  unsigned long long* status_sort;    // lookback words of radix passes
+  unsigned long long* hist;           // [n_inst][passes][kRadix]
+  unsigned long long r_used;
+  unsigned long long cond;            // cudaGraphConditionalHandle
+  uint32_t n_inst, single, use_cond;
+  uint32_t dphase, fphase;
+  uint32_t bits, passes, dbits;
+};
+
+// ---------------------------------------------------------------- status words
+// [63:40] epoch (24 bits) | [39:38] flag | [37:0] value
+constexpr unsigned long long kValMask = (1ull << 38) - 1;
+constexpr uint32_t FLAG_AGG = 1, FLAG_INC = 2;
+
+__device__ __forceinline__ unsigned long long st_pack(uint32_t epoch, uint32_t flag,
+                                                      unsigned long long v) {
+  return ((unsigned long long)(epoch & 0xFFFFFFu) << 40) | ((unsigned long long)flag << 38) |
+         (v & kValMask);
+}
+__device__ __forceinline__ void st_put(unsigned long long* p, unsigned long long v) {
+  *(volatile unsigned long long*)p = v;
+}
+__device__ __forceinline__ unsigned long long st_get(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+__device__ __forceinline__ bool st_ready(unsigned long long s, uint32_t epoch) {
+  return (uint32_t)(s >> 40) == (epoch & 0xFFFFFFu) && ((s >> 38) & 3u) != 0;
+}
+
+__device__ __forceinline__ void fail_timeout(Ctl* ctl) {
+  atomicExch(&ctl->error, DEV_TIMEOUT);
+  atomicExch(&ctl->abort, 1u);
+}
+
+// Warp-cooperative decoupled lookback (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016): exclusive prefix of
+// tile t over tiles [t0, t).  Every lane of the calling warp participates.
+// Each poll is bounded; on timeout the control block records DEV_TIMEOUT and
+// the returned value is meaningless (the run is void).
+__device__ __forceinline__ unsigned long long lookback_scalar(const unsigned long long* status,
+                                                              uint32_t t, uint32_t t0,
+                                                              uint32_t epoch, Ctl* ctl) {
+  const uint32_t lane = threadIdx.x & 31;
+  unsigned long long excl = 0;
+  long long base = (long long)t - 1;
+  while (base >= (long long)t0) {
+    long long idx = base - lane;
+    unsigned long long s;
+    uint32_t flag, timed_out = 0;
+    if (idx >= (long long)t0) {
+      uint32_t spins = 0;
+      s = st_get(status + idx);
+      while (!st_ready(s, epoch)) {
+        if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) { timed_out = 1; break; }
+        __nanosleep(64);
+        s = st_get(status + idx);
+      }
+      flag = (uint32_t)(s >> 38) & 3u;
+    } else {
+      s = 0;
+      flag = FLAG_INC;  // before the segment: an inclusive zero
+    }
+    if (__any_sync(0xffffffffu, timed_out)) {
+      if (lane == 0 && !*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
+      return 0;
+    }
+    unsigned long long v = s & kValMask;
+    uint32_t inc = __ballot_sync(0xffffffffu, flag == FLAG_INC);
+    uint32_t upto = inc ? (uint32_t)(__ffs(inc) - 1) : 31u;
+    unsigned long long mine = lane <= upto ? v : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    excl += mine;
+    if (inc) break;
+    base -= 32;
+  }
+  return excl;
+}
+
+// Block-wide exclusive scan of one 64-bit value per thread; *total = block sum.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
+                                                              unsigned long long* sh /*kWarps*/,
+                                                              unsigned long long* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < (uint32_t)kWarps ? sh[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    if (lane < (uint32_t)kWarps) sh[lane] = w;  // inclusive warp prefix
+  }
+  __syncthreads();
+  unsigned long long wp = warp ? sh[warp - 1] : 0ull;
+  *total = sh[kWarps - 1];
+  __syncthreads();
+  return wp + x - v;
+}
+
+// Global tile -> segment: the segment k with tile0 <= t < tile0 + ntiles.
+__device__ __forceinline__ uint32_t find_seg(const Seg* segs, uint32_t nseg, uint32_t t) {
+  uint32_t lo = 0, hi = nseg;  // largest k with tile0 <= t
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (segs[mid].tile0 <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Dynamic tile claim: thread 0 takes the next tile; returns it to every thread.
+__device__ __forceinline__ uint32_t claim_tile(Stage* stp, uint32_t* sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) *sh = atomicAdd(&stp->ctr, 1u);
+  __syncthreads();
+  return *sh;
+}
+
+template <typename K>
+__device__ __forceinline__ unsigned long long lower_bound_k(const K* a, unsigned long long n, K x) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    unsigned long long mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+template <typename K>
+__device__ __forceinline__ unsigned long long upper_bound_k(const K* a, unsigned long long n, K x) {
+  unsigned long long lo = 0, hi = n;
+  while (lo < hi) {
+    unsigned long long mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace wg

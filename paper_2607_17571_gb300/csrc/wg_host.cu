@@ -1,0 +1,1325 @@
+// wg_host.cu -- host runtime of libwg: context, device memory, relation load,
+// the fixpoint engine (a CUDA graph whose conditional WHILE node holds the
+// semi-naive loop), batching / continuous serving, and the C-ABI of wg.h.
+//
+// Engine rule (Sec. Asynchronous Fixpoint Engine): the GPU decides every
+// stage, iteration and buffer transition; the host only learns that the
+// fixpoint was reached.  Here the device also decides termination (the WHILE
+// condition is set by the plan kernel that sees the empty delta), so a query
+// costs one graph launch unless a buffer turns out too small: then the run
+// stops before writing past it, the host grows the pools (live data copied),
+// and the same graph is launched again from the unchanged (Full, Delta, i).
+#include <algorithm>
+#include <chrono>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/wg.h"
+#include "wg_device.cuh"
+#include "wg_launch.h"
+
+using namespace wg;
+
+namespace {
+thread_local std::string g_err;
+
+int set_err(int code, const std::string& m) {
+  g_err = m;
+  return code;
+}
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return set_err(WG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+#define TRY(call)               \
+  do {                          \
+    int r_ = (call);            \
+    if (r_ != WG_OK) return r_; \
+  } while (0)
+
+uint32_t bits_for(uint64_t nv) {  // bits to hold ranks 0..nv-1 (at least 1)
+  uint32_t w = 1;
+  while (w < 32 && (1ull << w) < nv) ++w;
+  return w;
+}
+size_t round_up(size_t b) { return (b + 255) & ~size_t(255); }
+double now_us() {
+  return std::chrono::duration<double, std::micro>(
+             std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+struct Relation;
+struct Query;
+struct EngineBase;
+
+// ------------------------------------------------------------------ context
+struct wg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  wg_alloc_fn alloc = nullptr;
+  wg_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  size_t budget = 0, used = 0;
+  int num_sms = 0;
+  uint64_t next_id = 1;
+  std::map<uint64_t, std::unique_ptr<Relation>> rels;
+  std::map<uint64_t, std::unique_ptr<Query>> queries;
+  std::vector<std::unique_ptr<EngineBase>> idle;  // single-query engines ready for reuse
+  std::map<int, std::unique_ptr<EngineBase>> batch;  // batch engines by key class
+  std::vector<uint64_t> pending;                  // submitted, not yet admitted
+  // scratch of the standalone primitives
+  void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
+  unsigned long long* s_status = nullptr; size_t s_status_n = 0;
+  unsigned long long* s_hist = nullptr;
+  Stage* s_stage = nullptr;
+  Seg* s_seg = nullptr;
+  Ctl* s_ctl = nullptr;
+  uint32_t s_epoch = 0;
+};
+
+static int dev_alloc(wg_ctx* c, size_t bytes, void** out) {
+  *out = nullptr;
+  if (bytes == 0) return WG_OK;
+  bytes = round_up(bytes);
+  if (c->used + bytes > c->budget)
+    return set_err(WG_E_BUDGET, "allocation of " + std::to_string(bytes) +
+                                    " bytes exceeds the memory budget");
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, (void*)c->stream, c->user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (!p) return set_err(WG_E_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  c->used += bytes;
+  *out = p;
+  return WG_OK;
+}
+static void dev_free(wg_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  bytes = round_up(bytes);
+  if (c->free_fn) c->free_fn(p, bytes, (void*)c->stream, c->user);
+  else cudaFreeAsync(p, c->stream);
+  c->used -= bytes;
+}
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int get(wg_ctx* c, size_t b) {
+    if (b <= bytes && p) return WG_OK;
+    release(c);
+    TRY(dev_alloc(c, b, &p));
+    bytes = round_up(b);
+    return WG_OK;
+  }
+  void release(wg_ctx* c) {
+    dev_free(c, p, bytes);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+static int grid_of(wg_ctx* c, int occ) { return c->num_sms * std::max(1, occ); }
+
+// ------------------------------------------------------------------ primitives
+// Standalone segmented stages on one segment (relation load, wg_sort_keys,
+// wg_unique_diff, wg_merge_disjoint).  Same kernels as the fixpoint loop.
+static int prim_scratch(wg_ctx* c, size_t tmp_bytes, size_t ntiles) {
+  if (!c->s_stage) {
+    void* p;
+    TRY(dev_alloc(c, sizeof(Stage) * S_NUM, &p)); c->s_stage = (Stage*)p;
+    TRY(dev_alloc(c, sizeof(Seg), &p)); c->s_seg = (Seg*)p;
+    TRY(dev_alloc(c, sizeof(Ctl), &p)); c->s_ctl = (Ctl*)p;
+    TRY(dev_alloc(c, sizeof(unsigned long long) * kMaxPasses * kRadix, &p));
+    c->s_hist = (unsigned long long*)p;
+    CK(cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream));
+  }
+  if (tmp_bytes > c->s_tmp_bytes) {
+    dev_free(c, c->s_tmp, c->s_tmp_bytes);
+    c->s_tmp = nullptr; c->s_tmp_bytes = 0;
+    TRY(dev_alloc(c, tmp_bytes, &c->s_tmp));
+    c->s_tmp_bytes = round_up(tmp_bytes);
+  }
+  const size_t need = (ntiles + 1) * kRadix;
+  if (need > c->s_status_n) {
+    dev_free(c, c->s_status, c->s_status_n * 8);
+    c->s_status = nullptr; c->s_status_n = 0;
+    void* p;
+    TRY(dev_alloc(c, need * 8, &p));
+    c->s_status = (unsigned long long*)p;
+    c->s_status_n = need;
+    CK(cudaMemsetAsync(c->s_status, 0, need * 8, c->stream));
+    c->s_epoch = 0;
+  }
+  return WG_OK;
+}
+static uint32_t prim_epoch(wg_ctx* c) {
+  if (++c->s_epoch >= (1u << 23)) {  // epochs wrap at 24 bits: clear the words first
+    cudaMemsetAsync(c->s_status, 0, c->s_status_n * 8, c->stream);
+    c->s_epoch = 1;
+  }
+  return c->s_epoch;
+}
+static Stage prim_stage(wg_ctx* c, uint32_t ntiles) {
+  Stage s{};
+  s.segs = c->s_seg; s.ctl = c->s_ctl; s.status = c->s_status; s.hist = c->s_hist;
+  s.nseg = 1; s.ntiles = ntiles;
+  return s;
+}
+static int prim_put(wg_ctx* c, int slot, const Stage& s) {
+  CK(cudaMemcpyAsync(c->s_stage + slot, &s, sizeof(Stage), cudaMemcpyHostToDevice, c->stream));
+  return WG_OK;
+}
+static int prim_seg(wg_ctx* c, const Seg& s) {
+  CK(cudaMemcpyAsync(c->s_seg, &s, sizeof(Seg), cudaMemcpyHostToDevice, c->stream));
+  return WG_OK;
+}
+
+static void pass_plan(uint32_t bits, uint32_t* passes, uint32_t* dbits) {
+  bits = std::max(1u, bits);
+  *passes = (bits + 7) / 8;
+  *dbits = (bits + *passes - 1) / *passes;
+}
+
+template <typename K>
+static int prim_sort(wg_ctx* c, K* keys, size_t n, uint32_t bits) {
+  if (n <= 1) return WG_OK;
+  const uint32_t ntiles = (uint32_t)((n + kTileC - 1) / kTileC);
+  TRY(prim_scratch(c, n * sizeof(K), ntiles));
+  uint32_t passes, dbits;
+  pass_plan(bits, &passes, &dbits);
+  Seg sg{};
+  sg.n = n; sg.tile0 = 0; sg.ntiles = ntiles;
+  TRY(prim_seg(c, sg));
+  CK(cudaMemsetAsync(c->s_hist, 0, sizeof(unsigned long long) * passes * kRadix, c->stream));
+  Stage h = prim_stage(c, ntiles);
+  h.in = keys; h.passes = passes; h.dbits = dbits;
+  TRY(prim_put(c, S_HIST, h));
+  TRY(prim_put(c, S_HSCAN, h));
+  K* buf[2] = {keys, (K*)c->s_tmp};
+  for (uint32_t p = 0; p < passes; ++p) {
+    Stage s = h;
+    s.in = buf[p & 1]; s.out = buf[(p + 1) & 1];
+    s.shift = p * dbits; s.pass = p; s.epoch = prim_epoch(c);
+    TRY(prim_put(c, S_PASS0 + p, s));
+  }
+  launch_sort_hist<K>(c->s_stage + S_HIST, grid_of(c, occupancy_sort<K>(0)), c->stream);
+  launch_sort_hscan(c->s_stage + S_HSCAN, 64, c->stream);
+  for (uint32_t p = 0; p < passes; ++p)
+    launch_sort_pass<K>(c->s_stage + S_PASS0 + p, grid_of(c, occupancy_sort<K>(1)), c->stream);
+  CK(cudaGetLastError());
+  if (passes & 1) CK(cudaMemcpyAsync(keys, c->s_tmp, n * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+  return WG_OK;
+}
+
+template <typename K>
+static int prim_unique(wg_ctx* c, const K* in, size_t n, const K* full, size_t nf, K* out,
+                       size_t* n_out) {
+  *n_out = 0;
+  if (n == 0) return WG_OK;
+  const uint32_t ntiles = (uint32_t)((n + kTileC - 1) / kTileC);
+  TRY(prim_scratch(c, 0, ntiles));
+  Seg sg{};
+  sg.n = n; sg.aux_n = nf; sg.ntiles = ntiles;
+  TRY(prim_seg(c, sg));
+  Stage u = prim_stage(c, ntiles);
+  u.in = in; u.aux = full; u.out = out; u.epoch = prim_epoch(c);
+  TRY(prim_put(c, S_UNIQ, u));
+  launch_unique_diff<K>(c->s_stage + S_UNIQ, grid_of(c, occupancy_sort<K>(2)), c->stream);
+  CK(cudaGetLastError());
+  Seg back{};
+  Ctl ctl{};
+  CK(cudaMemcpyAsync(&back, c->s_seg, sizeof(Seg), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (ctl.error) {
+    cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream);
+    return set_err(WG_E_DEVICE_TIMEOUT, "a device lookback wait gave up");
+  }
+  *n_out = back.res;
+  return WG_OK;
+}
+
+template <typename K>
+static int prim_merge(wg_ctx* c, const K* a, size_t na, const K* b, size_t nb, K* out) {
+  if (na + nb == 0) return WG_OK;
+  const uint32_t ntiles = (uint32_t)((na + nb + kTileM - 1) / kTileM);
+  TRY(prim_scratch(c, 0, 0));
+  Seg sg{};
+  sg.n = na; sg.aux_n = nb; sg.ntiles = ntiles;
+  TRY(prim_seg(c, sg));
+  Stage m = prim_stage(c, ntiles);
+  m.in = a; m.aux = b; m.out = out;
+  TRY(prim_put(c, S_MERGE, m));
+  launch_merge<K>(c->s_stage + S_MERGE, grid_of(c, occupancy_sort<K>(3)), c->stream);
+  CK(cudaGetLastError());
+  return WG_OK;
+}
+
+// ------------------------------------------------------------------ relations
+struct Relation {
+  uint64_t ne = 0;
+  uint32_t nv = 0, w = 1;
+  int kb = 4;
+  DBuf keys, off, adj, V;
+  uint64_t peak_cand = 0, peak_full = 0;  // capacities seen by earlier queries
+  void release(wg_ctx* c) { keys.release(c); off.release(c); adj.release(c); V.release(c); }
+};
+
+template <typename K>
+static int build_edges(wg_ctx* c, Relation* R, const uint32_t* d_src, const uint32_t* d_dst,
+                       size_t n) {
+  DBuf kt, ke;
+  TRY(kt.get(c, n * sizeof(K)));
+  launch_rank_edges<K>(d_src, d_dst, n, (const uint32_t*)R->V.p, R->nv, R->w, (K*)kt.p,
+                       grid_of(c, 4), c->stream);
+  CK(cudaGetLastError());
+  TRY(prim_sort<K>(c, (K*)kt.p, n, 2 * R->w));
+  TRY(ke.get(c, n * sizeof(K)));
+  size_t ne = 0;
+  TRY(prim_unique<K>(c, (const K*)kt.p, n, (const K*)nullptr, 0, (K*)ke.p, &ne));
+  kt.release(c);
+  R->ne = ne;
+  R->keys = ke;
+  TRY(R->off.get(c, (size_t(R->nv) + 1) * 4));
+  TRY(R->adj.get(c, std::max<size_t>(ne, 1) * 4));
+  launch_csr<K>((const K*)ke.p, ne, R->nv, R->w, (uint32_t*)R->off.p, (uint32_t*)R->adj.p,
+                grid_of(c, 4), c->stream);
+  CK(cudaGetLastError());
+  return WG_OK;
+}
+
+static int load_relation(wg_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, size_t n,
+                         Relation* R) {
+  if (n >= (1ull << 32)) return set_err(WG_E_INVAL, "at most 2^32 - 1 edges");
+  if (n == 0) {
+    R->nv = 0; R->w = 1; R->kb = 4; R->ne = 0;
+    TRY(R->off.get(c, 4));
+    TRY(R->adj.get(c, 4));
+    TRY(R->V.get(c, 4));
+    CK(cudaMemsetAsync(R->off.p, 0, 4, c->stream));
+    return WG_OK;
+  }
+  // distinct vertex ids, sorted: ranks keep the order of ids
+  DBuf ids, vt;
+  TRY(ids.get(c, 2 * n * 4));
+  CK(cudaMemcpyAsync(ids.p, d_src, n * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync((uint32_t*)ids.p + n, d_dst, n * 4, cudaMemcpyDeviceToDevice, c->stream));
+  TRY(prim_sort<uint32_t>(c, (uint32_t*)ids.p, 2 * n, 32));
+  TRY(vt.get(c, 2 * n * 4));
+  size_t nv = 0;
+  TRY(prim_unique<uint32_t>(c, (const uint32_t*)ids.p, 2 * n, nullptr, 0, (uint32_t*)vt.p, &nv));
+  ids.release(c);
+  TRY(R->V.get(c, nv * 4));
+  CK(cudaMemcpyAsync(R->V.p, vt.p, nv * 4, cudaMemcpyDeviceToDevice, c->stream));
+  vt.release(c);
+  R->nv = (uint32_t)nv;
+  R->w = bits_for(nv);
+  R->kb = 2 * R->w <= 32 ? 4 : 8;
+  if (R->kb == 4) return build_edges<uint32_t>(c, R, d_src, d_dst, n);
+  return build_edges<unsigned long long>(c, R, d_src, d_dst, n);
+}
+
+// ------------------------------------------------------------------ engine
+struct KStat {
+  const char* name;
+  uint64_t launches = 0;
+  double ms = 0, bytes = 0;
+};
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+  virtual int kb() const = 0;
+  virtual uint32_t bits() const = 0;
+  virtual uint32_t slots() const = 0;
+  virtual void release() = 0;
+};
+
+struct Query {
+  uint64_t id = 0;
+  int kind = WG_TC;
+  Relation* rel = nullptr;
+  uint64_t rel_id = 0;
+  wg_opts opts{};
+  int state = WG_PENDING, error = WG_OK;
+  EngineBase* eng = nullptr;     // single engine owned while the query lives
+  std::unique_ptr<EngineBase> own;
+  bool batch = false;
+  int bclass = -1;
+  uint32_t slot = 0;
+  // results
+  uint64_t n_tuples = 0;
+  uint32_t iterations = 0, regrows = 0;
+  uint64_t candidates = 0, launches = 0;
+  double device_ms = 0;
+  double t_submit_us = 0, t_done_us = 0;
+  std::vector<unsigned long long> log;
+  std::vector<KStat> prof;
+  // where the result lives (rank-space keys of width kb)
+  const void* res_ptr = nullptr;
+  DBuf res_own;                  // batch results copied out of the retire pool
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+template <typename K>
+struct Engine : EngineBase {
+  wg_ctx* c;
+  bool single;
+  uint32_t n_slots, bits_, passes, dbits;
+  Dev* dv = nullptr;   // device block
+  Dev h{};             // host mirror (read back after each run)
+  std::vector<Inst> hi;
+  DBuf b_dev, b_inst, b_seg, b_log;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist;
+  unsigned long long capC = 0, capF = 0, capR = 0;
+  uint32_t log_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_uniq = 0, g_merge = 0;
+  bool in_flight = false;
+  cudaEvent_t ev_done = nullptr;
+  uint64_t launches_issued = 0;
+  uint32_t regrows = 0;
+  int kernels_per_iter() const { return 9 + (int)passes; }
+
+  Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap)
+      : c(ctx), single(single_), n_slots(n), bits_(bits), log_cap(logcap) {
+    pass_plan(bits, &passes, &dbits);
+  }
+  ~Engine() override { release(); }
+  int kb() const override { return (int)sizeof(K); }
+  uint32_t bits() const override { return bits_; }
+  uint32_t slots() const override { return n_slots; }
+
+  void release() override {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr; graph = nullptr;
+    if (ev_done) cudaEventDestroy(ev_done);
+    ev_done = nullptr;
+    DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
+                   &R, &pos, &st_s, &st_k, &hist};
+    for (DBuf* b : all) b->release(c);
+  }
+
+  int init() {
+    TRY(b_dev.get(c, sizeof(Dev)));
+    TRY(b_inst.get(c, sizeof(Inst) * n_slots));
+    TRY(b_seg.get(c, sizeof(Seg) * n_slots * 5));
+    TRY(b_log.get(c, sizeof(unsigned long long) * (size_t)n_slots * log_cap));
+    TRY(hist.get(c, sizeof(unsigned long long) * (size_t)n_slots * passes * kRadix));
+    dv = (Dev*)b_dev.p;
+    hi.assign(n_slots, Inst{});
+    CK(cudaMemsetAsync(b_inst.p, 0, sizeof(Inst) * n_slots, c->stream));
+    std::memset(&h, 0, sizeof(h));
+    h.inst = (Inst*)b_inst.p;
+    Seg* s = (Seg*)b_seg.p;
+    h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
+    h.segM = s + 4 * n_slots;
+    h.hist = (unsigned long long*)hist.p;
+    h.n_inst = n_slots; h.single = single ? 1 : 0;
+    h.bits = bits_; h.passes = passes; h.dbits = dbits;
+    h.ctl.iter_budget = 0xFFFFFFFFu;
+    CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
+    g_count = grid_of(c, occupancy_join<K>(0));
+    g_emit = grid_of(c, occupancy_join<K>(1));
+    g_hist = grid_of(c, occupancy_sort<K>(0));
+    g_pass = grid_of(c, occupancy_sort<K>(1));
+    g_uniq = grid_of(c, occupancy_sort<K>(2));
+    g_merge = grid_of(c, occupancy_sort<K>(3));
+    return WG_OK;
+  }
+
+  // write the pool fields (D .. hist) of the device block
+  int put_pools() {
+    h.D[0] = D[0].p; h.D[1] = D[1].p; h.C[0] = C[0].p; h.C[1] = C[1].p;
+    h.F[0] = F[0].p; h.F[1] = F[1].p; h.R = R.p;
+    h.capC = capC; h.capF = capF; h.capR = capR;
+    h.pos = (unsigned long long*)pos.p;
+    h.status_scalar = (unsigned long long*)st_s.p;
+    h.status_sort = (unsigned long long*)st_k.p;
+    const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
+    CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, c->stream));
+    return WG_OK;
+  }
+
+  // (Re)size the pools; live data (the current delta and full relation and the
+  // retired results) is copied into the new buffers.
+  int ensure(unsigned long long wantC, unsigned long long wantF, unsigned long long wantR,
+             bool keep) {
+    wantC = std::max<unsigned long long>(wantC, 1ull << 16);
+    wantF = std::max<unsigned long long>(wantF, 1ull << 16);
+    wantR = single ? 0 : std::max<unsigned long long>(wantR, 1ull << 16);
+    uint64_t liveD = 0, liveF = 0;
+    if (keep) {
+      for (const Inst& I : hi)
+        if (I.state == INST_ACTIVE) {
+          liveD = std::max<uint64_t>(liveD, I.d_off + I.n_delta);
+          liveF = std::max<uint64_t>(liveF, I.f_off + I.n_full);
+        }
+    }
+    if (wantC > capC) {
+      DBuf nd[2], nc[2], np, ns, nk;
+      for (int i = 0; i < 2; ++i) {
+        TRY(nd[i].get(c, wantC * sizeof(K)));
+        TRY(nc[i].get(c, wantC * sizeof(K)));
+      }
+      TRY(np.get(c, wantC * 8));
+      const size_t tiles = wantC / kTileD + n_slots + 2;
+      TRY(ns.get(c, tiles * 8));
+      TRY(nk.get(c, (wantC / kTileC + n_slots + 2) * kRadix * 8));
+      CK(cudaMemsetAsync(ns.p, 0, ns.bytes, c->stream));
+      CK(cudaMemsetAsync(nk.p, 0, nk.bytes, c->stream));
+      if (liveD)
+        CK(cudaMemcpyAsync(nd[h.dphase].p, D[h.dphase].p, liveD * sizeof(K),
+                           cudaMemcpyDeviceToDevice, c->stream));
+      for (int i = 0; i < 2; ++i) {
+        D[i].release(c); C[i].release(c);
+        D[i] = nd[i]; C[i] = nc[i];
+      }
+      pos.release(c); st_s.release(c); st_k.release(c);
+      pos = np; st_s = ns; st_k = nk;
+      capC = wantC;
+      h.ctl.epoch = 0;
+    }
+    if (wantF > capF) {
+      DBuf nf[2];
+      for (int i = 0; i < 2; ++i) TRY(nf[i].get(c, wantF * sizeof(K)));
+      if (liveF)
+        CK(cudaMemcpyAsync(nf[h.fphase].p, F[h.fphase].p, liveF * sizeof(K),
+                           cudaMemcpyDeviceToDevice, c->stream));
+      for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
+      capF = wantF;
+    }
+    if (!single && wantR > capR) {
+      DBuf nr;
+      TRY(nr.get(c, wantR * sizeof(K)));
+      if (keep && h.r_used)
+        CK(cudaMemcpyAsync(nr.p, R.p, h.r_used * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+      R.release(c);
+      R = nr;
+      capR = wantR;
+    }
+    return put_pools();
+  }
+
+  // The kernels of one semi-naive iteration (Secs. Per-Iteration Pipeline and
+  // Fused Deduplication): join count -> plan -> join emit -> radix histogram ->
+  // radix passes -> fused dedup + set difference -> plan (termination) -> merge.
+  void launch_iteration(cudaStream_t s, std::vector<KStat>* prof = nullptr,
+                        std::vector<cudaEvent_t>* evs = nullptr) {
+    auto mark = [&]() {
+      if (evs) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        evs->push_back(e);
+      }
+    };
+    (void)prof;
+    launch_plan_delta(dv, s);
+    mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s); mark();
+    launch_plan_cand(dv, s);
+    mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
+    mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
+    launch_sort_hscan(dv->st + S_HSCAN, c->num_sms, s);
+    for (uint32_t p = 0; p < passes; ++p) {
+      mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
+    }
+    mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
+    launch_plan_merge(dv, s);
+    mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();
+  }
+
+  int capture() {
+    if (exec) return WG_OK;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    launch_iteration(cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &body);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return set_err(WG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&exec, graph, 0));
+    h.cond = (unsigned long long)cond;
+    CK(cudaMemcpyAsync(&dv->cond, &h.cond, sizeof(h.cond), cudaMemcpyHostToDevice, c->stream));
+    return WG_OK;
+  }
+
+  int put_ctl(uint32_t budget, bool use_cond) {
+    h.ctl.abort = 0; h.ctl.error = 0; h.ctl.cont = 1; h.ctl.launch_iters = 0;
+    h.ctl.iter_budget = budget;
+    h.ctl.need_cand = h.ctl.need_full = h.ctl.need_res = 0;
+    if (h.ctl.epoch > (1u << 22)) {  // clear lookback words before the epoch wraps
+      CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+      CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+      h.ctl.epoch = 0;
+    }
+    CK(cudaMemcpyAsync(&dv->ctl, &h.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    h.use_cond = use_cond ? 1 : 0;
+    CK(cudaMemcpyAsync(&dv->use_cond, &h.use_cond, 4, cudaMemcpyHostToDevice, c->stream));
+    return WG_OK;
+  }
+
+  int read_back() {
+    CK(cudaMemcpyAsync(&h.ctl, &dv->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&h.r_used, &dv->r_used, sizeof(h.r_used), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&h.dphase, &dv->dphase, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hi.data(), b_inst.p, sizeof(Inst) * n_slots, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return WG_OK;
+  }
+
+  // Launch the loop (graph, or one host round trip per iteration).
+  int launch(uint32_t budget, bool host_loop) {
+    if (host_loop) {
+      TRY(put_ctl(budget, false));
+      for (;;) {
+        launch_iteration(c->stream);
+        launches_issued += kernels_per_iter();
+        uint32_t cont = 0;
+        CK(cudaMemcpyAsync(&cont, &dv->ctl.cont, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // the per-iteration host sync
+        if (!cont) break;
+      }
+      CK(cudaGetLastError());
+    } else {
+      TRY(capture());
+      TRY(put_ctl(budget, true));
+      CK(cudaGraphLaunch(exec, c->stream));
+    }
+    CK(cudaEventRecord(ev_done, c->stream));
+    in_flight = true;
+    return WG_OK;
+  }
+
+  // After a launch completed: read the state back; grow and report when a
+  // pool overflowed.  *again = the same loop must be launched once more.
+  int settle(bool* again) {
+    *again = false;
+    in_flight = false;
+    TRY(read_back());
+    // kernels actually issued inside the graph: launch_iters iterations
+    if (exec && h.use_cond)  // body executions: committed iterations, plus one if it aborted
+      launches_issued += (uint64_t)(h.ctl.launch_iters + (h.ctl.abort ? 1u : 0u)) * kernels_per_iter();
+    if (h.ctl.error) return set_err(WG_E_DEVICE_TIMEOUT, "a bounded device wait gave up");
+    if (h.ctl.abort) {
+      ++regrows;
+      const unsigned long long nc = h.ctl.need_cand ? h.ctl.need_cand + h.ctl.need_cand / 4 + 4096 : 0;
+      const unsigned long long nf = h.ctl.need_full ? h.ctl.need_full + h.ctl.need_full / 4 + 4096 : 0;
+      const unsigned long long nr = h.ctl.need_res ? h.ctl.need_res + h.ctl.need_res / 2 + 4096 : 0;
+      TRY(ensure(std::max(capC, nc), std::max(capF, nf), std::max(capR, nr), true));
+      *again = true;
+      return WG_OK;
+    }
+    *again = h.ctl.n_active > 0;
+    return WG_OK;
+  }
+
+  // Fresh instance in `slot` over relation R.
+  int admit(uint32_t slot, Relation* Rl, int kind, uint32_t max_iters, unsigned long long d_off) {
+    Inst I{};
+    I.off = (const uint32_t*)Rl->off.p;
+    I.adj = (const uint32_t*)Rl->adj.p;
+    I.nv = Rl->nv; I.w = Rl->w;
+    I.kind = kind == WG_SG ? KIND_SG : KIND_TC;
+    I.state = INST_ACTIVE;
+    I.iter = 0;
+    I.max_iters = max_iters;
+    I.n_delta = Rl->nv;
+    I.d_off = d_off;
+    I.log = (unsigned long long*)b_log.p + (size_t)slot * log_cap;
+    I.log_cap = log_cap;
+    hi[slot] = I;
+    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    return WG_OK;
+  }
+  int init_deltas(uint32_t first, uint32_t count) {
+    launch_init_diag<K>((Inst*)b_inst.p, first, count, D[h.dphase].p, c->stream);
+    CK(cudaGetLastError());
+    return WG_OK;
+  }
+  int reset_single() {
+    h.dphase = 0; h.fphase = 0; h.r_used = 0;
+    CK(cudaMemcpyAsync(&dv->r_used, &h.r_used, sizeof(h.r_used), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&dv->dphase, &h.dphase, 8, cudaMemcpyHostToDevice, c->stream));
+    return WG_OK;
+  }
+  const void* pool_ptr(uint32_t pool) const {
+    return pool == 2 ? R.p : F[pool & 1].p;
+  }
+};
+
+static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
+                              uint32_t logcap, int* rc) {
+  EngineBase* e;
+  if (kb == 4) {
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap);
+    *rc = x->init();
+    e = x;
+  } else {
+    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap);
+    *rc = x->init();
+    e = x;
+  }
+  if (*rc != WG_OK) { delete e; return nullptr; }
+  return e;
+}
+
+// ------------------------------------------------------------------ single queries
+template <typename K>
+static int single_start(wg_ctx* c, Query* q) {
+  auto* E = static_cast<Engine<K>*>(q->eng);
+  Relation* Rl = q->rel;
+  const unsigned long long wantC = std::max<unsigned long long>(
+      {q->opts.reserve_cand, Rl->peak_cand, 8ull * Rl->ne + Rl->nv, 1ull << 16});
+  const unsigned long long wantF = std::max<unsigned long long>(
+      {q->opts.reserve_full, Rl->peak_full, 4ull * Rl->ne, 1ull << 16});
+  TRY(E->reset_single());
+  TRY(E->ensure(wantC, wantF, 0, false));
+  TRY(E->admit(0, Rl, q->kind, q->opts.max_iters, 0));
+  TRY(E->init_deltas(0, 1));
+  CK(cudaEventRecord(q->ev0, c->stream));
+  const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
+  if (q->opts.profile) {
+    // profiled run: host loop with CUDA events around every stage kernel
+    for (;;) {
+      TRY(E->put_ctl(0xFFFFFFFFu, false));
+      for (;;) {
+        Inst before{};
+        CK(cudaMemcpyAsync(&before, E->b_inst.p, sizeof(Inst), cudaMemcpyDeviceToHost, c->stream));
+        std::vector<cudaEvent_t> evs;
+        E->launch_iteration(c->stream, nullptr, &evs);
+        E->launches_issued += E->kernels_per_iter();
+        Inst after{};
+        uint32_t cont = 0, abort = 0;
+        CK(cudaMemcpyAsync(&after, E->b_inst.p, sizeof(Inst), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&cont, &E->dv->ctl.cont, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(&abort, &E->dv->ctl.abort, 4, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (!abort) {
+          const double kb = sizeof(K);
+          const double nd = (double)before.n_delta, nc = (double)after.n_cand,
+                       nn = (double)after.n_new, nf = (double)before.n_full;
+          // algorithmic bytes of each kernel (see the kernel headers)
+          std::vector<std::pair<const char*, double>> names = {
+              {"join_count", nd * (kb + 8 + 8)},
+              {"join_emit", nd * (kb + 8) + nc * (kb + 4)},
+              {"sort_hist", nc * kb}};
+          for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
+          names.push_back({"dedup_diff", (nc + nn) * kb});
+          names.push_back({"merge", 2 * (nf + nn) * kb});
+          for (size_t i = 0; i < names.size(); ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
+            KStat* st = nullptr;
+            for (auto& s : q->prof)
+              if (!std::strcmp(s.name, names[i].first)) st = &s;
+            if (!st) { q->prof.push_back(KStat{names[i].first}); st = &q->prof.back(); }
+            st->launches += 1; st->ms += ms; st->bytes += names[i].second;
+          }
+        }
+        for (auto e : evs) cudaEventDestroy(e);
+        if (!cont) break;
+      }
+      bool again = false;
+      E->in_flight = true;
+      TRY(E->settle(&again));
+      if (!again) break;
+    }
+    CK(cudaEventRecord(q->ev1, c->stream));
+    CK(cudaEventRecord(E->ev_done, c->stream));
+    E->in_flight = true;
+    q->state = WG_RUNNING;
+    return WG_OK;
+  }
+  TRY(E->launch(0xFFFFFFFFu, host_loop));
+  q->state = WG_RUNNING;
+  return WG_OK;
+}
+
+template <typename K>
+static int single_progress(wg_ctx* c, Query* q, bool block) {
+  auto* E = static_cast<Engine<K>*>(q->eng);
+  for (;;) {
+    if (E->in_flight) {
+      if (block) {
+        CK(cudaEventSynchronize(E->ev_done));
+      } else {
+        cudaError_t e = cudaEventQuery(E->ev_done);
+        if (e == cudaErrorNotReady) return WG_OK;
+        if (e != cudaSuccess) return set_err(WG_E_CUDA, cudaGetErrorString(e));
+      }
+    }
+    bool again = false;
+    int rc = E->settle(&again);
+    if (rc != WG_OK) {
+      q->state = WG_FAILED;
+      q->error = rc;
+      return rc;
+    }
+    if (again) {
+      const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
+      TRY(E->launch(0xFFFFFFFFu, host_loop));
+      continue;
+    }
+    const Inst& I = E->hi[0];
+    if (!q->opts.profile) CK(cudaEventRecord(q->ev1, c->stream));
+    CK(cudaEventSynchronize(q->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, q->ev0, q->ev1);
+    q->device_ms = ms;
+    q->n_tuples = I.n_full;
+    q->iterations = I.iters_done;
+    q->candidates = I.cand_total;
+    q->regrows = E->regrows;
+    q->launches = E->launches_issued;
+    q->res_ptr = (const K*)E->pool_ptr(I.res_pool) + I.res_off;
+    const uint32_t nlog = std::min<uint32_t>(I.iters_done + 1, E->log_cap);
+    q->log.assign(nlog, 0);
+    CK(cudaMemcpy(q->log.data(), I.log, nlog * 8, cudaMemcpyDeviceToHost));
+    q->rel->peak_cand = std::max<uint64_t>(q->rel->peak_cand, E->capC);
+    q->rel->peak_full = std::max<uint64_t>(q->rel->peak_full, E->capF);
+    if (I.state == INST_ITERCAP) {
+      q->state = WG_FAILED;
+      q->error = WG_E_ITER_CAP;
+    } else {
+      q->state = WG_DONE;
+    }
+    q->t_done_us = now_us();
+    return WG_OK;
+  }
+}
+
+// ------------------------------------------------------------------ batches
+// Key classes of batch engines: 32-bit keys (fields <= 16 bits), 64-bit keys
+// with fields <= 24 bits, 64-bit keys with fields <= 32 bits.
+static int batch_class(const Relation* R) { return R->kb == 4 ? 0 : (R->w <= 24 ? 1 : 2); }
+static uint32_t class_bits(int cls) { return cls == 0 ? 32 : (cls == 1 ? 48 : 64); }
+constexpr uint32_t kBatchSlots = 8192;
+constexpr uint32_t kBatchLogCap = 4096;
+
+struct BatchInfo {
+  std::vector<uint64_t> slot_q;  // query id per slot (0 = free)
+};
+static std::map<wg_ctx*, std::map<int, BatchInfo>> g_binfo;
+
+template <typename K>
+static int batch_admit(wg_ctx* c, int cls) {
+  auto& B = g_binfo[c][cls];
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  // live delta region and free slots
+  unsigned long long dend = 0;
+  for (const Inst& I : E->hi)
+    if (I.state == INST_ACTIVE) dend = std::max<unsigned long long>(dend, I.d_off + I.n_delta);
+  uint32_t first = 0xFFFFFFFFu, last = 0;
+  std::vector<uint64_t> still;
+  for (uint64_t qid : c->pending) {
+    auto it = c->queries.find(qid);
+    if (it == c->queries.end()) continue;
+    Query* q = it->second.get();
+    if (q->bclass != cls) { still.push_back(qid); continue; }
+    uint32_t slot = 0xFFFFFFFFu;
+    for (uint32_t s = 0; s < E->n_slots; ++s)
+      if (B.slot_q[s] == 0 && (E->hi[s].state != INST_ACTIVE)) { slot = s; break; }
+    // admission by memory: the fresh delta must fit in the candidate pools
+    if (slot == 0xFFFFFFFFu || dend + q->rel->nv > E->capC) { still.push_back(qid); continue; }
+    TRY(E->admit(slot, q->rel, q->kind, q->opts.max_iters, dend));
+    dend += q->rel->nv;
+    B.slot_q[slot] = qid;
+    q->slot = slot;
+    q->state = WG_RUNNING;
+    first = std::min(first, slot);
+    last = std::max(last, slot);
+  }
+  c->pending.swap(still);
+  if (first != 0xFFFFFFFFu) TRY(E->init_deltas(first, last - first + 1));
+  return WG_OK;
+}
+
+template <typename K>
+static int batch_retire(wg_ctx* c, int cls) {
+  auto& B = g_binfo[c][cls];
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  for (uint32_t s = 0; s < E->n_slots; ++s) {
+    if (!B.slot_q[s]) continue;
+    const Inst& I = E->hi[s];
+    if (I.state != INST_DONE && I.state != INST_ITERCAP) continue;
+    auto it = c->queries.find(B.slot_q[s]);
+    B.slot_q[s] = 0;
+    Inst cleared = I;
+    cleared.state = INST_FREE;
+    E->hi[s] = cleared;
+    CK(cudaMemcpyAsync((Inst*)E->b_inst.p + s, &cleared, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    if (it == c->queries.end()) continue;  // freed while running
+    Query* q = it->second.get();
+    q->n_tuples = I.n_full;
+    q->iterations = I.iters_done;
+    q->candidates = I.cand_total;
+    const uint32_t nlog = std::min<uint32_t>(I.iters_done + 1, E->log_cap);
+    q->log.assign(nlog, 0);
+    CK(cudaMemcpyAsync(q->log.data(), I.log, nlog * 8, cudaMemcpyDeviceToHost, c->stream));
+    TRY(q->res_own.get(c, std::max<size_t>(I.n_full, 1) * sizeof(K)));
+    if (I.n_full)
+      CK(cudaMemcpyAsync(q->res_own.p, (const K*)E->pool_ptr(I.res_pool) + I.res_off,
+                         I.n_full * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+    q->res_ptr = q->res_own.p;
+    q->state = I.state == INST_DONE ? WG_DONE : WG_FAILED;
+    q->error = I.state == INST_DONE ? WG_OK : WG_E_ITER_CAP;
+    q->t_done_us = now_us();
+  }
+  // every retired result has been copied out: the retire pool starts over
+  E->h.r_used = 0;
+  CK(cudaMemcpyAsync(&E->dv->r_used, &E->h.r_used, 8, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return WG_OK;
+}
+
+template <typename K>
+static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  if (E->in_flight) {
+    if (!wait_launch) {
+      cudaError_t e = cudaEventQuery(E->ev_done);
+      if (e == cudaErrorNotReady) return WG_OK;
+    }
+    CK(cudaEventSynchronize(E->ev_done));
+    bool again = false;
+    int rc = E->settle(&again);
+    if (rc != WG_OK) {
+      auto& B = g_binfo[c][cls];
+      for (uint32_t s = 0; s < E->n_slots; ++s)
+        if (B.slot_q[s]) {
+          auto it = c->queries.find(B.slot_q[s]);
+          if (it != c->queries.end()) { it->second->state = WG_FAILED; it->second->error = rc; }
+          B.slot_q[s] = 0;
+        }
+      return rc;
+    }
+    TRY(batch_retire<K>(c, cls));
+  }
+  TRY(batch_admit<K>(c, cls));
+  bool any = false;
+  for (const Inst& I : E->hi) any |= I.state == INST_ACTIVE;
+  if (any) TRY(E->launch(iters, false));
+  return WG_OK;
+}
+
+static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
+  if (!c->batch[cls]) return WG_OK;
+  return c->batch[cls]->kb() == 4 ? batch_round<uint32_t>(c, cls, iters, wait_launch)
+                                   : batch_round<unsigned long long>(c, cls, iters, wait_launch);
+}
+
+static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
+  if (c->batch[cls]) return WG_OK;
+  int rc = WG_OK;
+  EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, &rc);
+  if (!e) return rc;
+  c->batch[cls].reset(e);
+  g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
+  const unsigned long long budget_keys = (unsigned long long)((c->budget - c->used) / 4 / R->kb / 8);
+  const unsigned long long capC = std::max<unsigned long long>(1ull << 22, budget_keys);
+  if (R->kb == 4)
+    return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 2, false);
+  return static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 2, false);
+}
+
+template <typename K>
+static int copy_result(wg_ctx* c, Query* q, unsigned long long* dst, bool host) {
+  const size_t n = q->n_tuples;
+  if (!n) return WG_OK;
+  const size_t chunk = host ? (size_t)1 << 24 : n;
+  DBuf tmp;
+  if (host) TRY(tmp.get(c, std::min(n, chunk) * 8));
+  for (size_t at = 0; at < n; at += chunk) {
+    const size_t m = std::min(chunk, n - at);
+    unsigned long long* o = host ? (unsigned long long*)tmp.p : dst + at;
+    launch_result_map<K>((const K*)q->res_ptr + at, m, q->rel->w, (const uint32_t*)q->rel->V.p, o,
+                         grid_of(c, 4), c->stream);
+    CK(cudaGetLastError());
+    if (host) CK(cudaMemcpyAsync(dst + at, tmp.p, m * 8, cudaMemcpyDeviceToHost, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  tmp.release(c);
+  return WG_OK;
+}
+
+// ------------------------------------------------------------------ C-ABI
+extern "C" {
+
+const char* wg_last_error(void) { return g_err.c_str(); }
+
+int wg_init(int device, size_t budget, wg_alloc_fn alloc, wg_free_fn free_fn, void* user,
+            void* stream, wg_ctx** out) {
+  if (!out) return set_err(WG_E_INVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return set_err(WG_E_INVAL, "no such device");
+  CK(cudaSetDevice(device));
+  auto c = std::make_unique<wg_ctx>();
+  c->device = device;
+  c->alloc = alloc; c->free_fn = free_fn; c->user = user;
+  CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  c->budget = budget ? budget : (size_t)(0.9 * (double)fr);
+  *out = c.release();
+  return WG_OK;
+}
+
+void wg_destroy(wg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->queries) kv.second->res_own.release(c);
+  for (auto& kv : c->queries) {
+    Query* q = kv.second.get();
+    if (q->ev0) cudaEventDestroy(q->ev0);
+    if (q->ev1) cudaEventDestroy(q->ev1);
+    if (q->eng) q->eng->release();
+  }
+  c->queries.clear();
+  for (auto& e : c->idle) e->release();
+  c->idle.clear();
+  for (auto& kv : c->batch) if (kv.second) kv.second->release();
+  c->batch.clear();
+  g_binfo.erase(c);
+  for (auto& kv : c->rels) kv.second->release(c);
+  c->rels.clear();
+  dev_free(c, c->s_tmp, c->s_tmp_bytes);
+  dev_free(c, c->s_status, c->s_status_n * 8);
+  dev_free(c, c->s_hist, sizeof(unsigned long long) * kMaxPasses * kRadix);
+  dev_free(c, c->s_stage, sizeof(Stage) * S_NUM);
+  dev_free(c, c->s_seg, sizeof(Seg));
+  dev_free(c, c->s_ctl, sizeof(Ctl));
+  cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+size_t wg_mem_used(const wg_ctx* c) { return c ? c->used : 0; }
+
+static int load_common(wg_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, size_t n,
+                       wg_rel* out) {
+  auto R = std::make_unique<Relation>();
+  int rc = load_relation(c, d_src, d_dst, n, R.get());
+  if (rc != WG_OK) { R->release(c); return rc; }
+  CK(cudaStreamSynchronize(c->stream));
+  const uint64_t id = c->next_id++;
+  c->rels[id] = std::move(R);
+  *out = id;
+  return WG_OK;
+}
+
+int wg_relation_load(wg_ctx* c, const uint32_t* src, const uint32_t* dst, size_t n, wg_rel* out) {
+  if (!c || !out || (n && (!src || !dst))) return set_err(WG_E_INVAL, "bad argument");
+  *out = 0;
+  DBuf s, d;
+  if (n) {
+    TRY(s.get(c, n * 4));
+    TRY(d.get(c, n * 4));
+    CK(cudaMemcpyAsync(s.p, src, n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d.p, dst, n * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  int rc = load_common(c, (const uint32_t*)s.p, (const uint32_t*)d.p, n, out);
+  s.release(c);
+  d.release(c);
+  return rc;
+}
+
+int wg_relation_load_device(wg_ctx* c, const uint32_t* d_src, const uint32_t* d_dst, size_t n,
+                            wg_rel* out) {
+  if (!c || !out || (n && (!d_src || !d_dst))) return set_err(WG_E_INVAL, "bad argument");
+  *out = 0;
+  return load_common(c, d_src, d_dst, n, out);
+}
+
+int wg_relation_info(wg_ctx* c, wg_rel r, uint64_t* ne, uint32_t* nv, uint32_t* bits) {
+  if (!c) return set_err(WG_E_INVAL, "ctx is NULL");
+  auto it = c->rels.find(r);
+  if (it == c->rels.end()) return set_err(WG_E_INVAL, "no such relation");
+  if (ne) *ne = it->second->ne;
+  if (nv) *nv = it->second->nv;
+  if (bits) *bits = it->second->w;
+  return WG_OK;
+}
+
+void wg_relation_free(wg_ctx* c, wg_rel r) {
+  if (!c) return;
+  auto it = c->rels.find(r);
+  if (it == c->rels.end()) return;
+  for (auto& kv : c->queries)
+    if (kv.second->rel == it->second.get() && kv.second->state == WG_RUNNING) return;  // in use
+  cudaStreamSynchronize(c->stream);
+  it->second->release(c);
+  c->rels.erase(it);
+}
+
+static int make_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, Query** out) {
+  auto it = c->rels.find(edges);
+  if (it == c->rels.end()) return set_err(WG_E_INVAL, "no such relation");
+  auto q = std::make_unique<Query>();
+  q->id = c->next_id++;
+  q->kind = kind;
+  q->rel = it->second.get();
+  q->rel_id = edges;
+  if (opts) q->opts = *opts;
+  if (q->opts.max_iters == 0) q->opts.max_iters = 1u << 20;
+  CK(cudaEventCreate(&q->ev0));
+  CK(cudaEventCreate(&q->ev1));
+  q->t_submit_us = now_us();
+  *out = q.get();
+  c->queries[q->id] = std::move(q);
+  return WG_OK;
+}
+
+static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, wg_query* out) {
+  if (!c || !out) return set_err(WG_E_INVAL, "bad argument");
+  *out = 0;
+  Query* q;
+  TRY(make_query(c, kind, edges, opts, &q));
+  Relation* R = q->rel;
+  const uint32_t bits = 2 * R->w;
+  // reuse an idle engine of the same key width and pass plan
+  for (size_t i = 0; i < c->idle.size(); ++i)
+    if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits) {
+      q->own = std::move(c->idle[i]);
+      c->idle.erase(c->idle.begin() + i);
+      break;
+    }
+  int rc = WG_OK;
+  if (!q->own) {
+    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, &rc);
+    if (!e) { c->queries.erase(q->id); return rc; }
+    q->own.reset(e);
+  }
+  q->eng = q->own.get();
+  if (R->kb == 4) {
+    auto* E = static_cast<Engine<uint32_t>*>(q->eng);
+    E->regrows = 0; E->launches_issued = 0;
+    rc = single_start<uint32_t>(c, q);
+  } else {
+    auto* E = static_cast<Engine<unsigned long long>*>(q->eng);
+    E->regrows = 0; E->launches_issued = 0;
+    rc = single_start<unsigned long long>(c, q);
+  }
+  if (rc != WG_OK) {
+    q->state = WG_FAILED;
+    q->error = rc;
+  }
+  *out = q->id;
+  return rc;
+}
+
+int wg_tc(wg_ctx* c, wg_rel edges, const wg_opts* opts, wg_query* out) {
+  return single_query(c, WG_TC, edges, opts, out);
+}
+int wg_sg(wg_ctx* c, wg_rel edges, const wg_opts* opts, wg_query* out) {
+  return single_query(c, WG_SG, edges, opts, out);
+}
+
+int wg_submit(wg_ctx* c, const wg_request* reqs, size_t n, wg_query* ids) {
+  if (!c || (n && (!reqs || !ids))) return set_err(WG_E_INVAL, "bad argument");
+  for (size_t i = 0; i < n; ++i) {
+    ids[i] = 0;
+    if (reqs[i].kind != WG_TC && reqs[i].kind != WG_SG) return set_err(WG_E_INVAL, "bad kind");
+    Query* q;
+    TRY(make_query(c, reqs[i].kind, reqs[i].edges, &reqs[i].opts, &q));
+    q->batch = true;
+    q->bclass = batch_class(q->rel);
+    TRY(ensure_batch_engine(c, q->bclass, q->rel));
+    c->pending.push_back(q->id);
+    ids[i] = q->id;
+  }
+  return WG_OK;
+}
+
+int wg_serve_step(wg_ctx* c, uint32_t iters, size_t* n_running) {
+  if (!c) return set_err(WG_E_INVAL, "ctx is NULL");
+  if (iters == 0) iters = 0xFFFFFFFFu;
+  for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, iters, true));
+  if (n_running) {
+    size_t r = 0;
+    for (auto& kv : c->queries) r += kv.second->batch && kv.second->state == WG_RUNNING;
+    *n_running = r + c->pending.size();
+  }
+  return WG_OK;
+}
+
+static Query* find_q(wg_ctx* c, wg_query id) {
+  auto it = c->queries.find(id);
+  return it == c->queries.end() ? nullptr : it->second.get();
+}
+
+static int progress(wg_ctx* c, Query* q, bool block) {
+  if (q->state == WG_DONE || q->state == WG_FAILED) return WG_OK;
+  if (q->batch) {
+    // drive the batch engine until this query is retired
+    do {
+      for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, 0xFFFFFFFFu, block));
+    } while (block && q->state != WG_DONE && q->state != WG_FAILED);
+    return WG_OK;
+  }
+  return q->eng->kb() == 4 ? single_progress<uint32_t>(c, q, block)
+                           : single_progress<unsigned long long>(c, q, block);
+}
+
+int wg_poll(wg_ctx* c, wg_query id, wg_status* st) {
+  if (!c || !st) return set_err(WG_E_INVAL, "bad argument");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  int rc = progress(c, q, false);
+  st->state = q->state;
+  st->error = q->error;
+  st->n_tuples = q->n_tuples;
+  st->iterations = q->iterations;
+  st->regrows = q->regrows;
+  st->candidates = q->candidates;
+  st->gpu_launches = q->launches;
+  st->device_ms = q->device_ms;
+  return rc == WG_E_DEVICE_TIMEOUT || rc == WG_E_CUDA ? rc : WG_OK;
+}
+
+int wg_wait(wg_ctx* c, wg_query id, uint64_t timeout_us) {
+  if (!c) return set_err(WG_E_INVAL, "ctx is NULL");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  const double t0 = now_us();
+  for (;;) {
+    const bool block = timeout_us == 0;
+    TRY(progress(c, q, block));
+    if (q->state == WG_DONE) return WG_OK;
+    if (q->state == WG_FAILED) return set_err(q->error, "query failed");
+    if (timeout_us && now_us() - t0 > (double)timeout_us) return WG_E_NOT_READY;
+  }
+}
+
+static int result_common(wg_ctx* c, wg_query id, uint64_t* keys, size_t cap, size_t* n_out,
+                         bool host) {
+  if (!c || !n_out) return set_err(WG_E_INVAL, "bad argument");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  if (q->state != WG_DONE) return set_err(q->state == WG_FAILED ? q->error : WG_E_NOT_READY, "result not ready");
+  *n_out = q->n_tuples;
+  if (cap < q->n_tuples) return set_err(WG_E_CAPACITY, "buffer too small");
+  if (q->n_tuples && !keys) return set_err(WG_E_INVAL, "keys is NULL");
+  return q->rel->kb == 4 ? copy_result<uint32_t>(c, q, (unsigned long long*)keys, host)
+                         : copy_result<unsigned long long>(c, q, (unsigned long long*)keys, host);
+}
+
+int wg_result_copy(wg_ctx* c, wg_query q, uint64_t* keys, size_t cap, size_t* n_out) {
+  return result_common(c, q, keys, cap, n_out, true);
+}
+int wg_result_copy_device(wg_ctx* c, wg_query q, uint64_t* d_keys, size_t cap, size_t* n_out) {
+  return result_common(c, q, d_keys, cap, n_out, false);
+}
+
+int wg_result_iters(wg_ctx* c, wg_query id, uint64_t* sizes, size_t cap, size_t* n_out) {
+  if (!c || !n_out) return set_err(WG_E_INVAL, "bad argument");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  if (q->state != WG_DONE && q->state != WG_FAILED) return set_err(WG_E_NOT_READY, "not finished");
+  *n_out = q->log.size();
+  if (cap < q->log.size()) return set_err(WG_E_CAPACITY, "buffer too small");
+  if (!q->log.empty()) std::memcpy(sizes, q->log.data(), q->log.size() * 8);
+  return WG_OK;
+}
+
+int wg_result_profile(wg_ctx* c, wg_query id, wg_kernel_stat* stats, size_t cap, size_t* n_out) {
+  if (!c || !n_out) return set_err(WG_E_INVAL, "bad argument");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  *n_out = q->prof.size();
+  if (cap < q->prof.size()) return set_err(WG_E_CAPACITY, "buffer too small");
+  for (size_t i = 0; i < q->prof.size(); ++i) {
+    std::memset(&stats[i], 0, sizeof(wg_kernel_stat));
+    std::snprintf(stats[i].name, sizeof(stats[i].name), "%s", q->prof[i].name);
+    stats[i].launches = q->prof[i].launches;
+    stats[i].total_ms = q->prof[i].ms;
+    stats[i].bytes = q->prof[i].bytes;
+  }
+  return WG_OK;
+}
+
+void wg_query_free(wg_ctx* c, wg_query id) {
+  if (!c) return;
+  auto it = c->queries.find(id);
+  if (it == c->queries.end()) return;
+  Query* q = it->second.get();
+  if (q->state == WG_RUNNING && !q->batch) progress(c, q, true);
+  if (q->batch && q->state == WG_PENDING) {
+    c->pending.erase(std::remove(c->pending.begin(), c->pending.end(), id), c->pending.end());
+  }
+  cudaStreamSynchronize(c->stream);
+  q->res_own.release(c);
+  if (q->ev0) cudaEventDestroy(q->ev0);
+  if (q->ev1) cudaEventDestroy(q->ev1);
+  if (q->own) c->idle.push_back(std::move(q->own));  // keep pools and graph for the next query
+  c->queries.erase(it);
+}
+
+int wg_sort_keys(wg_ctx* c, void* d_keys, size_t n, int kb, uint32_t bits) {
+  if (!c || (n && !d_keys) || (kb != 4 && kb != 8) || bits == 0 || bits > 8u * kb)
+    return set_err(WG_E_INVAL, "bad argument");
+  int rc = kb == 4 ? prim_sort<uint32_t>(c, (uint32_t*)d_keys, n, bits)
+                   : prim_sort<unsigned long long>(c, (unsigned long long*)d_keys, n, bits);
+  if (rc != WG_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return WG_OK;
+}
+
+int wg_unique_diff(wg_ctx* c, const void* cand, size_t n, const void* full, size_t nf, void* out,
+                   size_t* n_out, int kb) {
+  if (!c || !n_out || (n && (!cand || !out)) || (nf && !full) || (kb != 4 && kb != 8))
+    return set_err(WG_E_INVAL, "bad argument");
+  return kb == 4 ? prim_unique<uint32_t>(c, (const uint32_t*)cand, n, (const uint32_t*)full, nf,
+                                         (uint32_t*)out, n_out)
+                 : prim_unique<unsigned long long>(c, (const unsigned long long*)cand, n,
+                                                   (const unsigned long long*)full, nf,
+                                                   (unsigned long long*)out, n_out);
+}
+
+int wg_merge_disjoint(wg_ctx* c, const void* a, size_t na, const void* b, size_t nb, void* out,
+                      int kb) {
+  if (!c || (na && !a) || (nb && !b) || (na + nb && !out) || (kb != 4 && kb != 8))
+    return set_err(WG_E_INVAL, "bad argument");
+  int rc = kb == 4 ? prim_merge<uint32_t>(c, (const uint32_t*)a, na, (const uint32_t*)b, nb, (uint32_t*)out)
+                   : prim_merge<unsigned long long>(c, (const unsigned long long*)a, na,
+                                                    (const unsigned long long*)b, nb,
+                                                    (unsigned long long*)out);
+  if (rc != WG_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return WG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,555 @@
+// wg_kern_join.cu -- the join of one semi-naive iteration and the engine's
+// device-side control (sm_103a).
+//
+// Join (Sec. Binary-Search Join, "Two-phase algorithm"): a count phase gives
+// every delta tuple the size of its output slab -- for TC the out-degree of its
+// destination, for SG the product of the two out-degrees -- and a single-pass
+// scan (decoupled lookback) turns the counts into slab offsets; the emit phase
+// writes every candidate into its slab with no atomics.  The edge relation is
+// sorted once at load and indexed by source (CSR offsets), so the range lookup
+// is two loads instead of a binary search.  Emit is partitioned by OUTPUT
+// position (load-balanced search over the slab offsets), so a hub with
+// thousands of edges is spread over many threads instead of serialising one.
+//
+// Plan kernels (one CTA) are the CUDA form of the paper's lightweight
+// dispatch-parameter kernel (Sec. Batched Indirect-Dispatch Loop): they read
+// the sizes the previous stage left in device memory and write the next
+// stage's work description.  plan_merge also makes the termination decision
+// (Sec. Background, step 5) and sets the graph's WHILE condition.
+#include "wg_device.cuh"
+#include "wg_launch.h"
+
+namespace wg {
+
+constexpr int kPlanThreads = 1024;
+
+__device__ __forceinline__ unsigned long long scan1024(unsigned long long v, unsigned long long* sh,
+                                                       unsigned long long* total) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  const unsigned long long wp = warp ? sh[warp - 1] : 0ull;
+  *total = sh[31];
+  __syncthreads();
+  return wp + x - v;
+}
+
+__device__ __forceinline__ uint32_t deg(const uint32_t* off, uint32_t v) { return off[v + 1] - off[v]; }
+
+// ------------------------------------------------------------------ join count
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
+  __shared__ K sd[kTileD];
+  __shared__ unsigned long long sp[kTileD];
+  __shared__ unsigned long long s_scan[kWarps];
+  __shared__ unsigned long long s_excl;
+  __shared__ uint32_t s_t, s_bad;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  // the radix histogram of this iteration starts from zero
+  const unsigned long long nz = (unsigned long long)stp->nseg * stp->passes * kRadix;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; i < nz;
+       i += (unsigned long long)gridDim.x * kThreads)
+    stp->hist[i] = 0;
+  const K* D = (const K*)stp->in;
+  unsigned long long* pos = stp->pos;
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
+  unsigned long long* status = stp->status;
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const Inst* I = stp->inst + sg.inst;
+    const uint32_t* off = I->off;
+    const uint32_t w = I->w, kind = I->kind, iter = I->iter;
+    const K mask = (K)(((K)1 << w) - 1);
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileD;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTileD, sg.n - start);
+    const K* p = D + sg.in_off + start;
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sd[i] = p[i];
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    const uint32_t b = threadIdx.x * kItemsD;
+    unsigned long long c[kItemsD], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kItemsD; ++i) {
+      c[i] = 0;
+      if (b + i < n) {
+        const K key = sd[b + i];
+        const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
+        if (kind == KIND_TC) {
+          c[i] = deg(off, y);                                  // T(x,y), E(y,z)
+        } else if (iter == 0) {
+          const unsigned long long d = deg(off, x);            // E(p,x), E(p,y), x != y
+          c[i] = d ? d * (d - 1) : 0;
+        } else {
+          c[i] = (unsigned long long)deg(off, x) * deg(off, y);  // E(a,x), sg(a,b), E(b,y)
+        }
+        sum += c[i];
+      }
+    }
+    unsigned long long tot;
+    const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);
+    const bool first = (t == sg.tile0);
+    if (threadIdx.x == 0) st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, tot));
+    if (!first && threadIdx.x < 32) {
+      const unsigned long long ex = lookback_scalar(status, t, sg.tile0, epoch, ctl);
+      if (threadIdx.x == 0) {
+        s_excl = ex;
+        if (*(volatile uint32_t*)&ctl->abort) s_bad = 1;
+        st_put(status + t, st_pack(epoch, FLAG_INC, ex + tot));
+      }
+    } else if (first && threadIdx.x == 0) {
+      s_excl = 0;
+    }
+    __syncthreads();
+    if (s_bad) return;
+    unsigned long long run = s_excl + texcl;
+#pragma unroll
+    for (int i = 0; i < kItemsD; ++i)
+      if (b + i < n) { sp[b + i] = run; run += c[i]; }
+    __syncthreads();
+    unsigned long long* q = pos + sg.in_off + start;
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) q[i] = sp[i];
+    if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = s_excl + tot;
+  }
+}
+
+// ------------------------------------------------------------------ join emit
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
+  __shared__ unsigned long long spos[kEmitWin];
+  __shared__ K skey[kEmitWin];
+  __shared__ unsigned long long s_i0, s_i1;
+  __shared__ uint32_t s_t;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* D = (const K*)stp->in;
+  K* C = (K*)stp->out;
+  const unsigned long long* pos_all = stp->pos;
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles;
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const Inst* I = stp->inst + sg.inst;
+    const uint32_t* off = I->off;
+    const uint32_t* adj = I->adj;
+    const uint32_t w = I->w, kind = I->kind, iter = I->iter;
+    const K mask = (K)(((K)1 << w) - 1);
+    const unsigned long long* P = pos_all + sg.in_off;
+    const K* Dq = D + sg.in_off;
+    const unsigned long long o0 = (unsigned long long)(t - sg.tile0) * kTileC;
+    const unsigned long long o1 = min(o0 + kTileC, sg.aux_n);
+    // delta tuples whose slabs cover [o0, o1): the last tuple starting at or
+    // before o0 through the last starting at or before o1 - 1
+    if (threadIdx.x == 0) s_i0 = upper_bound_k(P, sg.n, o0) - 1;
+    if (threadIdx.x == 32) s_i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
+    __syncthreads();
+    const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
+    const bool staged = m <= (unsigned long long)kEmitWin;
+    if (staged) {
+      for (uint32_t i = threadIdx.x; i < m; i += kThreads) {
+        spos[i] = P[i0 + i];
+        skey[i] = Dq[i0 + i];
+      }
+    }
+    __syncthreads();
+    K* Cq = C + sg.out_off;
+#pragma unroll 4
+    for (int j = 0; j < kItemsC; ++j) {
+      const unsigned long long o = o0 + (unsigned long long)j * kThreads + threadIdx.x;
+      if (o >= o1) break;
+      // largest i with pos[i] <= o
+      unsigned long long lo = 0, hi = m;
+      if (staged) {
+        while (hi - lo > 1) {
+          const unsigned long long mid = (lo + hi) >> 1;
+          if (spos[mid] <= o) lo = mid; else hi = mid;
+        }
+      } else {
+        while (hi - lo > 1) {
+          const unsigned long long mid = (lo + hi) >> 1;
+          if (P[i0 + mid] <= o) lo = mid; else hi = mid;
+        }
+      }
+      const unsigned long long r = o - (staged ? spos[lo] : P[i0 + lo]);
+      const K key = staged ? skey[lo] : Dq[i0 + lo];
+      const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
+      K outk;
+      if (kind == KIND_TC) {
+        outk = ((K)x << w) | (K)adj[off[y] + r];
+      } else if (iter == 0) {
+        const uint32_t dm1 = deg(off, x) - 1;  // ordered pairs of distinct children of x
+        const uint32_t qa = (uint32_t)(r / dm1);
+        uint32_t qb = (uint32_t)(r - (unsigned long long)qa * dm1);
+        qb += qb >= qa;
+        outk = ((K)adj[off[x] + qa] << w) | (K)adj[off[x] + qb];
+      } else {
+        const uint32_t db = deg(off, y);
+        const uint32_t qa = (uint32_t)(r / db);
+        const uint32_t qb = (uint32_t)(r - (unsigned long long)qa * db);
+        outk = ((K)adj[off[x] + qa] << w) | (K)adj[off[y] + qb];
+      }
+      Cq[o] = outk;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ plan kernels
+__global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long s_carry;
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort) return;
+  const uint32_t N = dv->n_inst;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    const bool valid = q < N;
+    const Inst* I = valid ? dv->inst + q : nullptr;
+    const bool act = valid && I->state == INST_ACTIVE;
+    const unsigned long long nd = act ? I->n_delta : 0ull;
+    const unsigned long long nt = (nd + kTileD - 1) / kTileD;
+    unsigned long long tot;
+    const unsigned long long ex = scan1024(nt, sh, &tot);
+    if (valid) {
+      Seg s;
+      s.in_off = I->d_off; s.n = nd; s.out_off = I->d_off; s.aux_off = 0; s.aux_n = 0; s.res = 0;
+      s.tile0 = (uint32_t)(s_carry + ex); s.ntiles = (uint32_t)nt; s.inst = q; s.flags = 0;
+      dv->segD[q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Stage& s = dv->st[S_COUNT];
+    s.in = dv->D[dv->dphase]; s.out = nullptr; s.aux = nullptr; s.out2 = nullptr;
+    s.segs = dv->segD; s.inst = dv->inst; s.ctl = &dv->ctl;
+    s.status = dv->status_scalar; s.hist = dv->hist; s.pos = dv->pos;
+    s.nseg = N; s.ntiles = (uint32_t)s_carry; s.ctr = 0; s.epoch = ++ctl.epoch;
+    s.passes = dv->passes; s.dbits = dv->dbits; s.shift = 0; s.pass = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long s_cc, s_ct;
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort) return;
+  const uint32_t N = dv->n_inst;
+  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    const bool valid = q < N;
+    Inst* I = valid ? dv->inst + q : nullptr;
+    const bool act = valid && I->state == INST_ACTIVE;
+    const unsigned long long nc = act ? dv->segD[q].res : 0ull;
+    const unsigned long long nt = (nc + kTileC - 1) / kTileC;
+    unsigned long long totc, tott;
+    const unsigned long long exc = scan1024(nc, sh, &totc);
+    const unsigned long long ext = scan1024(nt, sh, &tott);
+    if (valid) {
+      const unsigned long long c_off = s_cc + exc;
+      const uint32_t tile0 = (uint32_t)(s_ct + ext);
+      I->n_cand = nc;
+      I->c_off = c_off;
+      Seg e;
+      e.in_off = I->d_off; e.n = act ? I->n_delta : 0ull; e.out_off = c_off;
+      e.aux_off = 0; e.aux_n = nc; e.res = 0; e.tile0 = tile0; e.ntiles = (uint32_t)nt;
+      e.inst = q; e.flags = 0;
+      dv->segE[q] = e;
+      Seg s = e;
+      s.in_off = c_off; s.n = nc; s.aux_n = 0;
+      dv->segS[q] = s;
+      Seg u = s;
+      u.aux_off = I->f_off; u.aux_n = act ? I->n_full : 0ull;
+      dv->segU[q] = u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_cc += totc; s_ct += tott; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (s_cc > dv->capC) {  // candidates do not fit: stop before anything is written
+      ctl.need_cand = s_cc;
+      ctl.abort = 1;
+      return;
+    }
+    const uint32_t nt = (uint32_t)s_ct;
+    Stage base{};
+    base.segs = dv->segS; base.inst = dv->inst; base.ctl = &dv->ctl; base.hist = dv->hist;
+    base.pos = dv->pos; base.nseg = N; base.ntiles = nt; base.ctr = 0;
+    base.passes = dv->passes; base.dbits = dv->dbits;
+    Stage e = base;
+    e.in = dv->D[dv->dphase]; e.out = dv->C[0]; e.segs = dv->segE;
+    dv->st[S_EMIT] = e;
+    Stage h = base;
+    h.in = dv->C[0];
+    dv->st[S_HIST] = h;
+    dv->st[S_HSCAN] = base;
+    for (uint32_t p = 0; p < dv->passes; ++p) {
+      Stage s = base;
+      s.in = dv->C[p & 1]; s.out = dv->C[(p + 1) & 1];
+      s.status = dv->status_sort; s.shift = p * dv->dbits; s.pass = p; s.epoch = ++ctl.epoch;
+      dv->st[S_PASS0 + p] = s;
+    }
+    Stage u = base;
+    u.in = dv->C[dv->passes & 1]; u.aux = dv->F[dv->fphase]; u.out = dv->D[dv->dphase ^ 1];
+    u.segs = dv->segU; u.status = dv->status_scalar; u.epoch = ++ctl.epoch;
+    dv->st[S_UNIQ] = u;
+  }
+}
+
+__device__ __forceinline__ void set_continue(Dev* dv, uint32_t v) {
+  dv->ctl.cont = v;
+  if (dv->use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)dv->cond, v);
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan_merge(Dev* dv) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long s_f, s_r, s_t, s_act;
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort) {
+    if (threadIdx.x == 0) set_continue(dv, 0);
+    return;
+  }
+  const uint32_t N = dv->n_inst;
+  const bool single = dv->single != 0;
+  // pass 1: sizes only, so that a capacity overflow leaves the state untouched
+  if (threadIdx.x == 0) { s_f = 0; s_r = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    unsigned long long fsz = 0, rsz = 0;
+    if (q < N) {
+      const Inst* I = dv->inst + q;
+      if (I->state == INST_ACTIVE) {
+        const unsigned long long nn = dv->segU[q].res, nf = I->n_full + nn;
+        const bool done = I->iter >= 1 && nn == 0;
+        const bool fin = done || I->iter >= I->max_iters;
+        if (done && single) {
+          // the full relation is final where it is
+        } else if (fin && !single) {
+          rsz = nf;
+        } else {
+          fsz = nf;
+        }
+      }
+    }
+    unsigned long long tf, tr;
+    scan1024(fsz, sh, &tf);
+    scan1024(rsz, sh, &tr);
+    if (threadIdx.x == 0) { s_f += tf; s_r += tr; }
+    __syncthreads();
+  }
+  if (s_f > dv->capF || dv->r_used + s_r > dv->capR) {
+    if (threadIdx.x == 0) {
+      ctl.need_full = s_f;
+      ctl.need_res = dv->r_used + s_r;
+      ctl.abort = 1;
+      set_continue(dv, 0);
+    }
+    return;
+  }
+  // pass 2: commit the iteration
+  const uint32_t fph = dv->fphase, dph = dv->dphase;
+  if (threadIdx.x == 0) { s_f = 0; s_r = dv->r_used; s_t = 0; s_act = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    const bool valid = q < N;
+    Inst* I = valid ? dv->inst + q : nullptr;
+    const bool act = valid && I->state == INST_ACTIVE;
+    unsigned long long nn = 0, nf = 0, fsz = 0, rsz = 0, mt = 0;
+    bool fin = false, done = false, toR = false, keep = false;
+    if (act) {
+      nn = dv->segU[q].res;
+      nf = I->n_full + nn;
+      done = I->iter >= 1 && nn == 0;
+      fin = done || I->iter >= I->max_iters;
+      keep = done && single;  // nothing to merge and nothing runs after it
+      toR = fin && !single;
+      if (keep) {
+      } else if (toR) {
+        rsz = nf;
+      } else {
+        fsz = nf;
+      }
+      mt = keep ? 0ull : (nf + kTileM - 1) / kTileM;
+    }
+    unsigned long long tf, tr, tt, ta;
+    const unsigned long long exf = scan1024(fsz, sh, &tf);
+    const unsigned long long exr = scan1024(rsz, sh, &tr);
+    const unsigned long long ext = scan1024(mt, sh, &tt);
+    const unsigned long long exa = scan1024((act && !fin) ? 1ull : 0ull, sh, &ta);
+    (void)exa;
+    if (valid) {
+      Seg m;
+      m.in_off = I->f_off; m.n = act ? I->n_full : 0ull; m.aux_off = I->c_off; m.aux_n = nn;
+      m.res = 0; m.tile0 = (uint32_t)(s_t + ext); m.ntiles = (uint32_t)mt; m.inst = q;
+      m.flags = toR ? 1u : 0u;
+      const unsigned long long dst_off = keep ? I->f_off : (toR ? s_r + exr : s_f + exf);
+      m.out_off = dst_off;
+      dv->segM[q] = m;
+      if (act) {
+        const uint32_t it = I->iter;
+        if (it < I->log_cap) I->log[it] = nn;
+        I->n_new = nn;
+        I->cand_total += I->n_cand;
+        I->n_full = nf;
+        I->f_off = dst_off;
+        if (fin) {
+          I->state = done ? INST_DONE : INST_ITERCAP;
+          I->iters_done = it;
+          I->res_pool = keep ? fph : (toR ? 2u : (fph ^ 1u));
+          I->res_off = dst_off;
+          I->n_delta = 0;
+        } else {
+          I->d_off = I->c_off;
+          I->n_delta = nn;
+          I->iter = it + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_f += tf; s_r += tr; s_t += tt; s_act += ta; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Stage m{};
+    m.in = dv->F[fph]; m.aux = dv->D[dph ^ 1]; m.out = dv->F[fph ^ 1]; m.out2 = dv->R;
+    m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
+    m.ntiles = (uint32_t)s_t; m.ctr = 0;
+    dv->st[S_MERGE] = m;
+    dv->r_used = s_r;
+    dv->fphase = fph ^ 1u;
+    dv->dphase = dph ^ 1u;
+    ctl.n_active = (uint32_t)s_act;
+    ctl.launch_iters += 1;
+    set_continue(dv, (s_act > 0 && ctl.launch_iters < ctl.iter_budget) ? 1u : 0u);
+  }
+}
+
+// Delta^{-1} of a fresh instance: the diagonal {(v, v)}.  Joining it with E
+// through the ordinary TC join yields E itself (the TC base rule); through the
+// SG base-rule join it yields the sibling pairs.
+template <typename K>
+__global__ void k_init_diag(Inst* inst, uint32_t first, uint32_t count, K* dpool) {
+  for (uint32_t q = first + blockIdx.x; q < first + count; q += gridDim.x) {
+    const Inst I = inst[q];
+    K* o = dpool + I.d_off;
+    for (uint32_t v = threadIdx.x; v < I.nv; v += blockDim.x) o[v] = ((K)v << I.w) | (K)v;
+  }
+}
+
+// ------------------------------------------------------------------ load / result
+template <typename K>
+__global__ void k_rank_edges(const uint32_t* src, const uint32_t* dst, unsigned long long n,
+                             const uint32_t* V, uint32_t nv, uint32_t w, K* keys) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t rs = (uint32_t)lower_bound_k(V, nv, src[i]);
+    const uint32_t rd = (uint32_t)lower_bound_k(V, nv, dst[i]);
+    keys[i] = ((K)rs << w) | (K)rd;
+  }
+}
+
+template <typename K>
+__global__ void k_csr(const K* E, unsigned long long ne, uint32_t nv, uint32_t w, uint32_t* off,
+                      uint32_t* adj) {
+  const K mask = (K)(((K)1 << w) - 1);
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long v = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; v <= nv;
+       v += stride)
+    off[v] = v == nv ? (uint32_t)ne : (uint32_t)lower_bound_k(E, ne, (K)((K)v << w));
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += stride)
+    adj[i] = (uint32_t)(E[i] & mask);
+}
+
+template <typename K>
+__global__ void k_result_map(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
+                             unsigned long long* out) {
+  const K mask = (K)(((K)1 << w) - 1);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const K k = F[i];
+    out[i] = ((unsigned long long)V[(uint32_t)(k >> w)] << 32) | V[(uint32_t)(k & mask)];
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename K>
+void launch_join_count(Stage* st, int grid, cudaStream_t s) { k_join_count<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+int occupancy_join(int which) {
+  int b = 0;
+  if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_join_count<K>, kThreads, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_join_emit<K>, kThreads, 0);
+  return b;
+}
+void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_plan_merge(Dev* dv, cudaStream_t s) { k_plan_merge<<<1, kPlanThreads, 0, s>>>(dv); }
+template <typename K>
+void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s) {
+  if (count) k_init_diag<K><<<count < 4096 ? count : 4096, 256, 0, s>>>(inst, first, count, (K*)dpool);
+}
+template <typename K>
+void launch_rank_edges(const uint32_t* src, const uint32_t* dst, unsigned long long n,
+                       const uint32_t* V, uint32_t nv, uint32_t w, K* keys, int grid,
+                       cudaStream_t s) {
+  k_rank_edges<K><<<grid, 256, 0, s>>>(src, dst, n, V, nv, w, keys);
+}
+template <typename K>
+void launch_csr(const K* E, unsigned long long ne, uint32_t nv, uint32_t w, uint32_t* off,
+                uint32_t* adj, int grid, cudaStream_t s) {
+  k_csr<K><<<grid, 256, 0, s>>>(E, ne, nv, w, off, adj);
+}
+template <typename K>
+void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
+                       unsigned long long* out, int grid, cudaStream_t s) {
+  k_result_map<K><<<grid, 256, 0, s>>>(F, n, w, V, out);
+}
+
+#define WG_INST(K)                                                                          \
+  template void launch_join_count<K>(Stage*, int, cudaStream_t);                            \
+  template void launch_join_emit<K>(Stage*, int, cudaStream_t);                             \
+  template int occupancy_join<K>(int);                                                      \
+  template void launch_init_diag<K>(Inst*, uint32_t, uint32_t, void*, cudaStream_t);        \
+  template void launch_rank_edges<K>(const uint32_t*, const uint32_t*, unsigned long long,  \
+                                     const uint32_t*, uint32_t, uint32_t, K*, int,          \
+                                     cudaStream_t);                                         \
+  template void launch_csr<K>(const K*, unsigned long long, uint32_t, uint32_t, uint32_t*,  \
+                              uint32_t*, int, cudaStream_t);                                \
+  template void launch_result_map<K>(const K*, unsigned long long, uint32_t, const uint32_t*, \
+                                     unsigned long long*, int, cudaStream_t);
+WG_INST(uint32_t)
+WG_INST(unsigned long long)
+#undef WG_INST
+
+}  // namespace wg

@@ -1,0 +1,405 @@
+// wg_kern_sort.cu -- sorted-array stages of one semi-naive iteration (sm_103a):
+//   * LSD radix sort of packed keys (Sec. Buffer Routing and Adaptive Radix Sort):
+//     one upfront histogram of every digit, then one pass per digit that ranks a
+//     tile in shared memory, finds its global offset by decoupled lookback and
+//     scatters through shared memory so that stores come out in digit runs;
+//   * fused deduplication + set difference against the full relation
+//     (Sec. Fused Deduplication and Set Difference): classify, block scan,
+//     decoupled lookback, ordered scatter -- one pass over the candidates;
+//   * disjoint merge of the new delta into the full relation (Sec. Disjoint
+//     Merge): merge-path partitions, |out| = |Full| + |Delta| exactly, no atomics.
+// All kernels are segmented (one segment per fixpoint instance) and indirect:
+// their work comes from a device-resident Stage record.
+#include "wg_device.cuh"
+#include "wg_launch.h"
+
+namespace wg {
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit(K k, uint32_t shift, uint32_t mask) {
+  return (uint32_t)(k >> shift) & mask;
+}
+
+// ------------------------------------------------------------------ histogram
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
+  __shared__ K sk[kTileC];
+  __shared__ uint32_t sh[kMaxPasses * kRadix];
+  __shared__ uint32_t s_t;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* in = (const K*)stp->in;
+  const uint32_t passes = stp->passes, dbits = stp->dbits, nseg = stp->nseg;
+  const uint32_t ntiles = stp->ntiles, mask = (1u << dbits) - 1u;
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+    const K* p = in + sg.in_off + start;
+    for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[i] = p[i];
+    __syncthreads();
+    // blocked order keeps equal neighbours together: count digit runs, one
+    // shared atomic per run (clustered high digits cost one atomic per run)
+    const uint32_t b = threadIdx.x * kItemsC;
+    for (uint32_t ps = 0; ps < passes; ++ps) {
+      const uint32_t shift = ps * dbits;
+      uint32_t prev = 0xFFFFFFFFu, run = 0;
+#pragma unroll
+      for (int i = 0; i < kItemsC; ++i) {
+        if (b + i < n) {
+          const uint32_t d = digit(sk[b + i], shift, mask);
+          if (d == prev) {
+            ++run;
+          } else {
+            if (run) atomicAdd(&sh[ps * kRadix + prev], run);
+            prev = d;
+            run = 1;
+          }
+        }
+      }
+      if (run) atomicAdd(&sh[ps * kRadix + prev], run);
+    }
+    __syncthreads();
+    unsigned long long* gh = stp->hist + (unsigned long long)k * passes * kRadix;
+    for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads)
+      if (sh[i]) atomicAdd(&gh[i], (unsigned long long)sh[i]);
+  }
+}
+
+// Exclusive scan of every (segment, pass) row of the digit histogram: the
+// global start of each digit bucket.  One warp per row.
+__global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
+  if (*(volatile uint32_t*)&stp->ctl->abort) return;
+  const uint32_t rows = stp->nseg * stp->passes;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t r = blockIdx.x * kWarps + (threadIdx.x >> 5); r < rows; r += gridDim.x * kWarps) {
+    unsigned long long* h = stp->hist + (unsigned long long)r * kRadix;
+    unsigned long long v[kRadix / 32], s = 0;
+#pragma unroll
+    for (int i = 0; i < kRadix / 32; ++i) { v[i] = h[lane * (kRadix / 32) + i]; s += v[i]; }
+    unsigned long long x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    unsigned long long run = x - s;
+#pragma unroll
+    for (int i = 0; i < kRadix / 32; ++i) { h[lane * (kRadix / 32) + i] = run; run += v[i]; }
+  }
+}
+
+// ------------------------------------------------------------------ one radix pass
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_sort_pass(Stage* stp) {
+  __shared__ K sk[kTileC];
+  __shared__ uint32_t whist[kWarps][kRadix];     // per-warp counts -> prefix over warps
+  __shared__ uint32_t tstart[kRadix];            // digit start inside the tile
+  __shared__ unsigned long long gdst[kRadix];    // global base of each digit minus tstart
+  __shared__ unsigned long long s_scan[kWarps];
+  __shared__ uint32_t s_t, s_bad;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* in = (const K*)stp->in;
+  K* out = (K*)stp->out;
+  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u;
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
+  const uint32_t pass = stp->pass, passes = stp->passes;
+  unsigned long long* status = stp->status;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+    const K* p = in + sg.in_off + start;
+    for (uint32_t i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&whist[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+
+    // warp-striped load: warp w owns keys [w*32*kItemsC, (w+1)*32*kItemsC)
+    K key[kItemsC];
+    uint32_t dig[kItemsC], rank[kItemsC];
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const uint32_t idx = warp * 32 * kItemsC + i * 32 + lane;
+      const bool ok = idx < n;
+      key[i] = ok ? p[idx] : (K)0;
+      dig[i] = ok ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
+    }
+    // stable rank within the warp: peers with the same digit, in (i, lane) order
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const uint32_t d = dig[i];
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = 0;
+      if (d != 0xFFFFFFFFu) before = whist[warp][d];
+      rank[i] = before + __popc(peers & lt_mask);
+      __syncwarp();
+      if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
+        whist[warp][d] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+
+    // thread d owns digit d: prefix over warps, tile count, publish aggregate
+    const uint32_t d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t c = whist[w][d];
+      whist[w][d] = cnt;
+      cnt += c;
+    }
+    const bool first = (t == sg.tile0);
+    unsigned long long* my = status + (unsigned long long)t * kRadix + d;
+    st_put(my, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, cnt));
+    unsigned long long tot;
+    const unsigned long long ts = block_excl_scan(cnt, s_scan, &tot);
+    tstart[d] = (uint32_t)ts;
+    // per-digit lookback over earlier tiles of this segment
+    unsigned long long excl = 0;
+    if (!first) {
+      long long j = (long long)t - 1;
+      for (;;) {
+        unsigned long long s = st_get(status + (unsigned long long)j * kRadix + d);
+        uint32_t spins = 0;
+        while (!st_ready(s, epoch)) {
+          if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) break;
+          __nanosleep(64);
+          s = st_get(status + (unsigned long long)j * kRadix + d);
+        }
+        if (!st_ready(s, epoch)) {
+          if (!*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
+          s_bad = 1;
+          break;
+        }
+        excl += s & kValMask;
+        if (((s >> 38) & 3u) == FLAG_INC || j == (long long)sg.tile0) break;
+        --j;
+      }
+      st_put(my, st_pack(epoch, FLAG_INC, excl + cnt));
+    }
+    const unsigned long long* hbase =
+        stp->hist + ((unsigned long long)k * passes + pass) * kRadix;
+    gdst[d] = sg.out_off + hbase[d] + excl - ts;
+    __syncthreads();
+    if (s_bad) return;  // a lookback gave up: the run is void, write nothing
+
+    // scatter into shared memory in digit order, then stream runs out
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (dig[i] != 0xFFFFFFFFu) sk[tstart[dig[i]] + whist[warp][dig[i]] + rank[i]] = key[i];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
+      const K v = sk[i];
+      out[gdst[digit(v, shift, mask)] + i] = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ dedup + diff
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
+  __shared__ K sk[kTileC];
+  __shared__ K sf[kFWin];
+  __shared__ unsigned long long s_scan[kWarps];
+  __shared__ unsigned long long s_lo, s_hi, s_excl;
+  __shared__ K s_prev;
+  __shared__ uint32_t s_t, s_bad;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* in = (const K*)stp->in;
+  const K* full = (const K*)stp->aux;
+  K* out = (K*)stp->out;
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
+  unsigned long long* status = stp->status;
+
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+    const K* p = in + sg.in_off + start;
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[i] = p[i];
+    if (threadIdx.x == 0 && start > 0) s_prev = p[-1];
+    __syncthreads();
+    const K* F = full + sg.aux_off;
+    const unsigned long long nf = sg.aux_n;
+    if (threadIdx.x == 0) s_lo = lower_bound_k(F, nf, sk[0]);
+    if (threadIdx.x == 32) s_hi = upper_bound_k(F, nf, sk[n - 1]);
+    __syncthreads();
+    const unsigned long long lo = s_lo, hi = s_hi;
+    const bool staged = hi - lo <= (unsigned long long)kFWin;
+    if (staged)
+      for (uint32_t i = threadIdx.x; i < hi - lo; i += kThreads) sf[i] = F[lo + i];
+    __syncthreads();
+
+    // classify a blocked run of keys: first copy and not in Full
+    const uint32_t b = threadIdx.x * kItemsC;
+    K key[kItemsC];
+    uint32_t keep = 0;
+    unsigned long long cur = staged ? 0 : lo;
+    const unsigned long long end = staged ? hi - lo : hi;
+    const K* S = staged ? sf : F;
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const uint32_t j = b + i;
+      key[i] = 0;
+      if (j < n) {
+        const K c = sk[j];
+        key[i] = c;
+        const bool firstc = j ? (c != sk[j - 1]) : (start == 0 || c != s_prev);
+        if (firstc) {
+          unsigned long long a = cur, z = end;  // lower bound of c in S[cur, end)
+          while (a < z) {
+            const unsigned long long m = (a + z) >> 1;
+            if (S[m] < c) a = m + 1; else z = m;
+          }
+          cur = a;
+          if (!(a < end && S[a] == c)) keep |= 1u << i;
+        }
+      }
+    }
+    unsigned long long tot;
+    const unsigned long long texcl = block_excl_scan((unsigned long long)__popc(keep), s_scan, &tot);
+    const bool first = (t == sg.tile0);
+    if (threadIdx.x == 0) {
+      s_bad = 0;
+      st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, tot));
+    }
+    if (!first && threadIdx.x < 32) {
+      const unsigned long long ex = lookback_scalar(status, t, sg.tile0, epoch, ctl);
+      if (threadIdx.x == 0) {
+        s_excl = ex;
+        if (*(volatile uint32_t*)&ctl->abort) s_bad = 1;
+        st_put(status + t, st_pack(epoch, FLAG_INC, ex + tot));
+      }
+    } else if (first && threadIdx.x == 0) {
+      s_excl = 0;
+    }
+    __syncthreads();  // every read of sk is done: compact in place
+    if (s_bad) return;
+    uint32_t w = (uint32_t)texcl;
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (keep >> i & 1u) sk[w++] = key[i];
+    __syncthreads();
+    const unsigned long long ex = s_excl;
+    K* o = out + sg.out_off + ex;
+    for (uint32_t i = threadIdx.x; i < tot; i += kThreads) o[i] = sk[i];
+    if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = ex + tot;
+  }
+}
+
+// ------------------------------------------------------------------ disjoint merge
+// Merge path (Green, McColl, Bader 2012): number of A-elements among the first
+// d outputs of merge(A, B) when A and B share no key.
+template <typename K>
+__device__ __forceinline__ unsigned long long merge_path(const K* A, unsigned long long na,
+                                                         const K* B, unsigned long long nb,
+                                                         unsigned long long d) {
+  unsigned long long lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const unsigned long long m = (lo + hi) >> 1;
+    if (A[m] < B[d - 1 - m]) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_merge(Stage* stp) {
+  __shared__ K sm[kTileM];
+  __shared__ unsigned long long s_a0, s_a1;
+  __shared__ uint32_t s_t;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* A_all = (const K*)stp->in;
+  const K* B_all = (const K*)stp->aux;
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles;
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const K* A = A_all + sg.in_off;
+    const K* B = B_all + sg.aux_off;
+    const unsigned long long na = sg.n, nb = sg.aux_n;
+    K* out = (K*)((sg.flags & 1u) ? stp->out2 : stp->out) + sg.out_off;
+    const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * kTileM;
+    const unsigned long long d1 = min(d0 + kTileM, na + nb);
+    if (threadIdx.x == 0) s_a0 = merge_path(A, na, B, nb, d0);
+    if (threadIdx.x == 32) s_a1 = merge_path(A, na, B, nb, d1);
+    __syncthreads();
+    const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
+    const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0);
+    if (lb == 0) {
+      for (uint32_t i = threadIdx.x; i < la; i += kThreads) out[d0 + i] = A[a0 + i];
+    } else if (la == 0) {
+      for (uint32_t i = threadIdx.x; i < lb; i += kThreads) out[d0 + i] = B[b0 + i];
+    } else {
+      for (uint32_t i = threadIdx.x; i < la; i += kThreads) sm[i] = A[a0 + i];
+      for (uint32_t i = threadIdx.x; i < lb; i += kThreads) sm[la + i] = B[b0 + i];
+      __syncthreads();
+      const K* SA = sm;
+      const K* SB = sm + la;
+      for (uint32_t q = threadIdx.x; q < la + lb; q += kThreads) {
+        uint32_t lo = q > lb ? q - lb : 0, hi = q < la ? q : la;
+        while (lo < hi) {
+          const uint32_t m = (lo + hi) >> 1;
+          if (SA[m] < SB[q - 1 - m]) lo = m + 1; else hi = m;
+        }
+        const uint32_t ib = q - lo;
+        const bool takeA = lo < la && (ib >= lb || SA[lo] < SB[ib]);
+        out[d0 + q] = takeA ? SA[lo] : SB[ib];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename K>
+void launch_sort_hist(Stage* st, int grid, cudaStream_t s) { k_sort_hist<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_sort_hscan(Stage* st, int grid, cudaStream_t s) { k_sort_hscan<<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_sort_pass(Stage* st, int grid, cudaStream_t s) { k_sort_pass<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
+
+template <typename K>
+int occupancy_sort(int which) {
+  int b = 0;
+  switch (which) {
+    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_hist<K>, kThreads, 0); break;
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_pass<K>, kThreads, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unique_diff<K>, kThreads, 0); break;
+    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_merge<K>, kThreads, 0); break;
+    default: break;
+  }
+  return b;
+}
+
+#define WG_INST(K)                                              \
+  template void launch_sort_hist<K>(Stage*, int, cudaStream_t);  \
+  template void launch_sort_pass<K>(Stage*, int, cudaStream_t);  \
+  template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
+  template void launch_merge<K>(Stage*, int, cudaStream_t);      \
+  template int occupancy_sort<K>(int);
+WG_INST(uint32_t)
+WG_INST(unsigned long long)
+#undef WG_INST
+
+}  // namespace wg

@@ -1,0 +1,43 @@
+// wg_launch.h -- host-side launchers of the sm_103a kernels (one translation
+// unit per kernel family; the host engine only sees these declarations).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wg {
+
+struct Stage;
+struct Dev;
+struct Inst;
+
+// sorted-array stages (wg_kern_sort.cu); K = uint32_t or unsigned long long
+template <typename K> void launch_sort_hist(Stage* st, int grid, cudaStream_t s);
+void launch_sort_hscan(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
+template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge
+
+// join and engine control (wg_kern_join.cu)
+template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
+template <typename K> int occupancy_join(int which);  // 0 count, 1 emit
+void launch_plan_delta(Dev* dv, cudaStream_t s);
+void launch_plan_cand(Dev* dv, cudaStream_t s);
+void launch_plan_merge(Dev* dv, cudaStream_t s);
+template <typename K>
+void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s);
+
+// relation load and result extraction
+template <typename K>
+void launch_rank_edges(const uint32_t* src, const uint32_t* dst, unsigned long long n,
+                       const uint32_t* V, uint32_t nv, uint32_t w, K* keys, int grid,
+                       cudaStream_t s);
+template <typename K>
+void launch_csr(const K* E, unsigned long long ne, uint32_t nv, uint32_t w, uint32_t* off,
+                uint32_t* adj, int grid, cudaStream_t s);
+template <typename K>
+void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
+                       unsigned long long* out, int grid, cudaStream_t s);
+
+}  // namespace wg

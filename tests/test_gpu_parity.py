@@ -1,0 +1,175 @@
+"""End-to-end parity: the CUDA fixpoint through the C-ABI against the CPU
+oracle, bit-exact (result keys, iteration count, per-iteration delta sizes).
+
+Covers the paper's worked example, closed forms, random graphs with
+duplicates / self-loops, the full uint32 id range, the empty relation, the
+iteration cap, both key widths (32-bit keys when 2 * field bits <= 32,
+64-bit otherwise), buffer regrowth, the host-driven loop, and profiling.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle_sg, oracle_tc
+from paper_2607_17571_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2607_17571_gb300 import wg
+    c = wg.Context(0)
+    yield c
+    c.close()
+
+
+def run(ctx, kind, src, dst, **opts):
+    rel = ctx.load(src, dst)
+    q = (ctx.tc if kind == "tc" else ctx.sg)(rel, **opts)
+    st = q.wait()
+    keys, log = q.result(), q.delta_sizes()
+    info = rel.info()
+    q.free()
+    rel.free()
+    return keys, st, log, info
+
+
+def check(ctx, kind, src, dst, **opts):
+    want = (oracle_tc if kind == "tc" else oracle_sg)(src, dst)
+    keys, st, log, info = run(ctx, kind, src, dst, **opts)
+    assert keys.shape == want.keys.shape
+    assert np.array_equal(keys, want.keys)
+    assert st.iterations == want.iters
+    assert log == want.log.tolist()
+    assert st.n_tuples == want.keys.shape[0]
+    return st, info
+
+
+def test_chain_worked_example(ctx):
+    st, _ = check(ctx, "tc", [0, 1, 2], [1, 2, 3])
+    assert st.iterations == 3 and st.n_tuples == 6
+
+
+@pytest.mark.parametrize("n", [2, 3, 17, 300])
+def test_path(ctx, n):
+    g = I.path(n)
+    check(ctx, "tc", g.src, g.dst)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 100])
+def test_cycle(ctx, n):
+    g = I.cycle(n)
+    check(ctx, "tc", g.src, g.dst)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 8])
+def test_binary_tree_sg(ctx, d):
+    g = I.binary_tree(d)
+    check(ctx, "sg", g.src, g.dst)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small_tc(ctx, seed):
+    n = [3, 7, 20, 64, 150, 400, 1000, 2500][seed]
+    g = I.random_small(n, int(1.5 * n) + 3, seed)
+    check(ctx, "tc", g.src, g.dst)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small_sg(ctx, seed):
+    n = [3, 7, 20, 64, 150, 400, 1000, 2500][seed]
+    g = I.random_small(n, n + 3, 50 + seed)
+    check(ctx, "sg", g.src, g.dst)
+
+
+def test_er_1k_workload(ctx):
+    g = I.workload("tc_er_1k")
+    st, info = check(ctx, "tc", g.src, g.dst)
+    assert st.regrows >= 1          # capacities started small: the loop resumed after growing
+    assert info["field_bits"] == 10
+
+
+def test_forest_sg_small(ctx):
+    g = I.sg_forest(5000, 6, 2.0, 0.01, seed=21)
+    check(ctx, "sg", g.src, g.dst)
+
+
+def test_full_id_range(ctx):
+    big = 0xFFFFFFFF
+    check(ctx, "tc", [0, big, 7, 7], [big, 7, 0, 7])
+    check(ctx, "sg", [big, big, 5, 6], [5, 6, 0, big - 1])
+
+
+def test_duplicates_and_self_loops(ctx):
+    check(ctx, "tc", [5, 5, 5, 7, 9, 9], [7, 7, 5, 9, 9, 5])
+    check(ctx, "sg", [1, 1, 1, 2, 2], [2, 3, 3, 4, 4])
+
+
+def test_empty(ctx):
+    for kind in ("tc", "sg"):
+        keys, st, log, _ = run(ctx, kind, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+        assert keys.shape[0] == 0 and st.iterations == 1 and log == [0, 0]
+
+
+def test_wide_keys_u64_path(ctx):
+    # > 65536 distinct vertices: 17-bit fields, 64-bit keys
+    i = np.arange(40000, dtype=np.uint32)
+    src = np.concatenate([2 * i, (2 * i[:500] + 1)])
+    dst = np.concatenate([2 * i + 1, 2 * i[1:501]])
+    st, info = check(ctx, "tc", src, dst)
+    assert info["field_bits"] == 17
+    t = I.sg_forest(70000, 20000, 2.0, 0.002, seed=4)
+    st, info = check(ctx, "sg", t.src, t.dst)
+    assert info["field_bits"] == 17
+
+
+def test_iteration_cap(ctx):
+    from paper_2607_17571_gb300 import wg
+    g = I.path(60)
+    rel = ctx.load(g.src, g.dst)
+    q = ctx.tc(rel, max_iters=10)
+    with pytest.raises(wg.WgError) as e:
+        q.wait()
+    assert e.value.code == wg.WG_E_ITER_CAP
+    st = q.poll()
+    assert st.state == wg.WG_FAILED and st.iterations == 10
+    want = oracle_tc(g.src, g.dst, max_iters=10)
+    assert q.delta_sizes() == want.log.tolist()
+    q.free()
+    rel.free()
+
+
+def test_host_loop_equals_device_loop(ctx):
+    from paper_2607_17571_gb300 import wg
+    g = I.er_graph(500, 1200, seed=8)
+    a = run(ctx, "tc", g.src, g.dst, loop=wg.WG_LOOP_DEVICE)
+    b = run(ctx, "tc", g.src, g.dst, loop=wg.WG_LOOP_HOST)
+    assert np.array_equal(a[0], b[0]) and a[2] == b[2]
+
+
+def test_profile_mode(ctx):
+    g = I.er_graph(800, 2000, seed=3)
+    want = oracle_tc(g.src, g.dst)
+    rel = ctx.load(g.src, g.dst)
+    q = ctx.tc(rel, profile=True)
+    q.wait()
+    assert np.array_equal(q.result(), want.keys)
+    prof = {p["name"]: p for p in q.profile()}
+    assert {"join_count", "join_emit", "sort_pass", "dedup_diff", "merge"} <= set(prof)
+    assert prof["merge"]["launches"] == want.iters + 1
+    assert all(p["total_ms"] > 0 for p in prof.values())
+    q.free()
+    rel.free()
+
+
+def test_repeat_is_deterministic_and_reuses_engine(ctx):
+    g = I.er_graph(700, 1600, seed=12)
+    rel = ctx.load(g.src, g.dst)
+    outs = []
+    for _ in range(3):
+        q = ctx.tc(rel)
+        q.wait()
+        outs.append(q.result())
+        q.free()
+    rel.free()
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
