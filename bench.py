@@ -1,0 +1,324 @@
+#!/usr/bin/env python3
+"""Benchmark of the semi-naive fixpoint on one or more GPUs.
+
+A step is one complete fixpoint (every iteration of join, radix sort, fused
+dedup + set difference and merge, with the loop on the device) of the
+workload over a relation already resident in device memory.  Default
+workload: transitive closure of an R-MAT(0.57, 0.19, 0.19, 0.05) graph with
+2^17 nodes and 400k distinct DAG edges (random relabel, src < dst kept), seed 2
+-- 478,120,144 closure tuples in 15 iterations.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload tc_rmat17_400k|sg_forest_60k|tc_er_1k]
+
+Multi-GPU (torchrun, one rank per GPU): the path is run as independent
+replicas (each rank computes the whole fixpoint; no collective on the data
+path); value = tuples of all ranks / max-over-ranks time ("weak" scaling).
+`--impl reference` times the CPU oracle (tests' semi-naive std::set
+evaluator, row by row over all host cores) on a bounded sample of sources.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fixpoint derived tuples/s"
+UNIT = "tuples/s"
+WORKLOADS = {
+    "tc_rmat17_400k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^17 nodes, 400k distinct "
+                                            "DAG edges (random relabel, src<dst), seed 2"),
+    "sg_forest_60k": dict(kind="sg", desc="SG, forest of 60k nodes (40 roots, Poisson(2) "
+                                          "branching) + 1% equal-depth cross edges, seed 3"),
+    "tc_er_1k": dict(kind="tc", desc="TC, directed Erdos-Renyi 1,000 nodes, 3,000 edges, seed 1"),
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def combine_ranks(values, reduce_op):
+    """All-reduce helper over torch.distributed (identity when world == 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return values
+    t = torch.tensor(values, dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=reduce_op)
+    return t.cpu().tolist()
+
+
+def aggregate(per_rank_tuples, per_rank_ms):
+    """Whole-job throughput: all tuples over the slowest rank's time."""
+    import torch.distributed as dist
+    tot = combine_ranks([float(per_rank_tuples)], dist.ReduceOp.SUM)[0]
+    mx = combine_ranks([float(per_rank_ms)], dist.ReduceOp.MAX)[0]
+    return tot, mx
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(g, kind, budget_s, seed=0, threads=None):
+    """The oracle as it stands on the host cores, on a bounded sample."""
+    import oracle
+    threads = threads or os.cpu_count()
+    rng = np.random.default_rng(seed)
+    if kind == "tc":
+        srcs = np.unique(g.src)
+        take = 64
+        done_tuples, done_s, n_src = 0, 0.0, 0
+        while done_s < budget_s and n_src < srcs.shape[0]:
+            sample = np.sort(rng.choice(srcs, size=min(take, srcs.shape[0]), replace=False))
+            t = time.perf_counter()
+            keys, _, _, _ = oracle.oracle_tc_rows(g.src, g.dst, sample, n_threads=threads)
+            done_s += time.perf_counter() - t
+            done_tuples += keys.shape[0]
+            n_src += sample.shape[0]
+            take = min(srcs.shape[0], take * 2)
+        return dict(value=done_tuples / done_s, unit=UNIT, cores=threads, kind="oracle",
+                    sample=f"rows T(x,.) of {n_src} random sources of {srcs.shape[0]} "
+                           f"({done_tuples} tuples, {done_s:.1f} s)")
+    # SG does not split by rows: run the whole oracle with a wall-clock budget note
+    t = time.perf_counter()
+    r = oracle.oracle_sg(g.src, g.dst)
+    dt = time.perf_counter() - t
+    return dict(value=r.keys.shape[0] / dt, unit=UNIT, cores=1, kind="oracle",
+                sample=f"whole fixpoint ({r.keys.shape[0]} tuples, {dt:.1f} s)")
+
+
+def run_reference(args):
+    from paper_2607_17571_gb300 import inputs as I
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = WORKLOADS[args.workload]
+    g = I.workload(args.workload)
+    threads = os.cpu_count()
+    vals = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(g, wl["kind"], args.ref_step_seconds, seed=k, threads=threads)
+        if k >= args.warmup:
+            vals.append(cb)
+    v = statistics.mean(c["value"] for c in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": dict(vals[-1], value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2607_17571_gb300 import inputs as I
+    from paper_2607_17571_gb300 import wg
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    g = I.workload(args.workload)
+    n = len(g)
+    ctx = wg.Context(local)
+    stream = ctx.torch_stream
+    src_t = torch.from_numpy(g.src.view(np.int32)).cuda(local)
+    dst_t = torch.from_numpy(g.dst.view(np.int32)).cuda(local)
+    torch.cuda.synchronize()
+    rel = ctx.load_device(src_t.data_ptr(), dst_t.data_ptr(), n)
+    info = rel.info()
+    run = ctx.tc if wl["kind"] == "tc" else ctx.sg
+    kb = 4 if 2 * info["field_bits"] <= 32 else 8
+
+    # warm-up: also sizes the pools (a relation remembers the capacities it needed)
+    st = None
+    for _ in range(args.warmup):
+        q = run(rel)
+        st = q.wait()
+        q.free()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")  # > L2 (129 MB)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ms, tuples, launches, iters, regrows = [], 0, 0, 0, 0
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)                     # evict L2 between steps (untimed)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q = run(rel)
+        st = q.wait()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        tuples += st.n_tuples
+        launches += st.gpu_launches
+        iters, regrows = st.iterations, regrows + st.regrows
+        q.free()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    all_tuples, max_ms = aggregate(tuples, total_ms)
+    value = all_tuples / (max_ms / 1e3)
+
+    # roofline: the same fixpoint once more with CUDA events around every kernel
+    q = run(rel, profile=True)
+    q.wait()
+    prof = q.profile()
+    q.free()
+    dom = max(prof, key=lambda p: p["total_ms"])
+    peak, peak_src = read_peaks()
+    per_launch_bytes = dom["bytes"] / dom["launches"]
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if os.path.exists(tfile):
+        for line in open(tfile):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == args.workload and parts[1] == dom["name"]:
+                traffic = float(parts[2])
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom["name"],
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+            else "fallback 6.8 TB/s",
+            "per_kernel": [{"name": p["name"], "launches": p["launches"],
+                            "ms": round(p["total_ms"], 3),
+                            "GBps": round(p["bytes"] / (p["total_ms"] / 1e3) / 1e9, 1),
+                            "share": round(p["total_ms"] / sum(x["total_ms"] for x in prof), 4)}
+                           for p in sorted(prof, key=lambda p: -p["total_ms"])]}
+
+    # end to end through the public C-ABI with host buffers: H2D of the edge
+    # list, the fixpoint, D2H of the sorted result
+    e2e_ms, h2d, d2h = [], 2 * 4 * n, 0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r2 = ctx.load(g.src, g.dst)
+        q = run(r2)
+        q.wait()
+        res = q.result()
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+        d2h = res.nbytes
+        q.free()
+        r2.free()
+        del res
+    e2e_tuples, e2e_max = aggregate(st.n_tuples, statistics.mean(e2e_ms))
+    e2e = {"value": e2e_tuples / (e2e_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_max, 2)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, wl["kind"], args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(max_ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32" if kb == 4 else "u64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": wl["desc"],
+                           "closure_tuples": int(st.n_tuples), "iterations": int(iters),
+                           "candidates": int(st.candidates), "edges": n,
+                           "vertices": info["n_vertices"], "field_bits": info["field_bits"],
+                           "l2": "flushed between steps (256 MB write); working set > L2",
+                           "parallelism": f"replicas x{world}", "regrows_timed": regrows},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line))
+    rel.free()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tc_rmat17_400k", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,71 @@
+"""Full-size parity, in the launch configuration bench.py times (device loop,
+default options), against the oracle results stored in
+tests/golden/workloads.json (written by tests/golden/make_golden.py, which
+calls only oracle/): exact closure size, iteration count, per-iteration delta
+sizes and SHA-256 of the sorted result.  The R-MAT closure is also compared
+row by row on sampled sources, with the oracle run live."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle_tc_rows
+from paper_2607_17571_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "workloads.json")))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2607_17571_gb300 import wg
+    c = wg.Context(0)
+    yield c
+    c.close()
+
+
+def _edges_digest(g):
+    return hashlib.sha256(g.src.astype("<u4").tobytes() + g.dst.astype("<u4").tobytes()).hexdigest()
+
+
+def _full_check(ctx, name, kind):
+    gold = GOLD[name]
+    g = I.workload(name)
+    assert _edges_digest(g) == gold["edges_sha256"], "generated inputs differ from the golden's"
+    rel = ctx.load(g.src, g.dst)
+    q = (ctx.tc if kind == "tc" else ctx.sg)(rel)
+    st = q.wait()
+    assert st.n_tuples == gold["n_tuples"]
+    assert st.iterations == gold["iterations"]
+    assert q.delta_sizes() == gold["delta_sizes"]
+    keys = q.result()
+    assert hashlib.sha256(keys.astype("<u8").tobytes()).hexdigest() == gold["keys_sha256"]
+    q.free()
+    rel.free()
+    return g, keys
+
+
+def test_er_1k_full(ctx):
+    _full_check(ctx, "tc_er_1k", "tc")
+
+
+def test_sg_forest_60k_full(ctx):
+    g, keys = _full_check(ctx, "sg_forest_60k", "sg")
+    # SG is symmetric: (x, y) in SG iff (y, x) in SG
+    sw = ((keys & np.uint64(0xFFFFFFFF)) << np.uint64(32)) | (keys >> np.uint64(32))
+    assert np.array_equal(np.sort(sw), keys)
+
+
+def test_rmat_tc_400k_full(ctx):
+    g, keys = _full_check(ctx, "tc_rmat17_400k", "tc")
+    rng = np.random.default_rng(7)
+    srcs = np.sort(rng.choice(np.unique(g.src), size=200, replace=False))
+    want, row_len, _, _ = oracle_tc_rows(g.src, g.dst, srcs, n_threads=os.cpu_count())
+    hi = keys >> np.uint64(32)
+    lo = np.searchsorted(hi, srcs.astype(np.uint64), side="left")
+    up = np.searchsorted(hi, srcs.astype(np.uint64), side="right")
+    got = np.concatenate([keys[a:b] for a, b in zip(lo, up)])
+    assert np.array_equal(got, want)
+    assert np.array_equal(up - lo, row_len.astype(np.int64))
