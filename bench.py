@@ -39,6 +39,8 @@ WORKLOADS = {
     "sg_forest_60k": dict(kind="sg", desc="SG, forest of 60k nodes (40 roots, Poisson(2) "
                                           "branching) + 1% equal-depth cross edges, seed 3"),
     "tc_er_1k": dict(kind="tc", desc="TC, directed Erdos-Renyi 1,000 nodes, 3,000 edges, seed 1"),
+    "tc_rmat15_100k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^15 nodes, 100k distinct "
+                                           "DAG edges, seed 2 (profiling-size case)"),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -124,17 +126,17 @@ def cpu_baseline(g, kind, budget_s, seed=0, threads=None):
     threads = threads or os.cpu_count()
     rng = np.random.default_rng(seed)
     if kind == "tc":
-        srcs = np.unique(g.src)
+        srcs = rng.permutation(np.unique(g.src))
         take = 64
         done_tuples, done_s, n_src = 0, 0.0, 0
         while done_s < budget_s and n_src < srcs.shape[0]:
-            sample = np.sort(rng.choice(srcs, size=min(take, srcs.shape[0]), replace=False))
+            sample = np.sort(srcs[n_src:n_src + take])
             t = time.perf_counter()
             keys, _, _, _ = oracle.oracle_tc_rows(g.src, g.dst, sample, n_threads=threads)
             done_s += time.perf_counter() - t
             done_tuples += keys.shape[0]
             n_src += sample.shape[0]
-            take = min(srcs.shape[0], take * 2)
+            take *= 2
         return dict(value=done_tuples / done_s, unit=UNIT, cores=threads, kind="oracle",
                     sample=f"rows T(x,.) of {n_src} random sources of {srcs.shape[0]} "
                            f"({done_tuples} tuples, {done_s:.1f} s)")
@@ -192,7 +194,11 @@ def run_ours(args):
     torch.cuda.synchronize()
     rel = ctx.load_device(src_t.data_ptr(), dst_t.data_ptr(), n)
     info = rel.info()
-    run = ctx.tc if wl["kind"] == "tc" else ctx.sg
+    run0 = ctx.tc if wl["kind"] == "tc" else ctx.sg
+    loop = wg.WG_LOOP_HOST if args.loop == "host" else wg.WG_LOOP_DEVICE
+
+    def run(r, **kw):
+        return run0(r, loop=loop, **kw)
     kb = 4 if 2 * info["field_bits"] <= 32 else 8
 
     # warm-up: also sizes the pools (a relation remembers the capacities it needed)
@@ -273,9 +279,11 @@ def run_ours(args):
         q.free()
         r2.free()
         del res
-    e2e_tuples, e2e_max = aggregate(st.n_tuples, statistics.mean(e2e_ms))
-    e2e = {"value": e2e_tuples / (e2e_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_max, 2)}
+    e2e = None
+    if e2e_ms:
+        e2e_tuples, e2e_max = aggregate(st.n_tuples, statistics.mean(e2e_ms))
+        e2e = {"value": e2e_tuples / (e2e_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_max, 2)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -314,6 +322,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--loop", default="device", choices=["device", "host"],
+                    help="host: one launch per kernel and a host sync per iteration (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -277,4 +277,6 @@ def workload(name: str) -> EdgeList:
         return rmat_dag(17, 400_000, seed=2)
     if name == "sg_forest_60k":
         return sg_forest(60_000, 40, 2.0, 0.01, seed=3)
+    if name == "tc_rmat15_100k":  # a smaller skewed case (profiling captures)
+        return rmat_dag(15, 100_000, seed=2)
     raise KeyError(name)
