@@ -68,11 +68,17 @@ enum wg_loop {
                          Motivation, "Stage-Wise Synchronization"), for comparison */
 };
 
+/* wg_opts.flags */
+#define WG_FLAG_SEPARATE_STAGES 1u /* run deduplication + set difference and the merge as the
+                                      paper's separate stages (Secs. Fused Deduplication and
+                                      Set Difference, Disjoint Merge) instead of one fused
+                                      merge-path pass that also writes the merged relation */
+
 typedef struct wg_opts {
   uint32_t max_iters;    /* iteration cap; 0 = 1<<20 */
   uint32_t loop;         /* enum wg_loop */
   uint32_t profile;      /* 1 = time every kernel with CUDA events (forces WG_LOOP_HOST) */
-  uint32_t reserved0;
+  uint32_t flags;        /* WG_FLAG_* */
   uint64_t reserve_full; /* initial capacity of the full relation, tuples; 0 = auto */
   uint64_t reserve_cand; /* initial capacity of the candidate buffers, tuples; 0 = auto */
 } wg_opts;

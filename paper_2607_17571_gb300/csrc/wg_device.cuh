@@ -54,6 +54,7 @@ struct Seg {
   unsigned long long out_off;          // output offset in the output pool
   unsigned long long aux_off, aux_n;   // auxiliary sorted range (full relation / delta)
   unsigned long long res;              // produced count (written by the stage)
+  unsigned long long out2_off;         // second output offset (fused diff-merge: Full')
   uint32_t tile0, ntiles;              // global tiles [tile0, tile0 + ntiles)
   uint32_t inst, flags;                // owning instance; flags & 1: output to out2
 };
@@ -94,8 +95,14 @@ struct Inst {
 };
 
 // Stage slots of an engine (one Stage record per kernel of the iteration).
-enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_HSCAN, S_UNIQ, S_MERGE, S_PASS0,
+enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_HSCAN, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
                      S_NUM = S_PASS0 + kMaxPasses };
+
+// Tile of the fused dedup + set difference + merge: 16 KB of keys.
+template <typename K> struct FuseTile {
+  static constexpr int T = sizeof(K) == 4 ? 4096 : 2048;
+  static constexpr int E = T / kThreads;
+};
 
 // Device-resident state of one engine: pools, the instance table, the stage
 // records the plan kernels write, and the graph conditional handle.  Pools are
@@ -108,7 +115,8 @@ struct Dev {
   Seg* segE;  // join emit
   Seg* segS;  // radix sort
   Seg* segU;  // dedup + diff
-  Seg* segM;  // merge
+  Seg* segM;  // merge (separate mode) / retire copy (fused mode)
+  Seg* segF;  // fused dedup + diff + merge
   void* D[2];  // delta / new-delta pools (swap every iteration)
   void* C[2];  // candidate pools (radix ping-pong)
   void* F[2];  // full relation pools (swap every iteration)
@@ -120,10 +128,15 @@ struct Dev {
   unsigned long long* hist;           // [n_inst][passes][kRadix]
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
-  uint32_t n_inst, single, use_cond;
+  uint32_t n_inst, single, use_cond, fuse, fuse_tile;
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
 };
+
+// Shared-memory index with one pad word per 32: threads that walk their own
+// contiguous run (blocked order, stride 16 words) then hit distinct banks.
+__device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
+template <int N> struct Padded { static constexpr int n = N + N / 32 + 1; };
 
 // ---------------------------------------------------------------- status words
 // [63:40] epoch (24 bits) | [39:38] flag | [37:0] value

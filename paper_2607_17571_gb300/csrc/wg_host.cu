@@ -343,6 +343,7 @@ struct EngineBase {
   virtual int kb() const = 0;
   virtual uint32_t bits() const = 0;
   virtual uint32_t slots() const = 0;
+  virtual bool fused() const = 0;
   virtual void release() = 0;
 };
 
@@ -375,7 +376,7 @@ struct Query {
 template <typename K>
 struct Engine : EngineBase {
   wg_ctx* c;
-  bool single;
+  bool single, fuse;
   uint32_t n_slots, bits_, passes, dbits;
   Dev* dv = nullptr;   // device block
   Dev h{};             // host mirror (read back after each run)
@@ -386,19 +387,20 @@ struct Engine : EngineBase {
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_uniq = 0, g_merge = 0;
+  int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_uniq = 0, g_merge = 0, g_fuse = 0;
   bool in_flight = false;
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
   int kernels_per_iter() const { return 9 + (int)passes; }
 
-  Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap)
-      : c(ctx), single(single_), n_slots(n), bits_(bits), log_cap(logcap) {
+  Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_)
+      : c(ctx), single(single_), fuse(fuse_), n_slots(n), bits_(bits), log_cap(logcap) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
   int kb() const override { return (int)sizeof(K); }
+  bool fused() const override { return fuse; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -416,7 +418,7 @@ struct Engine : EngineBase {
   int init() {
     TRY(b_dev.get(c, sizeof(Dev)));
     TRY(b_inst.get(c, sizeof(Inst) * n_slots));
-    TRY(b_seg.get(c, sizeof(Seg) * n_slots * 5));
+    TRY(b_seg.get(c, sizeof(Seg) * n_slots * 6));
     TRY(b_log.get(c, sizeof(unsigned long long) * (size_t)n_slots * log_cap));
     TRY(hist.get(c, sizeof(unsigned long long) * (size_t)n_slots * passes * kRadix));
     dv = (Dev*)b_dev.p;
@@ -426,7 +428,8 @@ struct Engine : EngineBase {
     h.inst = (Inst*)b_inst.p;
     Seg* s = (Seg*)b_seg.p;
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
-    h.segM = s + 4 * n_slots;
+    h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
+    h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
@@ -439,6 +442,7 @@ struct Engine : EngineBase {
     g_pass = grid_of(c, occupancy_sort<K>(1));
     g_uniq = grid_of(c, occupancy_sort<K>(2));
     g_merge = grid_of(c, occupancy_sort<K>(3));
+    g_fuse = grid_of(c, occupancy_sort<K>(4));
     return WG_OK;
   }
 
@@ -477,10 +481,7 @@ struct Engine : EngineBase {
         TRY(nc[i].get(c, wantC * sizeof(K)));
       }
       TRY(np.get(c, wantC * 8));
-      const size_t tiles = wantC / kTileD + n_slots + 2;
-      TRY(ns.get(c, tiles * 8));
       TRY(nk.get(c, (wantC / kTileC + n_slots + 2) * kRadix * 8));
-      CK(cudaMemsetAsync(ns.p, 0, ns.bytes, c->stream));
       CK(cudaMemsetAsync(nk.p, 0, nk.bytes, c->stream));
       if (liveD)
         CK(cudaMemcpyAsync(nd[h.dphase].p, D[h.dphase].p, liveD * sizeof(K),
@@ -489,10 +490,11 @@ struct Engine : EngineBase {
         D[i].release(c); C[i].release(c);
         D[i] = nd[i]; C[i] = nc[i];
       }
-      pos.release(c); st_s.release(c); st_k.release(c);
-      pos = np; st_s = ns; st_k = nk;
+      pos.release(c); st_k.release(c);
+      pos = np; st_k = nk;
       capC = wantC;
       h.ctl.epoch = 0;
+      if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
     }
     if (wantF > capF) {
       DBuf nf[2];
@@ -502,6 +504,16 @@ struct Engine : EngineBase {
                            cudaMemcpyDeviceToDevice, c->stream));
       for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
       capF = wantF;
+    }
+    {  // scalar lookback words: join-count tiles and fused / dedup tiles
+      const size_t tiles = std::max<size_t>(capC / kTileD, capF / FuseTile<K>::T) + n_slots + 2;
+      if (tiles * 8 > st_s.bytes) {
+        st_s.release(c);
+        TRY(st_s.get(c, tiles * 8));
+        CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+        h.ctl.epoch = 0;
+        CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+      }
     }
     if (!single && wantR > capR) {
       DBuf nr;
@@ -538,9 +550,15 @@ struct Engine : EngineBase {
     for (uint32_t p = 0; p < passes; ++p) {
       mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
     }
-    mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
-    launch_plan_merge(dv, s);
-    mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();
+    if (fuse) {
+      mark(); launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s); mark();
+      launch_plan_post(dv, s);
+      mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
+    } else {
+      mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
+      launch_plan_merge(dv, s);
+      mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();
+    }
   }
 
   int capture() {
@@ -674,14 +692,14 @@ struct Engine : EngineBase {
 };
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
-                              uint32_t logcap, int* rc) {
+                              uint32_t logcap, bool fuse, int* rc) {
   EngineBase* e;
   if (kb == 4) {
-    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap);
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse);
     *rc = x->init();
     e = x;
   } else {
-    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap);
+    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse);
     *rc = x->init();
     e = x;
   }
@@ -730,8 +748,13 @@ static int single_start(wg_ctx* c, Query* q) {
               {"join_emit", nd * (kb + 8) + nc * (kb + 4)},
               {"sort_hist", nc * kb}};
           for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
-          names.push_back({"dedup_diff", (nc + nn) * kb});
-          names.push_back({"merge", 2 * (nf + nn) * kb});
+          if (E->fuse) {
+            names.push_back({"dedup_diff_merge", (nc + 2 * nf + 2 * nn) * kb});
+            names.push_back({"retire_copy", 0.0});
+          } else {
+            names.push_back({"dedup_diff", (nc + nn) * kb});
+            names.push_back({"merge", 2 * (nf + nn) * kb});
+          }
           for (size_t i = 0; i < names.size(); ++i) {
             float ms = 0;
             cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
@@ -937,7 +960,7 @@ static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch)
 static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   if (c->batch[cls]) return WG_OK;
   int rc = WG_OK;
-  EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, &rc);
+  EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, true, &rc);
   if (!e) return rc;
   c->batch[cls].reset(e);
   g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
@@ -1110,16 +1133,17 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   TRY(make_query(c, kind, edges, opts, &q));
   Relation* R = q->rel;
   const uint32_t bits = 2 * R->w;
-  // reuse an idle engine of the same key width and pass plan
+  const bool fuse = !(q->opts.flags & WG_FLAG_SEPARATE_STAGES);
+  // reuse an idle engine of the same key width, pass plan and stage layout
   for (size_t i = 0; i < c->idle.size(); ++i)
-    if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits) {
+    if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
       break;
     }
   int rc = WG_OK;
   if (!q->own) {
-    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, &rc);
+    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, &rc);
     if (!e) { c->queries.erase(q->id); return rc; }
     q->own.reset(e);
   }

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     unsigned long long tot;
     const unsigned long long ex = scan1024(nt, sh, &tot);
     if (valid) {
-      Seg s;
+      Seg s{};
       s.in_off = I->d_off; s.n = nd; s.out_off = I->d_off; s.aux_off = 0; s.aux_n = 0; s.res = 0;
       s.tile0 = (uint32_t)(s_carry + ex); s.ntiles = (uint32_t)nt; s.inst = q; s.flags = 0;
       dv->segD[q] = s;
@@ -254,11 +254,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
   __shared__ unsigned long long sh[32];
-  __shared__ unsigned long long s_cc, s_ct;
+  __shared__ unsigned long long s_cc, s_ct, s_fc, s_ft;
   Ctl& ctl = dv->ctl;
   if (ctl.abort) return;
   const uint32_t N = dv->n_inst;
-  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; }
+  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; s_fc = 0; s_ft = 0; }
   __syncthreads();
   for (uint32_t base = 0; base < N; base += kPlanThreads) {
     const uint32_t q = base + threadIdx.x;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       const uint32_t tile0 = (uint32_t)(s_ct + ext);
       I->n_cand = nc;
       I->c_off = c_off;
-      Seg e;
+      Seg e{};
       e.in_off = I->d_off; e.n = act ? I->n_delta : 0ull; e.out_off = c_off;
       e.aux_off = 0; e.aux_n = nc; e.res = 0; e.tile0 = tile0; e.ntiles = (uint32_t)nt;
       e.inst = q; e.flags = 0;
@@ -287,13 +287,32 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       u.aux_off = I->f_off; u.aux_n = act ? I->n_full : 0ull;
       dv->segU[q] = u;
     }
+    if (dv->fuse) {
+      // fused dedup + diff + merge: Full' of q at an upper bound |Full| + |C|
+      const unsigned long long nf = act ? I->n_full : 0ull, tf = dv->fuse_tile;
+      const unsigned long long ft = (nf + nc + tf - 1) / tf;
+      unsigned long long totf, totft;
+      const unsigned long long exf = scan1024(nf + nc, sh, &totf);
+      const unsigned long long exft = scan1024(ft, sh, &totft);
+      if (valid) {
+        Seg f{};
+        f.in_off = I->f_off; f.n = nf; f.aux_off = s_cc + exc; f.aux_n = nc;
+        f.out_off = s_cc + exc; f.out2_off = s_fc + exf; f.res = 0;
+        f.tile0 = (uint32_t)(s_ft + exft); f.ntiles = (uint32_t)ft; f.inst = q; f.flags = 0;
+        dv->segF[q] = f;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) { s_fc += totf; s_ft += totft; }
+    }
     __syncthreads();
     if (threadIdx.x == 0) { s_cc += totc; s_ct += tott; }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    if (s_cc > dv->capC) {  // candidates do not fit: stop before anything is written
-      ctl.need_cand = s_cc;
+    if (s_cc > dv->capC || (dv->fuse && s_fc > dv->capF)) {
+      // candidates or Full' might not fit: stop before anything is written
+      if (s_cc > dv->capC) ctl.need_cand = s_cc;
+      if (dv->fuse && s_fc > dv->capF) ctl.need_full = s_fc;
       ctl.abort = 1;
       return;
     }
@@ -315,10 +334,19 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       s.status = dv->status_sort; s.shift = p * dv->dbits; s.pass = p; s.epoch = ++ctl.epoch;
       dv->st[S_PASS0 + p] = s;
     }
-    Stage u = base;
-    u.in = dv->C[dv->passes & 1]; u.aux = dv->F[dv->fphase]; u.out = dv->D[dv->dphase ^ 1];
-    u.segs = dv->segU; u.status = dv->status_scalar; u.epoch = ++ctl.epoch;
-    dv->st[S_UNIQ] = u;
+    if (dv->fuse) {
+      Stage f = base;
+      f.in = dv->F[dv->fphase]; f.aux = dv->C[dv->passes & 1];
+      f.out = dv->D[dv->dphase ^ 1]; f.out2 = dv->F[dv->fphase ^ 1];
+      f.segs = dv->segF; f.status = dv->status_scalar; f.epoch = ++ctl.epoch;
+      f.ntiles = (uint32_t)s_ft;
+      dv->st[S_FUSE] = f;
+    } else {
+      Stage u = base;
+      u.in = dv->C[dv->passes & 1]; u.aux = dv->F[dv->fphase]; u.out = dv->D[dv->dphase ^ 1];
+      u.segs = dv->segU; u.status = dv->status_scalar; u.epoch = ++ctl.epoch;
+      dv->st[S_UNIQ] = u;
+    }
   }
 }
 
@@ -406,7 +434,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_merge(Dev* dv) {
     const unsigned long long exa = scan1024((act && !fin) ? 1ull : 0ull, sh, &ta);
     (void)exa;
     if (valid) {
-      Seg m;
+      Seg m{};
       m.in_off = I->f_off; m.n = act ? I->n_full : 0ull; m.aux_off = I->c_off; m.aux_n = nn;
       m.res = 0; m.tile0 = (uint32_t)(s_t + ext); m.ntiles = (uint32_t)mt; m.inst = q;
       m.flags = toR ? 1u : 0u;
@@ -440,6 +468,114 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_merge(Dev* dv) {
   if (threadIdx.x == 0) {
     Stage m{};
     m.in = dv->F[fph]; m.aux = dv->D[dph ^ 1]; m.out = dv->F[fph ^ 1]; m.out2 = dv->R;
+    m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
+    m.ntiles = (uint32_t)s_t; m.ctr = 0;
+    dv->st[S_MERGE] = m;
+    dv->r_used = s_r;
+    dv->fphase = fph ^ 1u;
+    dv->dphase = dph ^ 1u;
+    ctl.n_active = (uint32_t)s_act;
+    ctl.launch_iters += 1;
+    set_continue(dv, (s_act > 0 && ctl.launch_iters < ctl.iter_budget) ? 1u : 0u);
+  }
+}
+
+// After the fused stage: commit the iteration (log, termination, new delta,
+// Full' as the full relation) and schedule the copy of finished batch
+// instances into the retire pool.
+__global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long s_r, s_t, s_act;
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort) {
+    if (threadIdx.x == 0) set_continue(dv, 0);
+    return;
+  }
+  const uint32_t N = dv->n_inst;
+  const bool single = dv->single != 0;
+  if (threadIdx.x == 0) s_r = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    unsigned long long rsz = 0;
+    if (q < N && !single) {
+      const Inst* I = dv->inst + q;
+      if (I->state == INST_ACTIVE) {
+        const unsigned long long nn = dv->segF[q].res;
+        const bool fin = (I->iter >= 1 && nn == 0) || I->iter >= I->max_iters;
+        if (fin) rsz = I->n_full + nn;
+      }
+    }
+    unsigned long long tr;
+    scan1024(rsz, sh, &tr);
+    if (threadIdx.x == 0) s_r += tr;
+    __syncthreads();
+  }
+  if (dv->r_used + s_r > dv->capR && !single) {
+    if (threadIdx.x == 0) {
+      ctl.need_res = dv->r_used + s_r;
+      ctl.abort = 1;
+      set_continue(dv, 0);
+    }
+    return;
+  }
+  const uint32_t fph = dv->fphase, dph = dv->dphase;
+  __syncthreads();
+  if (threadIdx.x == 0) { s_r = dv->r_used; s_t = 0; s_act = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < N; base += kPlanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    const bool valid = q < N;
+    Inst* I = valid ? dv->inst + q : nullptr;
+    const bool act = valid && I->state == INST_ACTIVE;
+    unsigned long long nn = 0, nf = 0, rsz = 0, mt = 0;
+    bool fin = false, done = false, toR = false;
+    if (act) {
+      nn = dv->segF[q].res;
+      nf = I->n_full + nn;
+      done = I->iter >= 1 && nn == 0;
+      fin = done || I->iter >= I->max_iters;
+      toR = fin && !single;
+      if (toR) { rsz = nf; mt = (nf + kTileM - 1) / kTileM; }
+    }
+    unsigned long long tr, tt, ta;
+    const unsigned long long exr = scan1024(rsz, sh, &tr);
+    const unsigned long long ext = scan1024(mt, sh, &tt);
+    scan1024((act && !fin) ? 1ull : 0ull, sh, &ta);
+    if (valid) {
+      const unsigned long long fo = dv->segF[q].out2_off;
+      Seg m{};
+      m.in_off = fo; m.n = rsz; m.aux_off = 0; m.aux_n = 0; m.res = 0; m.out2_off = 0;
+      m.out_off = s_r + exr; m.tile0 = (uint32_t)(s_t + ext); m.ntiles = (uint32_t)mt;
+      m.inst = q; m.flags = 1u;
+      dv->segM[q] = m;
+      if (act) {
+        const uint32_t it = I->iter;
+        if (it < I->log_cap) I->log[it] = nn;
+        I->n_new = nn;
+        I->cand_total += I->n_cand;
+        I->n_full = nf;
+        I->f_off = fo;
+        if (fin) {
+          I->state = done ? INST_DONE : INST_ITERCAP;
+          I->iters_done = it;
+          I->res_pool = toR ? 2u : (fph ^ 1u);
+          I->res_off = toR ? s_r + exr : fo;
+          I->n_delta = 0;
+        } else {
+          I->d_off = I->c_off;
+          I->n_delta = nn;
+          I->iter = it + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_r += tr; s_t += tt; s_act += ta; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    Stage m{};
+    m.in = dv->F[fph ^ 1]; m.aux = nullptr; m.out = dv->R; m.out2 = dv->R;
     m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
     m.ntiles = (uint32_t)s_t; m.ctr = 0;
     dv->st[S_MERGE] = m;
@@ -515,6 +651,7 @@ int occupancy_join(int which) {
 void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_merge(Dev* dv, cudaStream_t s) { k_plan_merge<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_plan_post(Dev* dv, cudaStream_t s) { k_plan_post<<<1, kPlanThreads, 0, s>>>(dv); }
 template <typename K>
 void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s) {
   if (count) k_init_diag<K><<<count < 4096 ? count : 4096, 256, 0, s>>>(inst, first, count, (K*)dpool);

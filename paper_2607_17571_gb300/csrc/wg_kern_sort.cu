@@ -23,7 +23,7 @@ __device__ __forceinline__ uint32_t digit(K k, uint32_t shift, uint32_t mask) {
 // ------------------------------------------------------------------ histogram
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
-  __shared__ K sk[kTileC];
+  __shared__ K sk[Padded<kTileC>::n];
   __shared__ uint32_t sh[kMaxPasses * kRadix];
   __shared__ uint32_t s_t;
   Ctl* ctl = stp->ctl;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
     const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
     const K* p = in + sg.in_off + start;
     for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[i] = p[i];
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[pad32(i)] = p[i];
     __syncthreads();
     // blocked order keeps equal neighbours together: count digit runs, one
     // shared atomic per run (clustered high digits cost one atomic per run)
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
 #pragma unroll
       for (int i = 0; i < kItemsC; ++i) {
         if (b + i < n) {
-          const uint32_t d = digit(sk[b + i], shift, mask);
+          const uint32_t d = digit(sk[pad32(b + i)], shift, mask);
           if (d == prev) {
             ++run;
           } else {
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
 
 // ------------------------------------------------------------------ one radix pass
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_sort_pass(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(Stage* stp) {
   __shared__ K sk[kTileC];
   __shared__ uint32_t whist[kWarps][kRadix];     // per-warp counts -> prefix over warps
   __shared__ uint32_t tstart[kRadix];            // digit start inside the tile
@@ -127,18 +127,17 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(Stage* stp) {
 
     // warp-striped load: warp w owns keys [w*32*kItemsC, (w+1)*32*kItemsC)
     K key[kItemsC];
-    uint32_t dig[kItemsC], rank[kItemsC];
+    uint32_t rank[kItemsC];
+    const uint32_t wbase = warp * 32 * kItemsC + lane;
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i) {
-      const uint32_t idx = warp * 32 * kItemsC + i * 32 + lane;
-      const bool ok = idx < n;
-      key[i] = ok ? p[idx] : (K)0;
-      dig[i] = ok ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
+      const uint32_t idx = wbase + i * 32;
+      key[i] = idx < n ? p[idx] : (K)0;
     }
     // stable rank within the warp: peers with the same digit, in (i, lane) order
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i) {
-      const uint32_t d = dig[i];
+      const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
       if (d != 0xFFFFFFFFu) before = whist[warp][d];
@@ -197,7 +196,10 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(Stage* stp) {
     // scatter into shared memory in digit order, then stream runs out
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i)
-      if (dig[i] != 0xFFFFFFFFu) sk[tstart[dig[i]] + whist[warp][dig[i]] + rank[i]] = key[i];
+      if (wbase + i * 32 < n) {
+        const uint32_t dg = digit(key[i], shift, mask);
+        sk[tstart[dg] + whist[warp][dg] + rank[i]] = key[i];
+      }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
       const K v = sk[i];
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_pass(Stage* stp) {
 // ------------------------------------------------------------------ dedup + diff
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
-  __shared__ K sk[kTileC];
+  __shared__ K sk[Padded<kTileC>::n];
   __shared__ K sf[kFWin];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_lo, s_hi, s_excl;
@@ -231,13 +233,13 @@ __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
     const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
     const K* p = in + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[i] = p[i];
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[pad32(i)] = p[i];
     if (threadIdx.x == 0 && start > 0) s_prev = p[-1];
     __syncthreads();
     const K* F = full + sg.aux_off;
     const unsigned long long nf = sg.aux_n;
     if (threadIdx.x == 0) s_lo = lower_bound_k(F, nf, sk[0]);
-    if (threadIdx.x == 32) s_hi = upper_bound_k(F, nf, sk[n - 1]);
+    if (threadIdx.x == 32) s_hi = upper_bound_k(F, nf, sk[pad32(n - 1)]);
     __syncthreads();
     const unsigned long long lo = s_lo, hi = s_hi;
     const bool staged = hi - lo <= (unsigned long long)kFWin;
@@ -257,9 +259,9 @@ __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
       const uint32_t j = b + i;
       key[i] = 0;
       if (j < n) {
-        const K c = sk[j];
+        const K c = sk[pad32(j)];
         key[i] = c;
-        const bool firstc = j ? (c != sk[j - 1]) : (start == 0 || c != s_prev);
+        const bool firstc = j ? (c != sk[pad32(j - 1)]) : (start == 0 || c != s_prev);
         if (firstc) {
           unsigned long long a = cur, z = end;  // lower bound of c in S[cur, end)
           while (a < z) {
@@ -293,11 +295,11 @@ __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
     uint32_t w = (uint32_t)texcl;
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i)
-      if (keep >> i & 1u) sk[w++] = key[i];
+      if (keep >> i & 1u) sk[pad32(w++)] = key[i];
     __syncthreads();
     const unsigned long long ex = s_excl;
     K* o = out + sg.out_off + ex;
-    for (uint32_t i = threadIdx.x; i < tot; i += kThreads) o[i] = sk[i];
+    for (uint32_t i = threadIdx.x; i < tot; i += kThreads) o[i] = sk[pad32(i)];
     if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = ex + tot;
   }
 }
@@ -368,6 +370,148 @@ __global__ void __launch_bounds__(kThreads) k_merge(Stage* stp) {
   }
 }
 
+// ------------------------------------------------------------------ fused dedup + diff + merge
+// One merge-path pass over (Full, sorted candidates C) per instance.  In the
+// merged order ties put the Full element first, so a candidate is new exactly
+// when it differs from the element just before it: that single predicate is
+// both filters of Sec. Fused Deduplication and Set Difference.  Every kept
+// element is also written, in merged order, as Full' = Full u N -- the
+// disjoint merge of Sec. Disjoint Merge in the same pass, so Full is streamed
+// once (no binary searches) and N is never read back.  Output positions: a
+// tile's N-prefix comes from a decoupled lookback; the Full' position of a
+// kept element is (Full elements before it) + (N elements before it).
+template <typename K>
+__device__ __forceinline__ unsigned long long mpath_tie(const K* A, unsigned long long na,
+                                                        const K* B, unsigned long long nb,
+                                                        unsigned long long d) {
+  // number of A elements among the first d of the merge (A first on ties)
+  unsigned long long lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const unsigned long long m = (lo + hi) >> 1;
+    if (A[m] <= B[d - 1 - m]) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
+  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
+  __shared__ K sin[Padded<T>::n];  // Full part then candidate part; then Full' outputs
+  __shared__ K sn[Padded<T>::n];   // N outputs
+  __shared__ unsigned long long s_scan[kWarps];
+  __shared__ unsigned long long s_a0, s_a1, s_excl;
+  __shared__ K s_prev;
+  __shared__ uint32_t s_hasprev, s_t, s_bad;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const K* Aall = (const K*)stp->in;     // Full
+  const K* Ball = (const K*)stp->aux;    // sorted candidates
+  K* Nall = (K*)stp->out;                // new delta
+  K* Fall = (K*)stp->out2;               // Full'
+  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
+  unsigned long long* status = stp->status;
+  for (;;) {
+    const uint32_t t = claim_tile(stp, &s_t);
+    if (t >= ntiles) return;
+    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg sg = stp->segs[k];
+    const K* A = Aall + sg.in_off;
+    const K* B = Ball + sg.aux_off;
+    const unsigned long long na = sg.n, nb = sg.aux_n;
+    const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * T;
+    const unsigned long long d1 = min(d0 + (unsigned long long)T, na + nb);
+    if (threadIdx.x == 0) { s_a0 = mpath_tie(A, na, B, nb, d0); s_bad = 0; }
+    if (threadIdx.x == 32) s_a1 = mpath_tie(A, na, B, nb, d1);
+    __syncthreads();
+    const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
+    const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
+    for (uint32_t i = threadIdx.x; i < la; i += kThreads) sin[pad32(i)] = A[a0 + i];
+    for (uint32_t i = threadIdx.x; i < lb; i += kThreads) sin[pad32(la + i)] = B[b0 + i];
+    if (threadIdx.x == 0) {
+      // the element just before this tile in merged order (its largest predecessor)
+      s_hasprev = d0 > 0;
+      K p = 0;
+      if (a0 > 0) p = A[a0 - 1];
+      if (b0 > 0 && B[b0 - 1] > p) p = B[b0 - 1];
+      s_prev = p;
+    }
+    __syncthreads();
+    // padded views of the Full part (SA) and the candidate part (SB)
+    auto SA = [&](uint32_t i) { return sin[pad32(i)]; };
+    auto SB = [&](uint32_t j) { return sin[pad32(la + j)]; };
+    // blocked: thread owns merged positions [q0, q0 + E)
+    const uint32_t q0 = threadIdx.x * E;
+    K val[E];
+    uint32_t isN = 0, kept = 0;   // bit i: output i is a new tuple / is kept
+    if (q0 < L) {
+      uint32_t i, j;
+      {  // merge path inside the tile (Full first on ties)
+        uint32_t lo = q0 > lb ? q0 - lb : 0, hi = q0 < la ? q0 : la;
+        while (lo < hi) {
+          const uint32_t m = (lo + hi) >> 1;
+          if (SA(m) <= SB(q0 - 1 - m)) lo = m + 1; else hi = m;
+        }
+        i = lo;
+        j = q0 - i;
+      }
+      bool has = q0 > 0 || s_hasprev;
+      K prev = q0 > 0 ? (i > 0 ? SA(i - 1) : (K)0) : s_prev;
+      if (q0 > 0 && j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        val[e] = 0;
+        if (q0 + e < L) {
+          const bool takeA = i < la && (j >= lb || SA(i) <= SB(j));
+          const K v = takeA ? SA(i) : SB(j);
+          if (takeA) {
+            ++i;
+            kept |= 1u << e;
+          } else {
+            ++j;
+            if (!has || v != prev) { kept |= 1u << e; isN |= 1u << e; }
+          }
+          val[e] = v;
+          prev = v;
+          has = true;
+        }
+      }
+    }
+    // one scan for both counts: N in the high half, kept in the low half
+    unsigned long long tot;
+    const unsigned long long both = ((unsigned long long)__popc(isN) << 32) | __popc(kept);
+    const unsigned long long ex = block_excl_scan(both, s_scan, &tot);
+    const unsigned long long totN = tot >> 32, totK = tot & 0xFFFFFFFFull;
+    const bool first = (t == sg.tile0);
+    if (threadIdx.x == 0)
+      st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, totN));
+    if (!first && threadIdx.x < 32) {
+      const unsigned long long e = lookback_scalar(status, t, sg.tile0, epoch, ctl);
+      if (threadIdx.x == 0) {
+        s_excl = e;
+        if (*(volatile uint32_t*)&ctl->abort) s_bad = 1;
+        st_put(status + t, st_pack(epoch, FLAG_INC, e + totN));
+      }
+    } else if (first && threadIdx.x == 0) {
+      s_excl = 0;
+    }
+    __syncthreads();  // all reads of sin are done
+    if (s_bad) return;
+    uint32_t wk = (uint32_t)(ex & 0xFFFFFFFFull), wn = (uint32_t)(ex >> 32);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (kept >> e & 1u) sin[pad32(wk++)] = val[e];
+      if (isN >> e & 1u) sn[pad32(wn++)] = val[e];
+    }
+    __syncthreads();
+    const unsigned long long exN = s_excl;
+    K* fo = Fall + sg.out2_off + a0 + exN;
+    for (uint32_t i = threadIdx.x; i < totK; i += kThreads) fo[i] = sin[pad32(i)];
+    K* no = Nall + sg.out_off + exN;
+    for (uint32_t i = threadIdx.x; i < totN; i += kThreads) no[i] = sn[pad32(i)];
+    if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = exN + totN;
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename K>
 void launch_sort_hist(Stage* st, int grid, cudaStream_t s) { k_sort_hist<K><<<grid, kThreads, 0, s>>>(st); }
@@ -378,6 +522,8 @@ template <typename K>
 void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_diff_merge(Stage* st, int grid, cudaStream_t s) { k_diff_merge<K><<<grid, kThreads, 0, s>>>(st); }
 
 template <typename K>
 int occupancy_sort(int which) {
@@ -387,6 +533,7 @@ int occupancy_sort(int which) {
     case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_pass<K>, kThreads, 0); break;
     case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unique_diff<K>, kThreads, 0); break;
     case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_merge<K>, kThreads, 0); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_diff_merge<K>, kThreads, 0); break;
     default: break;
   }
   return b;
@@ -397,6 +544,7 @@ int occupancy_sort(int which) {
   template void launch_sort_pass<K>(Stage*, int, cudaStream_t);  \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
+  template void launch_diff_merge<K>(Stage*, int, cudaStream_t); \
   template int occupancy_sort<K>(int);
 WG_INST(uint32_t)
 WG_INST(unsigned long long)

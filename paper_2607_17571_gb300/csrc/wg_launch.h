@@ -16,7 +16,8 @@ void launch_sort_hscan(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
-template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge
+template <typename K> void launch_diff_merge(Stage* st, int grid, cudaStream_t s);
+template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge, 4 fused
 
 // join and engine control (wg_kern_join.cu)
 template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
@@ -25,6 +26,7 @@ template <typename K> int occupancy_join(int which);  // 0 count, 1 emit
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);
+void launch_plan_post(Dev* dv, cudaStream_t s);
 template <typename K>
 void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s);
 

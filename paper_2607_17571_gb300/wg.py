@@ -22,6 +22,7 @@ WG_E_INVAL, WG_E_NOMEM, WG_E_BUDGET, WG_E_CAPACITY = -1, -2, -3, -4
 WG_E_NOT_READY, WG_E_ITER_CAP, WG_E_DEVICE_TIMEOUT, WG_E_CUDA = -5, -6, -7, -8
 WG_TC, WG_SG = 0, 1
 WG_LOOP_DEVICE, WG_LOOP_HOST = 0, 1
+WG_FLAG_SEPARATE_STAGES = 1
 WG_PENDING, WG_RUNNING, WG_DONE, WG_FAILED = 0, 1, 2, 3
 ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPACITY",
           -5: "WG_E_NOT_READY", -6: "WG_E_ITER_CAP", -7: "WG_E_DEVICE_TIMEOUT", -8: "WG_E_CUDA"}
@@ -29,7 +30,7 @@ ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPAC
 
 class wg_opts(Structure):
     _fields_ = [("max_iters", c_uint32), ("loop", c_uint32), ("profile", c_uint32),
-                ("reserved0", c_uint32), ("reserve_full", c_uint64), ("reserve_cand", c_uint64)]
+                ("flags", c_uint32), ("reserve_full", c_uint64), ("reserve_cand", c_uint64)]
 
 
 class wg_status(Structure):
@@ -111,8 +112,10 @@ def _check(rc, where):
         raise WgError(rc, where)
 
 
-def _opts(max_iters=0, loop=WG_LOOP_DEVICE, profile=False, reserve_full=0, reserve_cand=0):
-    return wg_opts(max_iters, loop, 1 if profile else 0, 0, reserve_full, reserve_cand)
+def _opts(max_iters=0, loop=WG_LOOP_DEVICE, profile=False, reserve_full=0, reserve_cand=0,
+          separate_stages=False):
+    return wg_opts(max_iters, loop, 1 if profile else 0,
+                   WG_FLAG_SEPARATE_STAGES if separate_stages else 0, reserve_full, reserve_cand)
 
 
 def _u32(a):

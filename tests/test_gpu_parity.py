@@ -68,23 +68,26 @@ def test_binary_tree_sg(ctx, d):
     check(ctx, "sg", g.src, g.dst)
 
 
+@pytest.mark.parametrize("separate", [False, True])
 @pytest.mark.parametrize("seed", range(8))
-def test_random_small_tc(ctx, seed):
+def test_random_small_tc(ctx, seed, separate):
     n = [3, 7, 20, 64, 150, 400, 1000, 2500][seed]
     g = I.random_small(n, int(1.5 * n) + 3, seed)
-    check(ctx, "tc", g.src, g.dst)
+    check(ctx, "tc", g.src, g.dst, separate_stages=separate)
 
 
+@pytest.mark.parametrize("separate", [False, True])
 @pytest.mark.parametrize("seed", range(8))
-def test_random_small_sg(ctx, seed):
+def test_random_small_sg(ctx, seed, separate):
     n = [3, 7, 20, 64, 150, 400, 1000, 2500][seed]
     g = I.random_small(n, n + 3, 50 + seed)
-    check(ctx, "sg", g.src, g.dst)
+    check(ctx, "sg", g.src, g.dst, separate_stages=separate)
 
 
-def test_er_1k_workload(ctx):
+@pytest.mark.parametrize("separate", [False, True])
+def test_er_1k_workload(ctx, separate):
     g = I.workload("tc_er_1k")
-    st, info = check(ctx, "tc", g.src, g.dst)
+    st, info = check(ctx, "tc", g.src, g.dst, separate_stages=separate)
     assert st.regrows >= 1          # capacities started small: the loop resumed after growing
     assert info["field_bits"] == 10
 
@@ -111,15 +114,16 @@ def test_empty(ctx):
         assert keys.shape[0] == 0 and st.iterations == 1 and log == [0, 0]
 
 
-def test_wide_keys_u64_path(ctx):
+@pytest.mark.parametrize("separate", [False, True])
+def test_wide_keys_u64_path(ctx, separate):
     # > 65536 distinct vertices: 17-bit fields, 64-bit keys
     i = np.arange(40000, dtype=np.uint32)
     src = np.concatenate([2 * i, (2 * i[:500] + 1)])
     dst = np.concatenate([2 * i + 1, 2 * i[1:501]])
-    st, info = check(ctx, "tc", src, dst)
+    st, info = check(ctx, "tc", src, dst, separate_stages=separate)
     assert info["field_bits"] == 17
     t = I.sg_forest(70000, 20000, 2.0, 0.002, seed=4)
-    st, info = check(ctx, "sg", t.src, t.dst)
+    st, info = check(ctx, "sg", t.src, t.dst, separate_stages=separate)
     assert info["field_bits"] == 17
 
 
@@ -155,8 +159,8 @@ def test_profile_mode(ctx):
     q.wait()
     assert np.array_equal(q.result(), want.keys)
     prof = {p["name"]: p for p in q.profile()}
-    assert {"join_count", "join_emit", "sort_pass", "dedup_diff", "merge"} <= set(prof)
-    assert prof["merge"]["launches"] == want.iters + 1
+    assert {"join_count", "join_emit", "sort_pass", "dedup_diff_merge"} <= set(prof)
+    assert prof["dedup_diff_merge"]["launches"] == want.iters + 1
     assert all(p["total_ms"] > 0 for p in prof.values())
     q.free()
     rel.free()
