@@ -71,6 +71,7 @@ struct Stage {
   unsigned long long* status;   // lookback words
   unsigned long long* hist;     // radix digit counts [nseg][passes][kRadix]
   unsigned long long* pos;      // join prefix sums (one per delta tuple)
+  unsigned long long* splits;   // per-tile start found by a partition kernel (or NULL)
   uint32_t nseg, ntiles;
   uint32_t ctr;                 // dynamic tile counter (zeroed by the writer)
   uint32_t epoch;
@@ -126,6 +127,7 @@ struct Dev {
   unsigned long long* status_scalar;  // lookback words of scalar scans
   unsigned long long* status_sort;    // lookback words of radix passes
   unsigned long long* hist;           // [n_inst][passes][kRadix]
+  unsigned long long* splits;         // tile partitions, as many entries as status_scalar
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;

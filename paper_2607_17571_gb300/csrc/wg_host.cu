@@ -382,7 +382,7 @@ struct Engine : EngineBase {
   Dev h{};             // host mirror (read back after each run)
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
-  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl;
   unsigned long long capC = 0, capF = 0, capR = 0;
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
@@ -392,7 +392,7 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 9 + (int)passes; }
+  int kernels_per_iter() const { return 11 + (int)passes; }
 
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_)
       : c(ctx), single(single_), fuse(fuse_), n_slots(n), bits_(bits), log_cap(logcap) {
@@ -411,7 +411,7 @@ struct Engine : EngineBase {
     if (ev_done) cudaEventDestroy(ev_done);
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
-                   &R, &pos, &st_s, &st_k, &hist};
+                   &R, &pos, &st_s, &st_k, &hist, &spl};
     for (DBuf* b : all) b->release(c);
   }
 
@@ -454,6 +454,7 @@ struct Engine : EngineBase {
     h.pos = (unsigned long long*)pos.p;
     h.status_scalar = (unsigned long long*)st_s.p;
     h.status_sort = (unsigned long long*)st_k.p;
+    h.splits = (unsigned long long*)spl.p;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, c->stream));
     return WG_OK;
@@ -475,7 +476,7 @@ struct Engine : EngineBase {
         }
     }
     if (wantC > capC) {
-      DBuf nd[2], nc[2], np, ns, nk;
+      DBuf nd[2], nc[2], np, nk;
       for (int i = 0; i < 2; ++i) {
         TRY(nd[i].get(c, wantC * sizeof(K)));
         TRY(nc[i].get(c, wantC * sizeof(K)));
@@ -509,7 +510,9 @@ struct Engine : EngineBase {
       const size_t tiles = std::max<size_t>(capC / kTileD, capF / FuseTile<K>::T) + n_slots + 2;
       if (tiles * 8 > st_s.bytes) {
         st_s.release(c);
+        spl.release(c);
         TRY(st_s.get(c, tiles * 8));
+        TRY(spl.get(c, (tiles + 1) * 8));
         CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
         h.ctl.epoch = 0;
         CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
@@ -544,6 +547,7 @@ struct Engine : EngineBase {
     launch_plan_delta(dv, s);
     mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s); mark();
     launch_plan_cand(dv, s);
+    launch_partition<K>(dv->st + S_EMIT, 1, kTileC, c->num_sms * 4, s);
     mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
     launch_sort_hscan(dv->st + S_HSCAN, c->num_sms, s);
@@ -551,12 +555,14 @@ struct Engine : EngineBase {
       mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
     }
     if (fuse) {
+      launch_partition<K>(dv->st + S_FUSE, 0, FuseTile<K>::T, c->num_sms * 4, s);
       mark(); launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s); mark();
       launch_plan_post(dv, s);
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
     } else {
       mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
       launch_plan_merge(dv, s);
+      launch_partition<K>(dv->st + S_MERGE, 0, kTileM, c->num_sms * 4, s);
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();
     }
   }

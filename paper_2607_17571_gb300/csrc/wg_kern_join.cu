@@ -161,8 +161,17 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
     const unsigned long long o1 = min(o0 + kTileC, sg.aux_n);
     // delta tuples whose slabs cover [o0, o1): the last tuple starting at or
     // before o0 through the last starting at or before o1 - 1
-    if (threadIdx.x == 0) s_i0 = upper_bound_k(P, sg.n, o0) - 1;
-    if (threadIdx.x == 32) s_i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
+    if (stp->splits) {
+      // the partition kernel found the slab owner of every tile start; the
+      // next tile's start bounds this tile's last owner (extra tuples past it
+      // start at or after o1 and are never chosen)
+      const bool last = t == sg.tile0 + sg.ntiles - 1;
+      if (threadIdx.x == 0) s_i0 = stp->splits[t];
+      if (threadIdx.x == 32) s_i1 = last ? sg.n - 1 : stp->splits[t + 1];
+    } else {
+      if (threadIdx.x == 0) s_i0 = upper_bound_k(P, sg.n, o0) - 1;
+      if (threadIdx.x == 32) s_i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
+    }
     __syncthreads();
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
     const bool staged = m <= (unsigned long long)kEmitWin;
@@ -322,7 +331,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     base.pos = dv->pos; base.nseg = N; base.ntiles = nt; base.ctr = 0;
     base.passes = dv->passes; base.dbits = dv->dbits;
     Stage e = base;
-    e.in = dv->D[dv->dphase]; e.out = dv->C[0]; e.segs = dv->segE;
+    e.in = dv->D[dv->dphase]; e.out = dv->C[0]; e.segs = dv->segE; e.splits = dv->splits;
     dv->st[S_EMIT] = e;
     Stage h = base;
     h.in = dv->C[0];
@@ -339,7 +348,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       f.in = dv->F[dv->fphase]; f.aux = dv->C[dv->passes & 1];
       f.out = dv->D[dv->dphase ^ 1]; f.out2 = dv->F[dv->fphase ^ 1];
       f.segs = dv->segF; f.status = dv->status_scalar; f.epoch = ++ctl.epoch;
-      f.ntiles = (uint32_t)s_ft;
+      f.ntiles = (uint32_t)s_ft; f.splits = dv->splits;
       dv->st[S_FUSE] = f;
     } else {
       Stage u = base;
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_merge(Dev* dv) {
   if (threadIdx.x == 0) {
     Stage m{};
     m.in = dv->F[fph]; m.aux = dv->D[dph ^ 1]; m.out = dv->F[fph ^ 1]; m.out2 = dv->R;
-    m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
+    m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N; m.splits = dv->splits;
     m.ntiles = (uint32_t)s_t; m.ctr = 0;
     dv->st[S_MERGE] = m;
     dv->r_used = s_r;

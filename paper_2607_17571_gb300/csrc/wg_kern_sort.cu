@@ -340,8 +340,14 @@ __global__ void __launch_bounds__(kThreads) k_merge(Stage* stp) {
     K* out = (K*)((sg.flags & 1u) ? stp->out2 : stp->out) + sg.out_off;
     const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * kTileM;
     const unsigned long long d1 = min(d0 + kTileM, na + nb);
-    if (threadIdx.x == 0) s_a0 = merge_path(A, na, B, nb, d0);
-    if (threadIdx.x == 32) s_a1 = merge_path(A, na, B, nb, d1);
+    const bool last = t == sg.tile0 + sg.ntiles - 1;
+    if (stp->splits) {
+      if (threadIdx.x == 0) s_a0 = stp->splits[t];
+      if (threadIdx.x == 32) s_a1 = last ? na : stp->splits[t + 1];
+    } else {
+      if (threadIdx.x == 0) s_a0 = merge_path(A, na, B, nb, d0);
+      if (threadIdx.x == 32) s_a1 = merge_path(A, na, B, nb, d1);
+    }
     __syncthreads();
     const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0);
@@ -420,8 +426,14 @@ __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
     const unsigned long long na = sg.n, nb = sg.aux_n;
     const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * T;
     const unsigned long long d1 = min(d0 + (unsigned long long)T, na + nb);
-    if (threadIdx.x == 0) { s_a0 = mpath_tie(A, na, B, nb, d0); s_bad = 0; }
-    if (threadIdx.x == 32) s_a1 = mpath_tie(A, na, B, nb, d1);
+    const bool last = t == sg.tile0 + sg.ntiles - 1;
+    if (stp->splits) {
+      if (threadIdx.x == 0) { s_a0 = stp->splits[t]; s_bad = 0; }
+      if (threadIdx.x == 32) s_a1 = last ? na : stp->splits[t + 1];
+    } else {
+      if (threadIdx.x == 0) { s_a0 = mpath_tie(A, na, B, nb, d0); s_bad = 0; }
+      if (threadIdx.x == 32) s_a1 = mpath_tie(A, na, B, nb, d1);
+    }
     __syncthreads();
     const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
@@ -512,6 +524,30 @@ __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
   }
 }
 
+// ------------------------------------------------------------------ tile partitions
+// One thread per tile of the consumer stage: the merge-path split at the
+// tile's first output (mode 0: merge of in/aux, Full first on ties) or the
+// delta tuple whose join slab holds the tile's first candidate (mode 1).  All
+// the binary searches are in flight at once instead of heading every tile.
+template <typename K>
+__global__ void k_partition(Stage* cons, int mode, uint32_t tile) {
+  if (*(volatile uint32_t*)&cons->ctl->abort) return;
+  const uint32_t ntiles = cons->ntiles, nseg = cons->nseg;
+  unsigned long long* splits = cons->splits;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+    const uint32_t k = find_seg(cons->segs, nseg, t);
+    const Seg& sg = cons->segs[k];
+    const unsigned long long d = (unsigned long long)(t - sg.tile0) * tile;
+    if (mode == 0) {
+      const K* A = (const K*)cons->in + sg.in_off;
+      const K* B = (const K*)cons->aux + sg.aux_off;
+      splits[t] = mpath_tie(A, sg.n, B, sg.aux_n, d);
+    } else {
+      splits[t] = upper_bound_k(cons->pos + sg.in_off, sg.n, d) - 1;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 template <typename K>
 void launch_sort_hist(Stage* st, int grid, cudaStream_t s) { k_sort_hist<K><<<grid, kThreads, 0, s>>>(st); }
@@ -524,6 +560,10 @@ template <typename K>
 void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_diff_merge(Stage* st, int grid, cudaStream_t s) { k_diff_merge<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s) {
+  k_partition<K><<<grid, 256, 0, s>>>(consumer, mode, tile);
+}
 
 template <typename K>
 int occupancy_sort(int which) {
@@ -545,6 +585,7 @@ int occupancy_sort(int which) {
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t); \
+  template void launch_partition<K>(Stage*, int, uint32_t, int, cudaStream_t); \
   template int occupancy_sort<K>(int);
 WG_INST(uint32_t)
 WG_INST(unsigned long long)

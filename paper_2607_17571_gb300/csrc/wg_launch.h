@@ -17,6 +17,10 @@ template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s)
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_diff_merge(Stage* st, int grid, cudaStream_t s);
+// mode 0: merge-path splits of a (Full, candidates) / (Full, delta) stage;
+// mode 1: join-slab owner of each emit tile.  `tile` = outputs per tile.
+template <typename K>
+void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s);
 template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge, 4 fused
 
 // join and engine control (wg_kern_join.cu)
