@@ -210,6 +210,31 @@ int wg_unique_diff(wg_ctx* ctx, const void* d_cand, size_t n, const void* d_full
 int wg_merge_disjoint(wg_ctx* ctx, const void* d_a, size_t na, const void* d_b, size_t nb,
                       void* d_out, int key_bytes);
 
+/* ---- allocation-free radix sort ------------------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory -- code running inside another runtime's
+ * memory arena, or a process that must not call cudaMalloc or any allocator
+ * (PyTorch's included), e.g. to keep its device footprint fixed.  It performs
+ * the same sort as wg_sort_keys (stable LSD radix sort of n keys on their low
+ * `bits` bits, in place; key_bytes = 4 or 8; higher bits must be zero) but takes
+ * no context and allocates nothing: its scratch (stage records, digit
+ * histograms, lookback words and the ping-pong key buffer, about 8.6 MB) is one
+ * fixed static device array that every GPU loading the library holds until the
+ * process exits.
+ *  - n <= WG_NOALLOC_MAX_KEYS (1,048,576); a larger n returns WG_E_CAPACITY and
+ *    touches nothing.
+ *  - Asynchronous on `cuda_stream` (a cudaStream_t; NULL = the legacy default
+ *    stream) of the current device; the caller synchronises.
+ *  - All calls share the scratch array, which keeps the previous call's
+ *    contents (each call clears what must start at zero): calls whose work
+ *    overlaps on the GPU race; keep them ordered, e.g. on one stream.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress): make that first call before any stream capture.
+ * Errors: WG_E_INVAL (NULL keys with n > 0, bad key_bytes or bits),
+ * WG_E_CAPACITY, WG_E_CUDA. */
+#define WG_NOALLOC_MAX_KEYS 1048576u
+int wg_sort_keys_noalloc(void* d_keys, size_t n, int key_bytes, uint32_t bits, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

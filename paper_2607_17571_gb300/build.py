@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libwg.so")
-SOURCES = ["wg_kern_sort.cu", "wg_kern_join.cu", "wg_host.cu"]
+SOURCES = ["wg_kern_sort.cu", "wg_kern_join.cu", "wg_host.cu", "wg_noalloc.cu"]
 HEADERS = ["wg_device.cuh", "wg_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]

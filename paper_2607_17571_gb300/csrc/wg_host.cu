@@ -44,6 +44,11 @@ int set_err(int code, const std::string& m) {
     if (r_ != WG_OK) return r_; \
   } while (0)
 
+}  // namespace
+
+int wg::set_error(int code, const char* msg) { return set_err(code, msg); }
+
+namespace {
 uint32_t bits_for(uint64_t nv) {  // bits to hold ranks 0..nv-1 (at least 1)
   uint32_t w = 1;
   while (w < 32 && (1ull << w) < nv) ++w;

@@ -6,6 +6,9 @@
 
 namespace wg {
 
+// Records `msg` as the calling thread's wg_last_error() and returns `code`.
+int set_error(int code, const char* msg);
+
 struct Stage;
 struct Dev;
 struct Inst;

@@ -79,7 +79,9 @@ SIGNATURES = {
                                POINTER(c_size_t), c_int]),
     "wg_merge_disjoint": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_size_t, c_void_p,
                                   c_int]),
+    "wg_sort_keys_noalloc": (c_int, [c_void_p, c_size_t, c_int, c_uint32, c_void_p]),
 }
+WG_NOALLOC_MAX_KEYS = 1 << 20
 
 _lib = None
 
@@ -120,6 +122,14 @@ def _opts(max_iters=0, loop=WG_LOOP_DEVICE, profile=False, reserve_full=0, reser
 
 def _u32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def sort_keys_noalloc(ptr: int, n: int, key_bytes: int, bits: int, stream_ptr=None):
+    """wg_sort_keys_noalloc: in-place sort with the library's static scratch
+    (no context, no allocation); asynchronous on the given stream."""
+    _check(load_library().wg_sort_keys_noalloc(c_void_p(ptr), n, key_bytes, bits,
+                                               c_void_p(stream_ptr) if stream_ptr else None),
+           "wg_sort_keys_noalloc")
 
 
 class Query:
