@@ -133,10 +133,20 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
 }
 
 // ------------------------------------------------------------------ join emit
+// Load-balanced over output positions: a tile is kTileC consecutive
+// candidates of one instance.  Thread t produces the kItemsC consecutive
+// candidates [t*kItemsC, (t+1)*kItemsC) of the tile: one binary search finds
+// the delta tuple (join slab) holding its first candidate, then it walks the
+// slabs sequentially, keeping the slab's CSR range in registers.  Candidates
+// go through shared memory so that the global stores are coalesced.
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
-  __shared__ unsigned long long spos[kEmitWin];
-  __shared__ K skey[kEmitWin];
+  constexpr int kStageBytes = kEmitWin * (8 + (int)sizeof(K));
+  constexpr int kOutBytes = kTileC * (int)sizeof(K) + (kTileC / 32 + 1) * (int)sizeof(K);
+  __shared__ __align__(16) unsigned char smem[kStageBytes > kOutBytes ? kStageBytes : kOutBytes];
+  unsigned long long* spos = (unsigned long long*)smem;
+  K* skey = (K*)(smem + kEmitWin * 8);
+  K* sout = (K*)smem;  // reused once every thread holds its candidates
   __shared__ unsigned long long s_i0, s_i1;
   __shared__ uint32_t s_t;
   Ctl* ctl = stp->ctl;
@@ -159,12 +169,11 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
     const K* Dq = D + sg.in_off;
     const unsigned long long o0 = (unsigned long long)(t - sg.tile0) * kTileC;
     const unsigned long long o1 = min(o0 + kTileC, sg.aux_n);
-    // delta tuples whose slabs cover [o0, o1): the last tuple starting at or
-    // before o0 through the last starting at or before o1 - 1
+    const uint32_t nout = (uint32_t)(o1 - o0);
+    // delta tuples whose slabs cover [o0, o1): from the slab owner of o0 to
+    // (at most) the slab owner of o1; tuples past the last owner start at or
+    // after o1 and are never chosen
     if (stp->splits) {
-      // the partition kernel found the slab owner of every tile start; the
-      // next tile's start bounds this tile's last owner (extra tuples past it
-      // start at or after o1 and are never chosen)
       const bool last = t == sg.tile0 + sg.ntiles - 1;
       if (threadIdx.x == 0) s_i0 = stp->splits[t];
       if (threadIdx.x == 32) s_i1 = last ? sg.n - 1 : stp->splits[t + 1];
@@ -182,44 +191,60 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
       }
     }
     __syncthreads();
-    K* Cq = C + sg.out_off;
-#pragma unroll 4
-    for (int j = 0; j < kItemsC; ++j) {
-      const unsigned long long o = o0 + (unsigned long long)j * kThreads + threadIdx.x;
-      if (o >= o1) break;
-      // largest i with pos[i] <= o
-      unsigned long long lo = 0, hi = m;
-      if (staged) {
-        while (hi - lo > 1) {
-          const unsigned long long mid = (lo + hi) >> 1;
-          if (spos[mid] <= o) lo = mid; else hi = mid;
-        }
-      } else {
-        while (hi - lo > 1) {
-          const unsigned long long mid = (lo + hi) >> 1;
-          if (P[i0 + mid] <= o) lo = mid; else hi = mid;
+    auto posat = [&](unsigned long long i) { return staged ? spos[i] : P[i0 + i]; };
+    auto keyat = [&](unsigned long long i) { return staged ? skey[i] : Dq[i0 + i]; };
+    K out[kItemsC];
+    const uint32_t q0 = threadIdx.x * kItemsC;
+    if (q0 < nout) {
+      const unsigned long long o = o0 + q0;
+      unsigned long long lo = 0, hi = m;  // largest i with pos[i] <= o
+      while (hi - lo > 1) {
+        const unsigned long long mid = (lo + hi) >> 1;
+        if (posat(mid) <= o) lo = mid; else hi = mid;
+      }
+      unsigned long long i = lo;
+      unsigned long long base = posat(i);
+      unsigned long long nextb = i + 1 < m ? posat(i + 1) : ~0ull;
+      K key = keyat(i);
+      uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
+      uint32_t ox = off[x], oy = off[y], dy = off[y + 1] - oy, dx = off[x + 1] - ox;
+#pragma unroll
+      for (int e = 0; e < kItemsC; ++e) {
+        out[e] = 0;
+        const unsigned long long oe = o + e;
+        if (q0 + e < nout) {
+          while (oe >= nextb) {  // next non-empty slab
+            ++i;
+            base = nextb;
+            nextb = i + 1 < m ? posat(i + 1) : ~0ull;
+            if (oe < nextb) {
+              key = keyat(i);
+              x = (uint32_t)(key >> w); y = (uint32_t)(key & mask);
+              ox = off[x]; oy = off[y]; dy = off[y + 1] - oy; dx = off[x + 1] - ox;
+            }
+          }
+          const uint32_t r = (uint32_t)(oe - base);
+          if (kind == KIND_TC) {
+            out[e] = ((K)x << w) | (K)adj[oy + r];                       // T(x,y), E(y,z)
+          } else if (iter == 0) {
+            const uint32_t dm1 = dx - 1;                                  // distinct children of x
+            const uint32_t qa = r / dm1;
+            uint32_t qb = r - qa * dm1;
+            qb += qb >= qa;
+            out[e] = ((K)adj[ox + qa] << w) | (K)adj[ox + qb];
+          } else {
+            const uint32_t qa = r / dy, qb = r - qa * dy;                  // E(a,x), sg(a,b), E(b,y)
+            out[e] = ((K)adj[ox + qa] << w) | (K)adj[oy + qb];
+          }
         }
       }
-      const unsigned long long r = o - (staged ? spos[lo] : P[i0 + lo]);
-      const K key = staged ? skey[lo] : Dq[i0 + lo];
-      const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
-      K outk;
-      if (kind == KIND_TC) {
-        outk = ((K)x << w) | (K)adj[off[y] + r];
-      } else if (iter == 0) {
-        const uint32_t dm1 = deg(off, x) - 1;  // ordered pairs of distinct children of x
-        const uint32_t qa = (uint32_t)(r / dm1);
-        uint32_t qb = (uint32_t)(r - (unsigned long long)qa * dm1);
-        qb += qb >= qa;
-        outk = ((K)adj[off[x] + qa] << w) | (K)adj[off[x] + qb];
-      } else {
-        const uint32_t db = deg(off, y);
-        const uint32_t qa = (uint32_t)(r / db);
-        const uint32_t qb = (uint32_t)(r - (unsigned long long)qa * db);
-        outk = ((K)adj[off[x] + qa] << w) | (K)adj[off[y] + qb];
-      }
-      Cq[o] = outk;
     }
+    __syncthreads();  // staging arrays are dead: reuse the space for the output
+#pragma unroll
+    for (int e = 0; e < kItemsC; ++e) sout[pad32(q0 + e)] = out[e];
+    __syncthreads();
+    K* Cq = C + sg.out_off + o0;
+    for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
   }
 }
 

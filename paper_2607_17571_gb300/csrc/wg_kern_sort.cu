@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
 
 // ------------------------------------------------------------------ one radix pass
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 3) k_sort_pass(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
   __shared__ K sk[kTileC];
   __shared__ uint32_t whist[kWarps][kRadix];     // per-warp counts -> prefix over warps
   __shared__ uint32_t tstart[kRadix];            // digit start inside the tile
@@ -403,7 +403,6 @@ template <typename K>
 __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
   constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
   __shared__ K sin[Padded<T>::n];  // Full part then candidate part; then Full' outputs
-  __shared__ K sn[Padded<T>::n];   // N outputs
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_a0, s_a1, s_excl;
   __shared__ K s_prev;
@@ -508,18 +507,18 @@ __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
     }
     __syncthreads();  // all reads of sin are done
     if (s_bad) return;
-    uint32_t wk = (uint32_t)(ex & 0xFFFFFFFFull), wn = (uint32_t)(ex >> 32);
+    const unsigned long long exN = s_excl;
+    uint32_t wk = (uint32_t)(ex & 0xFFFFFFFFull);
+    // new tuples are few: each thread stores its own run of them directly
+    K* no = Nall + sg.out_off + exN + (ex >> 32);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       if (kept >> e & 1u) sin[pad32(wk++)] = val[e];
-      if (isN >> e & 1u) sn[pad32(wn++)] = val[e];
+      if (isN >> e & 1u) *no++ = val[e];
     }
     __syncthreads();
-    const unsigned long long exN = s_excl;
     K* fo = Fall + sg.out2_off + a0 + exN;
     for (uint32_t i = threadIdx.x; i < totK; i += kThreads) fo[i] = sin[pad32(i)];
-    K* no = Nall + sg.out_off + exN;
-    for (uint32_t i = threadIdx.x; i < totN; i += kThreads) no[i] = sn[pad32(i)];
     if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = exN + totN;
   }
 }
