@@ -482,12 +482,19 @@ struct Engine : EngineBase {
     }
     if (wantC > capC) {
       DBuf nd[2], nc[2], np, nk;
-      for (int i = 0; i < 2; ++i) {
-        TRY(nd[i].get(c, wantC * sizeof(K)));
-        TRY(nc[i].get(c, wantC * sizeof(K)));
+      auto undo = [&](int rc) {
+        for (int i = 0; i < 2; ++i) { nd[i].release(c); nc[i].release(c); }
+        np.release(c); nk.release(c);
+        return rc;
+      };
+      int rc = WG_OK;
+      for (int i = 0; i < 2 && rc == WG_OK; ++i) {
+        rc = nd[i].get(c, wantC * sizeof(K));
+        if (rc == WG_OK) rc = nc[i].get(c, wantC * sizeof(K));
       }
-      TRY(np.get(c, wantC * 8));
-      TRY(nk.get(c, (wantC / kTileC + n_slots + 2) * kRadix * 8));
+      if (rc == WG_OK) rc = np.get(c, wantC * 8);
+      if (rc == WG_OK) rc = nk.get(c, (wantC / kTileC + n_slots + 2) * kRadix * 8);
+      if (rc != WG_OK) return undo(rc);
       CK(cudaMemsetAsync(nk.p, 0, nk.bytes, c->stream));
       if (liveD)
         CK(cudaMemcpyAsync(nd[h.dphase].p, D[h.dphase].p, liveD * sizeof(K),
@@ -504,7 +511,9 @@ struct Engine : EngineBase {
     }
     if (wantF > capF) {
       DBuf nf[2];
-      for (int i = 0; i < 2; ++i) TRY(nf[i].get(c, wantF * sizeof(K)));
+      int rc = nf[0].get(c, wantF * sizeof(K));
+      if (rc == WG_OK) rc = nf[1].get(c, wantF * sizeof(K));
+      if (rc != WG_OK) { nf[0].release(c); nf[1].release(c); return rc; }
       if (liveF)
         CK(cudaMemcpyAsync(nf[h.fphase].p, F[h.fphase].p, liveF * sizeof(K),
                            cudaMemcpyDeviceToDevice, c->stream));
@@ -525,7 +534,7 @@ struct Engine : EngineBase {
     }
     if (!single && wantR > capR) {
       DBuf nr;
-      TRY(nr.get(c, wantR * sizeof(K)));
+      TRY(nr.get(c, wantR * sizeof(K)));  // nothing else is held on this path
       if (keep && h.r_used)
         CK(cudaMemcpyAsync(nr.p, R.p, h.r_used * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
       R.release(c);
@@ -657,14 +666,27 @@ struct Engine : EngineBase {
     if (h.ctl.error) return set_err(WG_E_DEVICE_TIMEOUT, "a bounded device wait gave up");
     if (h.ctl.abort) {
       ++regrows;
-      const unsigned long long nc = h.ctl.need_cand ? h.ctl.need_cand + h.ctl.need_cand / 4 + 4096 : 0;
-      const unsigned long long nf = h.ctl.need_full ? h.ctl.need_full + h.ctl.need_full / 4 + 4096 : 0;
-      const unsigned long long nr = h.ctl.need_res ? h.ctl.need_res + h.ctl.need_res / 2 + 4096 : 0;
-      TRY(ensure(std::max(capC, nc), std::max(capF, nf), std::max(capR, nr), true));
       *again = true;
-      return WG_OK;
+      return grow();
     }
     *again = h.ctl.n_active > 0;
+    return WG_OK;
+  }
+
+  // Grow the pools to what the aborted run asked for (plus headroom).
+  int grow() {
+    const unsigned long long nc = h.ctl.need_cand ? h.ctl.need_cand + h.ctl.need_cand / 4 + 4096 : 0;
+    const unsigned long long nf = h.ctl.need_full ? h.ctl.need_full + h.ctl.need_full / 4 + 4096 : 0;
+    const unsigned long long nr = h.ctl.need_res ? h.ctl.need_res + h.ctl.need_res / 2 + 4096 : 0;
+    return ensure(std::max(capC, nc), std::max(capF, nf), std::max(capR, nr), true);
+  }
+  // Take instance `slot` out of the running set (its state is dropped).
+  int evict(uint32_t slot) {
+    Inst I = hi[slot];
+    I.state = INST_FREE;
+    I.n_delta = 0; I.n_full = 0;
+    hi[slot] = I;
+    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
     return WG_OK;
   }
 
@@ -853,37 +875,54 @@ static int single_progress(wg_ctx* c, Query* q, bool block) {
 // with fields <= 24 bits, 64-bit keys with fields <= 32 bits.
 static int batch_class(const Relation* R) { return R->kb == 4 ? 0 : (R->w <= 24 ? 1 : 2); }
 static uint32_t class_bits(int cls) { return cls == 0 ? 32 : (cls == 1 ? 48 : 64); }
-constexpr uint32_t kBatchSlots = 8192;
-constexpr uint32_t kBatchLogCap = 4096;
+constexpr uint32_t kBatchSlots = 1024;    // queries running at once per key class
+constexpr uint32_t kBatchLogCap = 1024;   // per-iteration delta sizes kept per query
 
 struct BatchInfo {
   std::vector<uint64_t> slot_q;  // query id per slot (0 = free)
+  std::vector<double> est;       // admission estimate of the slot's final size
 };
 static std::map<wg_ctx*, std::map<int, BatchInfo>> g_binfo;
+
+// Admission estimate of a query's final relation: at most nv^2 tuples, capped
+// so that a single large query is still admitted into an idle engine.
+static double admit_estimate(const Relation* R, unsigned long long capF) {
+  return std::min((double)R->nv * (double)R->nv, (double)capF / 4.0);
+}
 
 template <typename K>
 static int batch_admit(wg_ctx* c, int cls) {
   auto& B = g_binfo[c][cls];
   auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
-  // live delta region and free slots
   unsigned long long dend = 0;
-  for (const Inst& I : E->hi)
-    if (I.state == INST_ACTIVE) dend = std::max<unsigned long long>(dend, I.d_off + I.n_delta);
-  uint32_t first = 0xFFFFFFFFu, last = 0;
+  double load = 0;
+  uint32_t active = 0;
+  for (uint32_t s = 0; s < E->n_slots; ++s)
+    if (E->hi[s].state == INST_ACTIVE) {
+      dend = std::max<unsigned long long>(dend, E->hi[s].d_off + E->hi[s].n_delta);
+      load += B.est[s];
+      ++active;
+    }
+  uint32_t first = 0xFFFFFFFFu, last = 0, next_free = 0;
   std::vector<uint64_t> still;
   for (uint64_t qid : c->pending) {
     auto it = c->queries.find(qid);
     if (it == c->queries.end()) continue;
     Query* q = it->second.get();
     if (q->bclass != cls) { still.push_back(qid); continue; }
-    uint32_t slot = 0xFFFFFFFFu;
-    for (uint32_t s = 0; s < E->n_slots; ++s)
-      if (B.slot_q[s] == 0 && (E->hi[s].state != INST_ACTIVE)) { slot = s; break; }
-    // admission by memory: the fresh delta must fit in the candidate pools
-    if (slot == 0xFFFFFFFFu || dend + q->rel->nv > E->capC) { still.push_back(qid); continue; }
+    while (next_free < E->n_slots &&
+           (B.slot_q[next_free] != 0 || E->hi[next_free].state == INST_ACTIVE))
+      ++next_free;
+    const double est = admit_estimate(q->rel, E->capF);
+    const bool fits = dend + q->rel->nv <= E->capC && (active == 0 || load + est <= (double)E->capF);
+    if (next_free >= E->n_slots || !fits) { still.push_back(qid); continue; }
+    const uint32_t slot = next_free;
     TRY(E->admit(slot, q->rel, q->kind, q->opts.max_iters, dend));
     dend += q->rel->nv;
+    load += est;
+    ++active;
     B.slot_q[slot] = qid;
+    B.est[slot] = est;
     q->slot = slot;
     q->state = WG_RUNNING;
     first = std::min(first, slot);
@@ -891,6 +930,41 @@ static int batch_admit(wg_ctx* c, int cls) {
   }
   c->pending.swap(still);
   if (first != 0xFFFFFFFFu) TRY(E->init_deltas(first, last - first + 1));
+  return WG_OK;
+}
+
+// The pools cannot grow within the budget: requeue the largest running
+// instance (it restarts later from its base rule).  A query that does not fit
+// even alone fails with WG_E_BUDGET.
+template <typename K>
+static int batch_preempt(wg_ctx* c, int cls, int why) {
+  auto& B = g_binfo[c][cls];
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  uint32_t victim = 0xFFFFFFFFu, active = 0;
+  unsigned long long big = 0;
+  for (uint32_t s = 0; s < E->n_slots; ++s) {
+    const Inst& I = E->hi[s];
+    if (I.state != INST_ACTIVE) continue;
+    ++active;
+    const unsigned long long sz = I.n_full + I.n_cand + I.n_delta;
+    if (victim == 0xFFFFFFFFu || sz > big) { big = sz; victim = s; }
+  }
+  if (victim == 0xFFFFFFFFu) return set_err(why, "batch pools cannot grow");
+  const uint64_t qid = B.slot_q[victim];
+  B.slot_q[victim] = 0;
+  TRY(E->evict(victim));
+  auto it = c->queries.find(qid);
+  if (it == c->queries.end()) return WG_OK;
+  Query* q = it->second.get();
+  if (active == 1) {  // alone and still too large
+    q->state = WG_FAILED;
+    q->error = why;
+    q->t_done_us = now_us();
+    return WG_OK;
+  }
+  q->state = WG_PENDING;
+  q->regrows += 1;
+  c->pending.insert(c->pending.begin(), qid);
   return WG_OK;
 }
 
@@ -904,25 +978,29 @@ static int batch_retire(wg_ctx* c, int cls) {
     if (I.state != INST_DONE && I.state != INST_ITERCAP) continue;
     auto it = c->queries.find(B.slot_q[s]);
     B.slot_q[s] = 0;
-    Inst cleared = I;
-    cleared.state = INST_FREE;
-    E->hi[s] = cleared;
-    CK(cudaMemcpyAsync((Inst*)E->b_inst.p + s, &cleared, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    Inst done = I;
+    TRY(E->evict(s));
     if (it == c->queries.end()) continue;  // freed while running
     Query* q = it->second.get();
-    q->n_tuples = I.n_full;
-    q->iterations = I.iters_done;
-    q->candidates = I.cand_total;
-    const uint32_t nlog = std::min<uint32_t>(I.iters_done + 1, E->log_cap);
+    q->n_tuples = done.n_full;
+    q->iterations = done.iters_done;
+    q->candidates = done.cand_total;
+    const uint32_t nlog = std::min<uint32_t>(done.iters_done + 1, E->log_cap);
     q->log.assign(nlog, 0);
-    CK(cudaMemcpyAsync(q->log.data(), I.log, nlog * 8, cudaMemcpyDeviceToHost, c->stream));
-    TRY(q->res_own.get(c, std::max<size_t>(I.n_full, 1) * sizeof(K)));
-    if (I.n_full)
-      CK(cudaMemcpyAsync(q->res_own.p, (const K*)E->pool_ptr(I.res_pool) + I.res_off,
-                         I.n_full * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(q->log.data(), done.log, nlog * 8, cudaMemcpyDeviceToHost, c->stream));
+    int rc = q->res_own.get(c, std::max<size_t>(done.n_full, 1) * sizeof(K));
+    if (rc != WG_OK) {
+      q->state = WG_FAILED;
+      q->error = rc;
+      q->t_done_us = now_us();
+      continue;
+    }
+    if (done.n_full)
+      CK(cudaMemcpyAsync(q->res_own.p, (const K*)E->pool_ptr(done.res_pool) + done.res_off,
+                         done.n_full * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
     q->res_ptr = q->res_own.p;
-    q->state = I.state == INST_DONE ? WG_DONE : WG_FAILED;
-    q->error = I.state == INST_DONE ? WG_OK : WG_E_ITER_CAP;
+    q->state = done.state == INST_DONE ? WG_DONE : WG_FAILED;
+    q->error = done.state == INST_DONE ? WG_OK : WG_E_ITER_CAP;
     q->t_done_us = now_us();
   }
   // every retired result has been copied out: the retire pool starts over
@@ -933,6 +1011,21 @@ static int batch_retire(wg_ctx* c, int cls) {
 }
 
 template <typename K>
+static void batch_fail_all(wg_ctx* c, int cls, int rc) {
+  auto& B = g_binfo[c][cls];
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  for (uint32_t s = 0; s < E->n_slots; ++s)
+    if (B.slot_q[s]) {
+      auto it = c->queries.find(B.slot_q[s]);
+      if (it != c->queries.end()) { it->second->state = WG_FAILED; it->second->error = rc; }
+      B.slot_q[s] = 0;
+      E->evict(s);
+    }
+}
+
+// One scheduling round: finish the launch in flight (grow or preempt after an
+// overflow, retire finished queries), admit queued queries, launch again.
+template <typename K>
 static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
   auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
   if (E->in_flight) {
@@ -941,17 +1034,25 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
       if (e == cudaErrorNotReady) return WG_OK;
     }
     CK(cudaEventSynchronize(E->ev_done));
-    bool again = false;
-    int rc = E->settle(&again);
-    if (rc != WG_OK) {
-      auto& B = g_binfo[c][cls];
-      for (uint32_t s = 0; s < E->n_slots; ++s)
-        if (B.slot_q[s]) {
-          auto it = c->queries.find(B.slot_q[s]);
-          if (it != c->queries.end()) { it->second->state = WG_FAILED; it->second->error = rc; }
-          B.slot_q[s] = 0;
-        }
-      return rc;
+    E->in_flight = false;
+    TRY(E->read_back());
+    if (E->exec && E->h.use_cond)
+      E->launches_issued += (uint64_t)(E->h.ctl.launch_iters + (E->h.ctl.abort ? 1u : 0u)) *
+                            E->kernels_per_iter();
+    if (E->h.ctl.error) {
+      batch_fail_all<K>(c, cls, WG_E_DEVICE_TIMEOUT);
+      return set_err(WG_E_DEVICE_TIMEOUT, "a bounded device wait gave up");
+    }
+    if (E->h.ctl.abort) {
+      ++E->regrows;
+      const int rc = E->grow();
+      if (rc == WG_E_BUDGET || rc == WG_E_NOMEM) {
+        cudaGetLastError();
+        TRY(batch_preempt<K>(c, cls, rc));
+      } else if (rc != WG_OK) {
+        batch_fail_all<K>(c, cls, rc);
+        return rc;
+      }
     }
     TRY(batch_retire<K>(c, cls));
   }
@@ -975,11 +1076,15 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   if (!e) return rc;
   c->batch[cls].reset(e);
   g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
-  const unsigned long long budget_keys = (unsigned long long)((c->budget - c->used) / 4 / R->kb / 8);
-  const unsigned long long capC = std::max<unsigned long long>(1ull << 22, budget_keys);
+  g_binfo[c][cls].est.assign(kBatchSlots, 0.0);
+  // start with pools worth about a third of the free budget; they grow later
+  // only as far as the budget allows (then the largest instance is preempted)
+  const double per_key = 4.0 * R->kb + 8.5 + 2.0 * R->kb + R->kb / 4.0;
+  const double avail = (double)(c->budget - c->used) / 3.0;
+  const unsigned long long capC = std::max<unsigned long long>(1ull << 20, (unsigned long long)(avail / per_key));
   if (R->kb == 4)
-    return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 2, false);
-  return static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 2, false);
+    return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 4, false);
+  return static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 4, false);
 }
 
 template <typename K>

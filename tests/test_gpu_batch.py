@@ -1,0 +1,137 @@
+"""Batched and served fixpoints (wg_submit / wg_serve_step / wg_wait).
+
+Every query's result must be byte-identical whether it runs alone (wg_tc /
+wg_sg) or inside a mix of concurrent queries, and equal to the oracle;
+queries submitted while others run join at the next iteration boundary;
+when the pools cannot grow inside the memory budget the largest running
+query is requeued and still finishes with the same result; a query that does
+not fit even alone fails with WG_E_BUDGET.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle_sg, oracle_tc
+from paper_2607_17571_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(seed, n_q=36):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_q):
+        r = rng.random()
+        if r < 0.55:
+            n = int(np.exp(rng.uniform(np.log(16), np.log(900))))
+            g = I.er_graph(n, int(n * rng.uniform(1.2, 2.5)), seed * 1000 + i)
+            out.append(("tc", g))
+        elif r < 0.8:
+            g = I.sg_forest(int(rng.integers(50, 2500)), int(rng.integers(2, 9)), 2.0, 0.01,
+                            seed * 1000 + i)
+            out.append(("sg", g))
+        else:
+            g = I.rmat_dag(int(rng.integers(8, 12)), int(rng.integers(200, 3000)), seed * 1000 + i)
+            out.append(("tc", g))
+    return out
+
+
+def _alone(ctx, kind, rel):
+    q = (ctx.tc if kind == "tc" else ctx.sg)(rel)
+    st = q.wait()
+    res = (q.result(), q.delta_sizes(), st.iterations)
+    q.free()
+    return res
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2607_17571_gb300 import wg
+    c = wg.Context(0)
+    yield c
+    c.close()
+
+
+def test_alone_equals_mix_equals_oracle(ctx):
+    from paper_2607_17571_gb300 import wg
+    qs = _mix(1)
+    rels = [ctx.load(g.src, g.dst) for _, g in qs]
+    alone = [_alone(ctx, k, r) for (k, _), r in zip(qs, rels)]
+    reqs = [(wg.WG_TC if k == "tc" else wg.WG_SG, r) for (k, _), r in zip(qs, rels)]
+    handles = ctx.submit(reqs)
+    for i, h in enumerate(handles):
+        st = h.wait()
+        assert st.state == wg.WG_DONE
+        got = (h.result(), h.delta_sizes(), st.iterations)
+        assert np.array_equal(got[0], alone[i][0]), i
+        assert got[1] == alone[i][1] and got[2] == alone[i][2]
+        h.free()
+    for (k, g), a in list(zip(qs, alone))[::5]:
+        want = (oracle_tc if k == "tc" else oracle_sg)(g.src, g.dst)
+        assert np.array_equal(a[0], want.keys) and a[1] == want.log.tolist()
+    for r in rels:
+        r.free()
+
+
+def test_continuous_admission(ctx):
+    from paper_2607_17571_gb300 import wg
+    qs = _mix(2, 30)
+    rels = [ctx.load(g.src, g.dst) for _, g in qs]
+    alone = [_alone(ctx, k, r) for (k, _), r in zip(qs, rels)]
+    handles = []
+    for wave in range(3):  # later waves arrive while earlier queries are on the GPU
+        part = list(range(wave * 10, wave * 10 + 10))
+        handles += ctx.submit([(wg.WG_TC if qs[i][0] == "tc" else wg.WG_SG, rels[i]) for i in part])
+        ctx.serve_step(2)
+    while ctx.serve_step(4) > 0:
+        pass
+    for i, h in enumerate(handles):
+        st = h.poll()
+        assert st.state == wg.WG_DONE
+        assert np.array_equal(h.result(), alone[i][0]) and h.delta_sizes() == alone[i][1]
+        h.free()
+    for r in rels:
+        r.free()
+
+
+def test_preemption_under_small_budget():
+    from paper_2607_17571_gb300 import wg
+    gs = [I.er_graph(n, 3 * n, 70 + n) for n in (300, 500, 700, 900, 1100, 1300)]
+    want = [oracle_tc(g.src, g.dst) for g in gs]
+    with wg.Context(0, mem_budget=96 << 20) as c:
+        rels = [c.load(g.src, g.dst) for g in gs]
+        hs = c.submit([(wg.WG_TC, r) for r in rels])
+        for h, w in zip(hs, want):
+            st = h.wait()
+            assert st.state == wg.WG_DONE
+            assert np.array_equal(h.result(), w.keys) and h.delta_sizes() == w.log.tolist()
+            h.free()
+
+
+def test_query_larger_than_budget_fails_cleanly():
+    from paper_2607_17571_gb300 import wg
+    g = I.er_graph(8000, 24000, 5)             # ~5e7 tuples: far beyond an 80 MB budget
+    small = I.er_graph(200, 500, 6)
+    with wg.Context(0, mem_budget=80 << 20) as c:
+        big_rel, small_rel = c.load(g.src, g.dst), c.load(small.src, small.dst)
+        hb, hs = c.submit([(wg.WG_TC, big_rel), (wg.WG_TC, small_rel)])
+        with pytest.raises(wg.WgError) as e:
+            hb.wait()
+        assert e.value.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
+        hs.wait()
+        assert np.array_equal(hs.result(), oracle_tc(small.src, small.dst).keys)
+
+
+def test_iteration_cap_in_batch(ctx):
+    from paper_2607_17571_gb300 import wg
+    g = I.path(40)
+    rel = ctx.load(g.src, g.dst)
+    h, h2 = ctx.submit([(wg.WG_TC, rel, dict(max_iters=7)), (wg.WG_TC, rel)])
+    with pytest.raises(wg.WgError) as e:
+        h.wait()
+    assert e.value.code == wg.WG_E_ITER_CAP
+    assert h.delta_sizes() == oracle_tc(g.src, g.dst, max_iters=7).log.tolist()
+    h2.wait()
+    assert h2.poll().iterations == 39
+    h.free()
+    h2.free()
+    rel.free()
