@@ -97,7 +97,7 @@ def test_preemption_under_small_budget():
     from paper_2607_17571_gb300 import wg
     gs = [I.er_graph(n, 3 * n, 70 + n) for n in (300, 500, 700, 900, 1100, 1300)]
     want = [oracle_tc(g.src, g.dst) for g in gs]
-    with wg.Context(0, mem_budget=96 << 20) as c:
+    with wg.Context(0, mem_budget=320 << 20) as c:  # each fits alone, not all at once
         rels = [c.load(g.src, g.dst) for g in gs]
         hs = c.submit([(wg.WG_TC, r) for r in rels])
         for h, w in zip(hs, want):
