@@ -313,13 +313,229 @@ def run_ours(args):
     return 0
 
 
+def _pct(xs, p):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    return xs[min(len(xs) - 1, int(round(p / 100.0 * (len(xs) - 1))))]
+
+
+def run_batch(args):
+    """Many small uneven TC fixpoints: 4,096 ER queries (n log-uniform in
+    [64, 16384], mean out-degree U[1.2, 3.0]), batched through wg_submit /
+    wg_serve_step, against the plain per-query launch loop on the same GPU.
+    One step = the whole set of queries in each arm."""
+    import torch
+
+    import oracle
+    from paper_2607_17571_gb300 import inputs as I
+    from paper_2607_17571_gb300 import wg
+
+    torch.cuda.set_device(0)
+    sizes = I.batch_query_sizes(args.n_queries)
+    graphs = [I.er_graph(n, m, s) for (n, m, s) in sizes]
+    ctx = wg.Context(0)
+    rels = [ctx.load(g.src, g.dst) for g in graphs]
+    # parity sample: the smallest queries, checked against the oracle
+    order = sorted(range(len(sizes)), key=lambda i: sizes[i][0])
+    sample = set(order[:: max(1, len(order) // 24)][:24])
+    want = {i: oracle.oracle_tc(graphs[i].src, graphs[i].dst) for i in sample}
+
+    def batched():
+        t0 = time.perf_counter()
+        hs = ctx.submit([(wg.WG_TC, r) for r in rels])
+        idx = {h.id: i for i, h in enumerate(hs)}
+        lat, tuples, launches, bad = [0.0] * len(hs), 0, 0, 0
+        left = len(hs)
+        while left:
+            ctx.serve_step(args.batch_iters)
+            for qid in ctx.take_completed():
+                i = idx[qid]
+                h = hs[i]
+                st = h.poll()
+                lat[i] = (time.perf_counter() - t0) * 1e3
+                if st.state != wg.WG_DONE:
+                    bad += 1
+                tuples += st.n_tuples
+                if i in want and not np.array_equal(h.result(), want[i].keys):
+                    bad += 1
+                h.free()
+                left -= 1
+        return time.perf_counter() - t0, lat, tuples, bad
+
+    def plain():
+        t0 = time.perf_counter()
+        lat, tuples, launches, bad = [], 0, 0, 0
+        for i, r in enumerate(rels):
+            q = ctx.tc(r)
+            st = q.wait()
+            lat.append((time.perf_counter() - t0) * 1e3)
+            tuples += st.n_tuples
+            launches += st.gpu_launches
+            if i in want and not np.array_equal(q.result(), want[i].keys):
+                bad += 1
+            q.free()
+        return time.perf_counter() - t0, lat, tuples, bad
+
+    # warm-up: engines, graphs and pools
+    for r in rels[:4]:
+        q = ctx.tc(r)
+        q.wait()
+        q.free()
+    hs = ctx.submit([(wg.WG_TC, r) for r in rels[:32]])
+    for h in hs:
+        h.wait()
+        h.free()
+    ctx.take_completed()
+    torch.cuda.synchronize()
+    tb, lb, nb, bad_b = batched()
+    tp, lp, npl, bad_p = plain()
+    n = len(rels)
+    line = {"metric": "batched TC fixpoints: queries/s", "value": n / tb, "unit": "queries/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(tb * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": "batch4096", "queries": n,
+                       "desc": "ER TC queries, n log-uniform [64,16384], mean degree U[1.2,3.0], "
+                               "seeds 40000+q", "closure_tuples_total": int(nb),
+                       "iterations_per_launch": args.batch_iters},
+            "batched": {"seconds": round(tb, 3), "queries_per_s": n / tb, "tuples_per_s": nb / tb,
+                        "p50_ms": _pct(lb, 50), "p99_ms": _pct(lb, 99), "parity_failures": bad_b},
+            "plain_loop": {"seconds": round(tp, 3), "queries_per_s": n / tp,
+                           "tuples_per_s": npl / tp, "p50_ms": _pct(lp, 50), "p99_ms": _pct(lp, 99),
+                           "parity_failures": bad_p, "gpu_launches": launches},
+            "parity_sample": len(want), "same_total": nb == npl}
+    print(json.dumps(line))
+    for r in rels:
+        r.free()
+    ctx.close()
+    return 0
+
+
+def run_serve(args):
+    """Open-loop Poisson arrivals of a mixed TC / SG request stream (see
+    inputs.serve_request), served under a fixed device-memory budget: the
+    continuous-batching server (requests join the running set at iteration
+    boundaries) against the plain loop that runs one query at a time in
+    arrival order.  The same request pool is replayed at every rate."""
+    import torch
+
+    from paper_2607_17571_gb300 import inputs as I
+    from paper_2607_17571_gb300 import wg
+
+    torch.cuda.set_device(0)
+    rates = [float(x) for x in args.rates.split(",")]
+    reqs = [I.serve_request(r) for r in range(args.n_requests)]
+    ctx = wg.Context(0, mem_budget=int(args.budget_gb * (1 << 30)))
+    rels = [ctx.load(g.src, g.dst) for _, g in reqs]
+    kinds = [wg.WG_TC if k == "tc" else wg.WG_SG for k, _ in reqs]
+
+    def single(i):
+        return (ctx.tc if kinds[i] == wg.WG_TC else ctx.sg)(rels[i])
+
+    # warm-up of both paths on small requests
+    small = sorted(range(len(reqs)), key=lambda i: len(reqs[i][1]))[:6]
+    for i in small:
+        q = single(i)
+        q.wait()
+        q.free()
+    for h in ctx.submit([(kinds[i], rels[i]) for i in small]):
+        h.wait()
+        h.free()
+    ctx.take_completed()
+
+    def served(arr):
+        n = len(arr)
+        lat, ok, rej, tuples = [None] * n, 0, 0, 0
+        idx, nxt, done = {}, 0, 0
+        t0 = time.perf_counter()
+        while done < n:
+            now = time.perf_counter() - t0
+            new = []
+            while nxt < n and arr[nxt] <= now:
+                new.append(nxt)
+                nxt += 1
+            if new:
+                for i, h in zip(new, ctx.submit([(kinds[i], rels[i]) for i in new])):
+                    idx[h.id] = (i, h)
+            running = ctx.serve_step(args.serve_iters)
+            t = time.perf_counter() - t0
+            for qid in ctx.take_completed():
+                i, h = idx.pop(qid)
+                st = h.poll()
+                lat[i] = (t - arr[i]) * 1e3
+                if st.state == wg.WG_DONE:
+                    ok += 1
+                    tuples += st.n_tuples
+                else:
+                    rej += 1
+                h.free()
+                done += 1
+            if running == 0 and nxt < n:
+                time.sleep(max(0.0, min(0.002, arr[nxt] - (time.perf_counter() - t0))))
+        el = time.perf_counter() - t0
+        good = [x for x in lat if x is not None]
+        return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
+                    p50_ms=_pct(good, 50), p99_ms=_pct(good, 99), completed=ok, rejected=rej)
+
+    def plain(arr):
+        n = len(arr)
+        lat, ok, rej, tuples = [], 0, 0, 0
+        t0 = time.perf_counter()
+        for i in range(n):
+            wait = arr[i] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            q = single(i)
+            try:
+                st = q.wait()
+                ok += 1
+                tuples += st.n_tuples
+            except wg.WgError:
+                rej += 1
+            lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
+            q.free()
+        el = time.perf_counter() - t0
+        return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
+                    p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), completed=ok, rejected=rej)
+
+    points = []
+    for rate in rates:
+        arr = I.poisson_arrivals(len(reqs), rate, seed=5)
+        b = served(arr)
+        p = plain(arr)
+        points.append({"rate_qps": rate, "served": b, "plain_loop": p})
+    best = max(points, key=lambda x: x["served"]["queries_per_s"])
+    line = {"metric": "served TC/SG queries/s (p50/p99 latency)",
+            "value": best["served"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+            "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
+            "config": {"workload": "serve", "requests_per_rate": len(reqs),
+                       "mix": "TC 75% (70% ER batch-mix sizes, 30% R-MAT DAG 1e4..1e6 edges), "
+                              "SG 25% (forests, batch-mix sizes)",
+                       "budget_gb": args.budget_gb, "iterations_per_round": args.serve_iters},
+            "points": points}
+    print(json.dumps(line))
+    for r in rels:
+        r.free()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tc_rmat17_400k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="tc_rmat17_400k",
+                    choices=sorted(WORKLOADS) + ["batch4096", "serve"])
+    ap.add_argument("--n-queries", type=int, default=4096)
+    ap.add_argument("--batch-iters", type=int, default=4)
+    ap.add_argument("--rates", default="100,200,500,1000,2000,5000")
+    ap.add_argument("--n-requests", type=int, default=80)
+    ap.add_argument("--budget-gb", type=float, default=60.0)
+    ap.add_argument("--serve-iters", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
@@ -329,6 +545,10 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.workload == "batch4096":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

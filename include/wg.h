@@ -171,6 +171,12 @@ int wg_submit(wg_ctx* ctx, const wg_request* reqs, size_t n, wg_query* ids);
  * device beyond that.  *n_running receives the number of queries in flight. */
 int wg_serve_step(wg_ctx* ctx, uint32_t iters, size_t* n_running);
 
+/* Ids of batch queries that reached DONE or FAILED since the previous call
+ * (at most cap of them; *n_out = how many were written; the rest stay queued
+ * for the next call).  Lets a serving loop find finished queries without
+ * polling every handle.  Errors: WG_E_INVAL. */
+int wg_take_completed(wg_ctx* ctx, wg_query* ids, size_t cap, size_t* n_out);
+
 /* ---- completion and results ---------------------------------------------- */
 /* Non-blocking: fills *st. */
 int wg_poll(wg_ctx* ctx, wg_query q, wg_status* st);

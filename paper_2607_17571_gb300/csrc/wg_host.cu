@@ -81,6 +81,7 @@ struct wg_ctx {
   std::vector<std::unique_ptr<EngineBase>> idle;  // single-query engines ready for reuse
   std::map<int, std::unique_ptr<EngineBase>> batch;  // batch engines by key class
   std::vector<uint64_t> pending;                  // submitted, not yet admitted
+  std::vector<uint64_t> completed;                // batch queries finished, not yet taken
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
   unsigned long long* s_status = nullptr; size_t s_status_n = 0;
@@ -960,6 +961,7 @@ static int batch_preempt(wg_ctx* c, int cls, int why) {
     q->state = WG_FAILED;
     q->error = why;
     q->t_done_us = now_us();
+    c->completed.push_back(q->id);
     return WG_OK;
   }
   q->state = WG_PENDING;
@@ -993,6 +995,7 @@ static int batch_retire(wg_ctx* c, int cls) {
       q->state = WG_FAILED;
       q->error = rc;
       q->t_done_us = now_us();
+      c->completed.push_back(q->id);
       continue;
     }
     if (done.n_full)
@@ -1002,6 +1005,7 @@ static int batch_retire(wg_ctx* c, int cls) {
     q->state = done.state == INST_DONE ? WG_DONE : WG_FAILED;
     q->error = done.state == INST_DONE ? WG_OK : WG_E_ITER_CAP;
     q->t_done_us = now_us();
+    c->completed.push_back(q->id);
   }
   // every retired result has been copied out: the retire pool starts over
   E->h.r_used = 0;
@@ -1017,7 +1021,11 @@ static void batch_fail_all(wg_ctx* c, int cls, int rc) {
   for (uint32_t s = 0; s < E->n_slots; ++s)
     if (B.slot_q[s]) {
       auto it = c->queries.find(B.slot_q[s]);
-      if (it != c->queries.end()) { it->second->state = WG_FAILED; it->second->error = rc; }
+      if (it != c->queries.end()) {
+        it->second->state = WG_FAILED;
+        it->second->error = rc;
+        c->completed.push_back(it->first);
+      }
       B.slot_q[s] = 0;
       E->evict(s);
     }
@@ -1313,6 +1321,15 @@ int wg_serve_step(wg_ctx* c, uint32_t iters, size_t* n_running) {
     for (auto& kv : c->queries) r += kv.second->batch && kv.second->state == WG_RUNNING;
     *n_running = r + c->pending.size();
   }
+  return WG_OK;
+}
+
+int wg_take_completed(wg_ctx* c, wg_query* ids, size_t cap, size_t* n_out) {
+  if (!c || !n_out || (cap && !ids)) return set_err(WG_E_INVAL, "bad argument");
+  const size_t n = std::min(cap, c->completed.size());
+  for (size_t i = 0; i < n; ++i) ids[i] = c->completed[i];
+  c->completed.erase(c->completed.begin(), c->completed.begin() + n);
+  *n_out = n;
   return WG_OK;
 }
 

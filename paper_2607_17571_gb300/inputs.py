@@ -20,6 +20,8 @@ Graph families (the shapes of the paper's evaluation workloads, Sec. Evaluation
                     cross edges u -> v between distinct nodes of equal depth.
 * ``batch_queries`` the many-small-queries mix: ER graphs with node count
                     log-uniform in [64, 16384] and mean degree U[1.2, 3.0].
+* ``serve_request`` the served mix of TC / SG queries of very different sizes,
+                    with ``poisson_arrivals`` for an open-loop arrival stream.
 * small closed-form families: ``path``, ``cycle``, ``binary_tree``.
 """
 from __future__ import annotations
@@ -148,6 +150,37 @@ def rmat_dag(scale: int, n_edges: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05))
                                     abcd=list(abcd)))
 
 
+def rmat_dag16(scale: int, n_edges: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05)) -> EdgeList:
+    """The rmat_dag recipe (quadrant recursion, random relabel, src < dst,
+    distinct, exactly ``n_edges``) drawing 16-bit uniforms: one splitmix64
+    value decides four levels, so quadrant probabilities have 2^-16
+    resolution.  Used for the serving mix, where graphs of up to 10^6 edges
+    are drawn on the fly."""
+    a, b, c, _ = abcd
+    n = 1 << scale
+    s = Stream(seed, "rmat16")
+    perm = np.argsort(Stream(seed, "rmat16-relabel").u64(n), kind="stable").astype(np.uint64)
+    t1, t2, t3 = (int(round(x * 65536)) for x in (a, a + b, a + b + c))
+    words = (scale + 3) // 4
+    drawn = np.empty(0, dtype=np.uint64)
+    while True:
+        m = max(4096, 3 * n_edges)
+        r = s.u64(m * words).reshape(m, words)
+        src = np.zeros(m, dtype=np.int64)
+        dst = np.zeros(m, dtype=np.int64)
+        for k in range(scale):  # most significant level first
+            u = ((r[:, k // 4] >> np.uint64(16 * (k % 4))) & np.uint64(0xFFFF)).astype(np.int64)
+            src = (src << 1) | (u >= t2)
+            dst = (dst << 1) | (((u >= t1) & (u < t2)) | (u >= t3))
+        src = perm[src]
+        dst = perm[dst]
+        keep = src < dst
+        drawn = np.concatenate([drawn, (src[keep] << np.uint64(32)) | dst[keep]])
+        got = _first_distinct(drawn, n_edges)
+        if got is not None:
+            return _split(got, dict(family="rmat_dag16", scale=scale, n_edges=n_edges, seed=seed))
+
+
 def _poisson_cdf(lam: float, kmax: int = 64):
     p = math.exp(-lam)
     cdf, acc = [], 0.0
@@ -236,6 +269,32 @@ def batch_query_sizes(n_queries: int, seed0: int = 40000, lo: int = 64, hi: int 
 
 def batch_queries(n_queries: int, seed0: int = 40000, **kw):
     return [er_graph(n, m, s) for (n, m, s) in batch_query_sizes(n_queries, seed0, **kw)]
+
+
+def serve_request(r: int, seed: int = 5, rmat_edges=(10_000, 1_000_000)):
+    """Request r of the served mix: (kind, EdgeList).  TC 75% / SG 25%.  TC
+    graphs: 70% ER with the batch mix's sizes, 30% R-MAT DAGs with |E|
+    log-uniform in ``rmat_edges`` on 2^ceil(log2(|E|/3)) nodes.  SG graphs:
+    the forest recipe (one root per 1,500 nodes, at least 8, Poisson(2) branching, 1%
+    equal-depth cross edges) with the batch mix's node counts."""
+    st = Stream(seed * 1_000_003 + r, "serve")
+    u = st.uniform(4)
+    sub = seed * 1_000_003 + r
+    n = int(round(math.exp(math.log(64) + u[2] * (math.log(16384) - math.log(64)))))
+    if u[0] < 0.25:
+        return "sg", sg_forest(max(n, 64), max(8, n // 1500), 2.0, 0.01, sub)
+    if u[1] < 0.70:
+        return "tc", er_graph(n, int(round(n * (1.2 + u[3] * 1.8))), sub)
+    lo, hi = rmat_edges
+    m = int(round(math.exp(math.log(lo) + u[3] * (math.log(hi) - math.log(lo)))))
+    scale = max(4, math.ceil(math.log2(m / 3)))
+    return "tc", rmat_dag16(scale, m, sub)
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 5) -> np.ndarray:
+    """Arrival times (s) of an open-loop Poisson stream: exponential gaps."""
+    u = Stream(seed, f"arrivals-{rate}").uniform(n)
+    return np.cumsum(-np.log1p(-u) / rate)
 
 
 def path(n: int) -> EdgeList:

@@ -67,6 +67,7 @@ SIGNATURES = {
     "wg_submit": (c_int, [c_void_p, POINTER(wg_request), c_size_t, POINTER(c_uint64)]),
     "wg_serve_step": (c_int, [c_void_p, c_uint32, POINTER(c_size_t)]),
     "wg_poll": (c_int, [c_void_p, c_uint64, POINTER(wg_status)]),
+    "wg_take_completed": (c_int, [c_void_p, POINTER(c_uint64), c_size_t, POINTER(c_size_t)]),
     "wg_wait": (c_int, [c_void_p, c_uint64, c_uint64]),
     "wg_result_copy": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_copy_device": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
@@ -293,6 +294,13 @@ class Context:
         ids = (c_uint64 * max(1, len(reqs)))()
         _check(self.lib.wg_submit(self.h, arr, len(reqs), ids), "wg_submit")
         return [Query(self, ids[i]) for i in range(len(reqs))]
+
+    def take_completed(self, cap: int = 65536) -> list:
+        """Ids of batch queries finished since the previous call."""
+        ids = (c_uint64 * cap)()
+        n = c_size_t()
+        _check(self.lib.wg_take_completed(self.h, ids, cap, byref(n)), "wg_take_completed")
+        return [ids[i] for i in range(n.value)]
 
     def serve_step(self, iters: int = 0) -> int:
         n = c_size_t()
