@@ -334,8 +334,16 @@ def run_batch(args):
     torch.cuda.set_device(0)
     sizes = I.batch_query_sizes(args.n_queries)
     graphs = [I.er_graph(n, m, s) for (n, m, s) in sizes]
-    ctx = wg.Context(0)
-    rels = [ctx.load(g.src, g.dst) for g in graphs]
+    ctx, rels = None, None
+
+    def open_ctx():  # one context per arm, so neither holds the other's pools
+        nonlocal ctx, rels
+        if ctx is not None:
+            for r in rels:
+                r.free()
+            ctx.close()
+        ctx = wg.Context(0)
+        rels = [ctx.load(g.src, g.dst) for g in graphs]
     # parity sample: the smallest queries, checked against the oracle
     order = sorted(range(len(sizes)), key=lambda i: sizes[i][0])
     sample = set(order[:: max(1, len(order) // 24)][:24])
@@ -377,11 +385,8 @@ def run_batch(args):
             q.free()
         return time.perf_counter() - t0, lat, tuples, bad
 
-    # warm-up: engines, graphs and pools
-    for r in rels[:4]:
-        q = ctx.tc(r)
-        q.wait()
-        q.free()
+    # each arm: its own context, warmed up (engines, graphs, pools), then timed
+    open_ctx()
     hs = ctx.submit([(wg.WG_TC, r) for r in rels[:32]])
     for h in hs:
         h.wait()
@@ -389,6 +394,12 @@ def run_batch(args):
     ctx.take_completed()
     torch.cuda.synchronize()
     tb, lb, nb, bad_b = batched()
+    open_ctx()
+    for r in rels[:4]:
+        q = ctx.tc(r)
+        q.wait()
+        q.free()
+    torch.cuda.synchronize()
     tp, lp, npl, bad_p = plain()
     n = len(rels)
     line = {"metric": "batched TC fixpoints: queries/s", "value": n / tb, "unit": "queries/s",
@@ -426,23 +437,33 @@ def run_serve(args):
     torch.cuda.set_device(0)
     rates = [float(x) for x in args.rates.split(",")]
     reqs = [I.serve_request(r) for r in range(args.n_requests)]
-    ctx = wg.Context(0, mem_budget=int(args.budget_gb * (1 << 30)))
-    rels = [ctx.load(g.src, g.dst) for _, g in reqs]
     kinds = [wg.WG_TC if k == "tc" else wg.WG_SG for k, _ in reqs]
+    small = sorted(range(len(reqs)), key=lambda i: len(reqs[i][1]))[:6]
+    ctx, rels = None, None
 
     def single(i):
         return (ctx.tc if kinds[i] == wg.WG_TC else ctx.sg)(rels[i])
 
-    # warm-up of both paths on small requests
-    small = sorted(range(len(reqs)), key=lambda i: len(reqs[i][1]))[:6]
-    for i in small:
-        q = single(i)
-        q.wait()
-        q.free()
-    for h in ctx.submit([(kinds[i], rels[i]) for i in small]):
-        h.wait()
-        h.free()
-    ctx.take_completed()
+    def open_ctx(batched_arm):
+        """A fresh context under the budget for one arm (relations resident,
+        warmed up on the smallest requests)."""
+        nonlocal ctx, rels
+        if ctx is not None:
+            for r in rels:
+                r.free()
+            ctx.close()
+        ctx = wg.Context(0, mem_budget=int(args.budget_gb * (1 << 30)))
+        rels = [ctx.load(g.src, g.dst) for _, g in reqs]
+        if batched_arm:
+            for h in ctx.submit([(kinds[i], rels[i]) for i in small]):
+                h.wait()
+                h.free()
+            ctx.take_completed()
+        else:
+            for i in small:
+                q = single(i)
+                q.wait()
+                q.free()
 
     def served(arr):
         n = len(arr)
@@ -502,7 +523,9 @@ def run_serve(args):
     points = []
     for rate in rates:
         arr = I.poisson_arrivals(len(reqs), rate, seed=5)
+        open_ctx(True)
         b = served(arr)
+        open_ctx(False)
         p = plain(arr)
         points.append({"rate_qps": rate, "served": b, "plain_loop": p})
     best = max(points, key=lambda x: x["served"]["queries_per_s"])
