@@ -92,7 +92,8 @@ struct Inst {
   uint32_t res_pool, iters_done;
   unsigned long long cand_total;
   unsigned long long* log;     // |Delta^0|, |Delta^1|, ...
-  uint32_t log_cap, pad;
+  uint32_t log_cap;
+  uint32_t fresh;              // admitted, delta not yet initialised
 };
 
 // Stage slots of an engine (one Stage record per kernel of the iteration).

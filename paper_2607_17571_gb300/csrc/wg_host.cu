@@ -705,6 +705,7 @@ struct Engine : EngineBase {
     I.d_off = d_off;
     I.log = (unsigned long long*)b_log.p + (size_t)slot * log_cap;
     I.log_cap = log_cap;
+    I.fresh = 1;
     hi[slot] = I;
     CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
     return WG_OK;

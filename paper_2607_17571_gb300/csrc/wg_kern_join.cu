@@ -625,12 +625,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
 // Delta^{-1} of a fresh instance: the diagonal {(v, v)}.  Joining it with E
 // through the ordinary TC join yields E itself (the TC base rule); through the
 // SG base-rule join it yields the sibling pairs.
+// Only instances admitted since the last launch (fresh) are touched; the
+// range [first, first + count) may also hold running or free slots.
 template <typename K>
 __global__ void k_init_diag(Inst* inst, uint32_t first, uint32_t count, K* dpool) {
   for (uint32_t q = first + blockIdx.x; q < first + count; q += gridDim.x) {
     const Inst I = inst[q];
+    if (!I.fresh || I.state != INST_ACTIVE) continue;  // uniform across the block
     K* o = dpool + I.d_off;
     for (uint32_t v = threadIdx.x; v < I.nv; v += blockDim.x) o[v] = ((K)v << I.w) | (K)v;
+    __syncthreads();
+    if (threadIdx.x == 0) inst[q].fresh = 0;
   }
 }
 

@@ -93,6 +93,25 @@ def test_continuous_admission(ctx):
         r.free()
 
 
+def test_slot_reuse_with_running_neighbours(ctx):
+    # queries finish at very different times, so freed slots are reused while
+    # their neighbours still run: only the new instances may be initialised
+    from paper_2607_17571_gb300 import wg
+    gs = [I.path(n) for n in (3, 40, 4, 60, 5, 35, 6, 50)] + [I.er_graph(300, 600, 9)] * 6
+    want = [oracle_tc(g.src, g.dst) for g in gs]
+    rels = [ctx.load(g.src, g.dst) for g in gs]
+    hs = ctx.submit([(wg.WG_TC, r) for r in rels[:8]])
+    for _ in range(3):
+        ctx.serve_step(4)          # the short paths finish, their slots free up
+    hs += ctx.submit([(wg.WG_TC, r) for r in rels[8:]])
+    for h, w in zip(hs, want):
+        h.wait()
+        assert np.array_equal(h.result(), w.keys) and h.delta_sizes() == w.log.tolist()
+        h.free()
+    for r in rels:
+        r.free()
+
+
 def test_preemption_under_small_budget():
     from paper_2607_17571_gb300 import wg
     gs = [I.er_graph(n, 3 * n, 70 + n) for n in (300, 500, 700, 900, 1100, 1300)]
