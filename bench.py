@@ -383,7 +383,7 @@ def run_batch(args):
             if i in want and not np.array_equal(q.result(), want[i].keys):
                 bad += 1
             q.free()
-        return time.perf_counter() - t0, lat, tuples, bad
+        return time.perf_counter() - t0, lat, tuples, bad, launches
 
     # each arm: its own context, warmed up (engines, graphs, pools), then timed
     open_ctx()
@@ -400,7 +400,7 @@ def run_batch(args):
         q.wait()
         q.free()
     torch.cuda.synchronize()
-    tp, lp, npl, bad_p = plain()
+    tp, lp, npl, bad_p, launches = plain()
     n = len(rels)
     line = {"metric": "batched TC fixpoints: queries/s", "value": n / tb, "unit": "queries/s",
             "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(tb * 1e3, 1),
