@@ -470,7 +470,7 @@ def run_serve(args):
         lat, ok, rej, tuples = [None] * n, 0, 0, 0
         idx, nxt, done = {}, 0, 0
         t0 = time.perf_counter()
-        while done < n:
+        while done < n and time.perf_counter() - t0 < args.arm_seconds:
             now = time.perf_counter() - t0
             new = []
             while nxt < n and arr[nxt] <= now:
@@ -496,14 +496,20 @@ def run_serve(args):
                 time.sleep(max(0.0, min(0.002, arr[nxt] - (time.perf_counter() - t0))))
         el = time.perf_counter() - t0
         good = [x for x in lat if x is not None]
+        unfinished = n - done
+        while ctx.serve_step(0) > 0:  # drain what is left before the context closes
+            pass
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
-                    p50_ms=_pct(good, 50), p99_ms=_pct(good, 99), completed=ok, rejected=rej)
+                    p50_ms=_pct(good, 50), p99_ms=_pct(good, 99), completed=ok, rejected=rej,
+                    unfinished_in_time=unfinished)
 
     def plain(arr):
         n = len(arr)
         lat, ok, rej, tuples = [], 0, 0, 0
         t0 = time.perf_counter()
         for i in range(n):
+            if time.perf_counter() - t0 > args.arm_seconds:
+                break
             wait = arr[i] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
@@ -518,7 +524,8 @@ def run_serve(args):
             q.free()
         el = time.perf_counter() - t0
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
-                    p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), completed=ok, rejected=rej)
+                    p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), completed=ok, rejected=rej,
+                    unfinished_in_time=n - ok - rej)
 
     points = []
     for rate in rates:
@@ -559,6 +566,8 @@ def main():
     ap.add_argument("--n-requests", type=int, default=80)
     ap.add_argument("--budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-iters", type=int, default=4)
+    ap.add_argument("--arm-seconds", type=float, default=60.0,
+                    help="wall-time limit of one serving arm at one rate")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)

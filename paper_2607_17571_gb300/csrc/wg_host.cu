@@ -881,8 +881,11 @@ constexpr uint32_t kBatchSlots = 1024;    // queries running at once per key cla
 constexpr uint32_t kBatchLogCap = 1024;   // per-iteration delta sizes kept per query
 
 struct BatchInfo {
-  std::vector<uint64_t> slot_q;  // query id per slot (0 = free)
-  std::vector<double> est;       // admission estimate of the slot's final size
+  std::vector<uint64_t> slot_q;    // query id per slot (0 = free)
+  std::vector<double> est;         // admission estimate of the slot's final size
+  std::vector<uint64_t> seq;       // admission order of the slot's instance
+  uint64_t next_seq = 1;
+  bool hold = false;               // no admissions after a preemption until one retires
 };
 static std::map<wg_ctx*, std::map<int, BatchInfo>> g_binfo;
 
@@ -905,6 +908,8 @@ static int batch_admit(wg_ctx* c, int cls) {
       load += B.est[s];
       ++active;
     }
+  if (B.hold && active > 0) return WG_OK;
+  B.hold = false;
   uint32_t first = 0xFFFFFFFFu, last = 0, next_free = 0;
   std::vector<uint64_t> still;
   for (uint64_t qid : c->pending) {
@@ -925,6 +930,7 @@ static int batch_admit(wg_ctx* c, int cls) {
     ++active;
     B.slot_q[slot] = qid;
     B.est[slot] = est;
+    B.seq[slot] = B.next_seq++;
     q->slot = slot;
     q->state = WG_RUNNING;
     first = std::min(first, slot);
@@ -935,22 +941,24 @@ static int batch_admit(wg_ctx* c, int cls) {
   return WG_OK;
 }
 
-// The pools cannot grow within the budget: requeue the largest running
-// instance (it restarts later from its base rule).  A query that does not fit
-// even alone fails with WG_E_BUDGET.
+// The pools cannot grow within the budget: requeue the most recently
+// admitted running instance (it restarts later from its base rule), and admit
+// nothing new until some instance retires.  Evicting the youngest keeps the
+// oldest instance progressing, so every query eventually runs with the whole
+// pool; a query that does not fit even alone fails with WG_E_BUDGET.
 template <typename K>
 static int batch_preempt(wg_ctx* c, int cls, int why) {
   auto& B = g_binfo[c][cls];
   auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
   uint32_t victim = 0xFFFFFFFFu, active = 0;
-  unsigned long long big = 0;
+  uint64_t young = 0;
   for (uint32_t s = 0; s < E->n_slots; ++s) {
     const Inst& I = E->hi[s];
     if (I.state != INST_ACTIVE) continue;
     ++active;
-    const unsigned long long sz = I.n_full + I.n_cand + I.n_delta;
-    if (victim == 0xFFFFFFFFu || sz > big) { big = sz; victim = s; }
+    if (victim == 0xFFFFFFFFu || B.seq[s] > young) { young = B.seq[s]; victim = s; }
   }
+  B.hold = true;
   if (victim == 0xFFFFFFFFu) return set_err(why, "batch pools cannot grow");
   const uint64_t qid = B.slot_q[victim];
   B.slot_q[victim] = 0;
@@ -981,6 +989,7 @@ static int batch_retire(wg_ctx* c, int cls) {
     if (I.state != INST_DONE && I.state != INST_ITERCAP) continue;
     auto it = c->queries.find(B.slot_q[s]);
     B.slot_q[s] = 0;
+    B.hold = false;  // room was freed: admissions may resume
     Inst done = I;
     TRY(E->evict(s));
     if (it == c->queries.end()) continue;  // freed while running
@@ -1086,6 +1095,7 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   c->batch[cls].reset(e);
   g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
   g_binfo[c][cls].est.assign(kBatchSlots, 0.0);
+  g_binfo[c][cls].seq.assign(kBatchSlots, 0);
   // start with pools worth about a third of the free budget; they grow later
   // only as far as the budget allows (then the largest instance is preempted)
   const double per_key = 4.0 * R->kb + 8.5 + 2.0 * R->kb + R->kb / 4.0;
