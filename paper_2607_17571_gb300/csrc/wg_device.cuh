@@ -72,6 +72,8 @@ struct Stage {
   unsigned long long* hist;     // radix digit counts [nseg][passes][kRadix]
   unsigned long long* pos;      // join prefix sums (one per delta tuple)
   unsigned long long* splits;   // per-tile start found by a partition kernel (or NULL)
+  unsigned long long* xlen;     // join count: candidates per source x (or NULL)
+  unsigned long long hist_n;    // join count: histogram counters to clear
   uint32_t nseg, ntiles;
   uint32_t ctr;                 // dynamic tile counter (zeroed by the writer)
   uint32_t epoch;
@@ -129,9 +131,12 @@ struct Dev {
   unsigned long long* status_sort;    // lookback words of radix passes
   unsigned long long* hist;           // [n_inst][passes][kRadix]
   unsigned long long* splits;         // tile partitions, as many entries as status_scalar
+  unsigned long long* xlen;           // candidates per source vertex (x-grouped sort)
+  Seg* segX;                          // one sort segment per source vertex
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;
+  uint32_t xseg;                      // sort each source's candidates on the low field only
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
 };

@@ -65,6 +65,10 @@ struct Relation;
 struct Query;
 struct EngineBase;
 
+// Largest vertex count for which single TC queries sort per source vertex
+// (per-vertex digit histograms: 512 counters of 8 bytes per vertex and pass).
+constexpr uint32_t kXSegMaxVertices = 1u << 18;
+
 // ------------------------------------------------------------------ context
 struct wg_ctx {
   int device = 0;
@@ -350,6 +354,7 @@ struct EngineBase {
   virtual uint32_t bits() const = 0;
   virtual uint32_t slots() const = 0;
   virtual bool fused() const = 0;
+  virtual bool xgrouped() const = 0;
   virtual void release() = 0;
 };
 
@@ -382,13 +387,14 @@ struct Query {
 template <typename K>
 struct Engine : EngineBase {
   wg_ctx* c;
-  bool single, fuse;
+  bool single, fuse, xseg;
+  uint32_t nv_cap = 0;  // vertices the x-grouped sort buffers can hold
   uint32_t n_slots, bits_, passes, dbits;
   Dev* dv = nullptr;   // device block
   Dev h{};             // host mirror (read back after each run)
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
-  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b;
   unsigned long long capC = 0, capF = 0, capR = 0;
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
@@ -398,15 +404,18 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 11 + (int)passes; }
+  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 1 : 0); }
 
-  Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_)
-      : c(ctx), single(single_), fuse(fuse_), n_slots(n), bits_(bits), log_cap(logcap) {
+  Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
+         bool xseg_)
+      : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
+        log_cap(logcap) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
   int kb() const override { return (int)sizeof(K); }
   bool fused() const override { return fuse; }
+  bool xgrouped() const override { return xseg; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -417,7 +426,7 @@ struct Engine : EngineBase {
     if (ev_done) cudaEventDestroy(ev_done);
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
-                   &R, &pos, &st_s, &st_k, &hist, &spl};
+                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b};
     for (DBuf* b : all) b->release(c);
   }
 
@@ -435,7 +444,7 @@ struct Engine : EngineBase {
     Seg* s = (Seg*)b_seg.p;
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
     h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
-    h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T;
+    h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T; h.xseg = xseg ? 1 : 0;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
@@ -461,6 +470,9 @@ struct Engine : EngineBase {
     h.status_scalar = (unsigned long long*)st_s.p;
     h.status_sort = (unsigned long long*)st_k.p;
     h.splits = (unsigned long long*)spl.p;
+    h.hist = (unsigned long long*)hist.p;
+    h.xlen = (unsigned long long*)xlen_b.p;
+    h.segX = (Seg*)segx_b.p;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, c->stream));
     return WG_OK;
@@ -494,7 +506,7 @@ struct Engine : EngineBase {
         if (rc == WG_OK) rc = nc[i].get(c, wantC * sizeof(K));
       }
       if (rc == WG_OK) rc = np.get(c, wantC * 8);
-      if (rc == WG_OK) rc = nk.get(c, (wantC / kTileC + n_slots + 2) * kRadix * 8);
+      if (rc == WG_OK) rc = nk.get(c, (wantC / kTileC + std::max(n_slots, nv_cap) + 2) * kRadix * 8);
       if (rc != WG_OK) return undo(rc);
       CK(cudaMemsetAsync(nk.p, 0, nk.bytes, c->stream));
       if (liveD)
@@ -562,6 +574,7 @@ struct Engine : EngineBase {
     launch_plan_delta(dv, s);
     mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s); mark();
     launch_plan_cand(dv, s);
+    if (xseg) launch_xseg_build(dv, s);
     launch_partition<K>(dv->st + S_EMIT, 1, kTileC, c->num_sms * 4, s);
     mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
@@ -674,6 +687,21 @@ struct Engine : EngineBase {
     return WG_OK;
   }
 
+  // Buffers of the x-grouped sort for relations of up to nv vertices.
+  int ensure_nv(uint32_t nv) {
+    if (!xseg || nv <= nv_cap) return WG_OK;
+    xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c);
+    TRY(xlen_b.get(c, (size_t)nv * 8));
+    TRY(segx_b.get(c, (size_t)nv * sizeof(Seg)));
+    TRY(hist.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8));
+    TRY(st_k.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8));
+    CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+    h.ctl.epoch = 0;
+    if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+    nv_cap = nv;
+    return put_pools();
+  }
+
   // Grow the pools to what the aborted run asked for (plus headroom).
   int grow() {
     const unsigned long long nc = h.ctl.need_cand ? h.ctl.need_cand + h.ctl.need_cand / 4 + 4096 : 0;
@@ -727,14 +755,14 @@ struct Engine : EngineBase {
 };
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
-                              uint32_t logcap, bool fuse, int* rc) {
+                              uint32_t logcap, bool fuse, bool xseg, int* rc) {
   EngineBase* e;
   if (kb == 4) {
-    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse);
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg);
     *rc = x->init();
     e = x;
   } else {
-    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse);
+    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg);
     *rc = x->init();
     e = x;
   }
@@ -752,6 +780,7 @@ static int single_start(wg_ctx* c, Query* q) {
   const unsigned long long wantF = std::max<unsigned long long>(
       {q->opts.reserve_full, Rl->peak_full, 4ull * Rl->ne, 1ull << 16});
   TRY(E->reset_single());
+  TRY(E->ensure_nv(Rl->nv));
   TRY(E->ensure(wantC, wantF, 0, false));
   TRY(E->admit(0, Rl, q->kind, q->opts.max_iters, 0));
   TRY(E->init_deltas(0, 1));
@@ -1090,7 +1119,8 @@ static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch)
 static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   if (c->batch[cls]) return WG_OK;
   int rc = WG_OK;
-  EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, true, &rc);
+  EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, true,
+                             false, &rc);
   if (!e) return rc;
   c->batch[cls].reset(e);
   g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
@@ -1267,18 +1297,22 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   Query* q;
   TRY(make_query(c, kind, edges, opts, &q));
   Relation* R = q->rel;
-  const uint32_t bits = 2 * R->w;
   const bool fuse = !(q->opts.flags & WG_FLAG_SEPARATE_STAGES);
+  // TC candidates leave the join grouped by source: sort each group on the
+  // destination field only (per-vertex histograms bound the vertex count)
+  const bool xseg = kind == WG_TC && R->nv <= kXSegMaxVertices;
+  const uint32_t bits = xseg ? R->w : 2 * R->w;
   // reuse an idle engine of the same key width, pass plan and stage layout
   for (size_t i = 0; i < c->idle.size(); ++i)
-    if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse) {
+    if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
+        c->idle[i]->xgrouped() == xseg) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
       break;
     }
   int rc = WG_OK;
   if (!q->own) {
-    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, &rc);
+    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc);
     if (!e) { c->queries.erase(q->id); return rc; }
     q->own.reset(e);
   }

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   // the radix histogram of this iteration starts from zero
-  const unsigned long long nz = (unsigned long long)stp->nseg * stp->passes * kRadix;
+  const unsigned long long nz = stp->hist_n;
   for (unsigned long long i = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; i < nz;
        i += (unsigned long long)gridDim.x * kThreads)
     stp->hist[i] = 0;
@@ -104,6 +104,24 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
         }
         sum += c[i];
       }
+    }
+    if (stp->xlen) {
+      // candidates per source x (Delta is sorted by x: one atomic per run)
+      uint32_t px = 0xFFFFFFFFu;
+      unsigned long long run = 0;
+#pragma unroll
+      for (int i = 0; i < kItemsD; ++i) {
+        if (b + i < n) {
+          const uint32_t x = (uint32_t)(sd[b + i] >> w);
+          if (x != px) {
+            if (run) atomicAdd(stp->xlen + px, run);
+            px = x;
+            run = 0;
+          }
+          run += c[i];
+        }
+      }
+      if (run) atomicAdd(stp->xlen + px, run);
     }
     unsigned long long tot;
     const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);
@@ -276,6 +294,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     if (threadIdx.x == 0) s_carry += tot;
     __syncthreads();
   }
+  const uint32_t nvx = dv->xseg ? dv->inst[0].nv : 0u;
+  for (uint32_t x = threadIdx.x; x < nvx; x += kPlanThreads) dv->xlen[x] = 0;
   if (threadIdx.x == 0) {
     Stage& s = dv->st[S_COUNT];
     s.in = dv->D[dv->dphase]; s.out = nullptr; s.aux = nullptr; s.out2 = nullptr;
@@ -283,6 +303,65 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     s.status = dv->status_scalar; s.hist = dv->hist; s.pos = dv->pos;
     s.nseg = N; s.ntiles = (uint32_t)s_carry; s.ctr = 0; s.epoch = ++ctl.epoch;
     s.passes = dv->passes; s.dbits = dv->dbits; s.shift = 0; s.pass = 0;
+    s.xlen = dv->xseg ? dv->xlen : nullptr;
+    s.hist_n = (unsigned long long)(dv->xseg ? nvx : N) * dv->passes * kRadix;
+  }
+}
+
+// x-grouped sort (single TC instance): the join emits candidates grouped by
+// source x in ascending order (Delta is sorted and each slab is contiguous),
+// so sorting each x-group on the destination field sorts the whole array.
+// Every source vertex becomes one sort segment: offsets and tile ranges from
+// the per-x candidate totals the count kernel accumulated.
+__global__ void __launch_bounds__(kPlanThreads) k_xseg_build(Dev* dv) {
+  constexpr int kPer = 16;
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long s_len, s_tiles;
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort) return;
+  const Inst& I = dv->inst[0];
+  const uint32_t nv = I.state == INST_ACTIVE ? I.nv : 0u;
+  if (threadIdx.x == 0) { s_len = I.c_off; s_tiles = 0; }
+  __syncthreads();
+  for (uint32_t base = 0; base < nv; base += kPer * kPlanThreads) {
+    const uint32_t x0 = base + threadIdx.x * kPer;
+    unsigned long long len[kPer], sl = 0, stl = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      len[i] = x0 + i < nv ? dv->xlen[x0 + i] : 0ull;
+      sl += len[i];
+      stl += (len[i] + kTileC - 1) / kTileC;
+    }
+    unsigned long long tl, tt;
+    const unsigned long long el = scan1024(sl, sh, &tl);
+    const unsigned long long et = scan1024(stl, sh, &tt);
+    unsigned long long off = s_len + el, tile = s_tiles + et;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      if (x0 + i < nv) {
+        Seg g{};
+        g.in_off = off; g.n = len[i]; g.out_off = off;
+        g.tile0 = (uint32_t)tile; g.ntiles = (uint32_t)((len[i] + kTileC - 1) / kTileC);
+        g.inst = 0;
+        dv->segX[x0 + i] = g;
+        off += len[i];
+        tile += g.ntiles;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { s_len += tl; s_tiles += tt; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int ids[2] = {S_HIST, S_HSCAN};
+    for (int k = 0; k < 2; ++k) {
+      dv->st[ids[k]].segs = dv->segX; dv->st[ids[k]].nseg = nv;
+      dv->st[ids[k]].ntiles = (uint32_t)s_tiles;
+    }
+    for (uint32_t p = 0; p < dv->passes; ++p) {
+      dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
+      dv->st[S_PASS0 + p].ntiles = (uint32_t)s_tiles;
+    }
   }
 }
 
@@ -691,6 +770,7 @@ void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_merge(Dev* dv, cudaStream_t s) { k_plan_merge<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_post(Dev* dv, cudaStream_t s) { k_plan_post<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_xseg_build(Dev* dv, cudaStream_t s) { k_xseg_build<<<1, kPlanThreads, 0, s>>>(dv); }
 template <typename K>
 void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s) {
   if (count) k_init_diag<K><<<count < 4096 ? count : 4096, 256, 0, s>>>(inst, first, count, (K*)dpool);
