@@ -73,6 +73,7 @@ struct Stage {
   unsigned long long* pos;      // join prefix sums (one per delta tuple)
   unsigned long long* splits;   // per-tile start found by a partition kernel (or NULL)
   unsigned long long* xlen;     // join count: candidates per source x (or NULL)
+  uint32_t* tile_seg;           // tile -> segment map (or NULL: binary search)
   unsigned long long hist_n;    // join count: histogram counters to clear
   uint32_t nseg, ntiles;
   uint32_t ctr;                 // dynamic tile counter (zeroed by the writer)
@@ -133,6 +134,7 @@ struct Dev {
   unsigned long long* splits;         // tile partitions, as many entries as status_scalar
   unsigned long long* xlen;           // candidates per source vertex (x-grouped sort)
   Seg* segX;                          // one sort segment per source vertex
+  uint32_t* tile_seg;                 // tile -> x-segment map of the x-grouped sort
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;
@@ -145,6 +147,26 @@ struct Dev {
 // contiguous run (blocked order, stride 16 words) then hit distinct banks.
 __device__ __forceinline__ uint32_t pad32(uint32_t i) { return i + (i >> 5); }
 template <int N> struct Padded { static constexpr int n = N + N / 32 + 1; };
+
+// Copy n <= kThreads*ITEMS consecutive elements to shared memory with every
+// global load in flight at once: a fixed-trip, predicated, unrolled loop
+// (a loop bounded by n would pay one load latency per iteration).
+template <int ITEMS, typename T, typename Idx>
+__device__ __forceinline__ void tile_to_smem(T* dst, const T* src, uint32_t n, Idx idx) {
+  T v[ITEMS];
+#pragma unroll
+  for (int e = 0; e < ITEMS; ++e) {
+    const uint32_t i = threadIdx.x + e * kThreads;
+    v[e] = i < n ? src[i] : (T)0;
+  }
+#pragma unroll
+  for (int e = 0; e < ITEMS; ++e) {
+    const uint32_t i = threadIdx.x + e * kThreads;
+    if (i < n) dst[idx(i)] = v[e];
+  }
+}
+struct Ident { __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return i; } };
+struct Pad32 { __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return i + (i >> 5); } };
 
 // ---------------------------------------------------------------- status words
 // [63:40] epoch (24 bits) | [39:38] flag | [37:0] value
@@ -246,7 +268,9 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 }
 
 // Global tile -> segment: the segment k with tile0 <= t < tile0 + ntiles.
-__device__ __forceinline__ uint32_t find_seg(const Seg* segs, uint32_t nseg, uint32_t t) {
+__device__ __forceinline__ uint32_t find_seg(const Seg* segs, uint32_t nseg, uint32_t t,
+                                             const uint32_t* tile_seg = nullptr) {
+  if (tile_seg) return tile_seg[t];
   uint32_t lo = 0, hi = nseg;  // largest k with tile0 <= t
   while (hi - lo > 1) {
     uint32_t mid = (lo + hi) >> 1;

@@ -394,7 +394,7 @@ struct Engine : EngineBase {
   Dev h{};             // host mirror (read back after each run)
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
-  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b;
   unsigned long long capC = 0, capF = 0, capR = 0;
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
@@ -426,7 +426,7 @@ struct Engine : EngineBase {
     if (ev_done) cudaEventDestroy(ev_done);
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
-                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b};
+                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b};
     for (DBuf* b : all) b->release(c);
   }
 
@@ -473,6 +473,7 @@ struct Engine : EngineBase {
     h.hist = (unsigned long long*)hist.p;
     h.xlen = (unsigned long long*)xlen_b.p;
     h.segX = (Seg*)segx_b.p;
+    h.tile_seg = (uint32_t*)tseg_b.p;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, c->stream));
     return WG_OK;
@@ -519,6 +520,10 @@ struct Engine : EngineBase {
       pos.release(c); st_k.release(c);
       pos = np; st_k = nk;
       capC = wantC;
+      if (xseg) {
+        tseg_b.release(c);
+        TRY(tseg_b.get(c, (capC / kTileC + nv_cap + 2) * 4));
+      }
       h.ctl.epoch = 0;
       if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
     }
@@ -690,11 +695,13 @@ struct Engine : EngineBase {
   // Buffers of the x-grouped sort for relations of up to nv vertices.
   int ensure_nv(uint32_t nv) {
     if (!xseg || nv <= nv_cap) return WG_OK;
-    xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c);
+    xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c); tseg_b.release(c);
     TRY(xlen_b.get(c, (size_t)nv * 8));
     TRY(segx_b.get(c, (size_t)nv * sizeof(Seg)));
     TRY(hist.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8));
     TRY(st_k.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8));
+    tseg_b.release(c);
+    TRY(tseg_b.get(c, (capC / kTileC + nv + 2) * 4));
     CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
     h.ctl.epoch = 0;
     if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));

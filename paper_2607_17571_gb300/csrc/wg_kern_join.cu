@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileD;
     const uint32_t n = (uint32_t)min((unsigned long long)kTileD, sg.n - start);
     const K* p = D + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sd[i] = p[i];
+    tile_to_smem<kItemsD>(sd, p, n, Ident());
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
     const uint32_t b = threadIdx.x * kItemsD;
@@ -203,10 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
     const bool staged = m <= (unsigned long long)kEmitWin;
     if (staged) {
-      for (uint32_t i = threadIdx.x; i < m; i += kThreads) {
-        spos[i] = P[i0 + i];
-        skey[i] = Dq[i0 + i];
-      }
+      tile_to_smem<kEmitWin / kThreads>(spos, P + i0, (uint32_t)m, Ident());
+      tile_to_smem<kEmitWin / kThreads>(skey, Dq + i0, (uint32_t)m, Ident());
     }
     __syncthreads();
     auto posat = [&](unsigned long long i) { return staged ? spos[i] : P[i0 + i]; };
@@ -344,6 +342,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_xseg_build(Dev* dv) {
         g.tile0 = (uint32_t)tile; g.ntiles = (uint32_t)((len[i] + kTileC - 1) / kTileC);
         g.inst = 0;
         dv->segX[x0 + i] = g;
+        for (uint32_t j = 0; j < g.ntiles; ++j) dv->tile_seg[tile + j] = x0 + i;
         off += len[i];
         tile += g.ntiles;
       }
@@ -356,11 +355,11 @@ __global__ void __launch_bounds__(kPlanThreads) k_xseg_build(Dev* dv) {
     const int ids[2] = {S_HIST, S_HSCAN};
     for (int k = 0; k < 2; ++k) {
       dv->st[ids[k]].segs = dv->segX; dv->st[ids[k]].nseg = nv;
-      dv->st[ids[k]].ntiles = (uint32_t)s_tiles;
+      dv->st[ids[k]].ntiles = (uint32_t)s_tiles; dv->st[ids[k]].tile_seg = dv->tile_seg;
     }
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
-      dv->st[S_PASS0 + p].ntiles = (uint32_t)s_tiles;
+      dv->st[S_PASS0 + p].ntiles = (uint32_t)s_tiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
     }
   }
 }

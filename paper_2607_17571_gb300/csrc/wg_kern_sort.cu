@@ -34,13 +34,13 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
     const Seg sg = stp->segs[k];
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
     const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
     const K* p = in + sg.in_off + start;
     for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[pad32(i)] = p[i];
+    tile_to_smem<kItemsC>(sk, p, n, Pad32());
     __syncthreads();
     // blocked order keeps equal neighbours together: count digit runs, one
     // shared atomic per run (clustered high digits cost one atomic per run)
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
     const Seg sg = stp->segs[k];
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
     const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
@@ -228,12 +228,12 @@ __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
     const Seg sg = stp->segs[k];
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
     const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
     const K* p = in + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) sk[pad32(i)] = p[i];
+    tile_to_smem<kItemsC>(sk, p, n, Pad32());
     if (threadIdx.x == 0 && start > 0) s_prev = p[-1];
     __syncthreads();
     const K* F = full + sg.aux_off;
@@ -243,8 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
     __syncthreads();
     const unsigned long long lo = s_lo, hi = s_hi;
     const bool staged = hi - lo <= (unsigned long long)kFWin;
-    if (staged)
-      for (uint32_t i = threadIdx.x; i < hi - lo; i += kThreads) sf[i] = F[lo + i];
+    if (staged) tile_to_smem<kFWin / kThreads>(sf, F + lo, (uint32_t)(hi - lo), Ident());
     __syncthreads();
 
     // classify a blocked run of keys: first copy and not in Full
@@ -332,7 +331,7 @@ __global__ void __launch_bounds__(kThreads) k_merge(Stage* stp) {
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
     const Seg sg = stp->segs[k];
     const K* A = A_all + sg.in_off;
     const K* B = B_all + sg.aux_off;
@@ -351,13 +350,34 @@ __global__ void __launch_bounds__(kThreads) k_merge(Stage* stp) {
     __syncthreads();
     const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0);
-    if (lb == 0) {
-      for (uint32_t i = threadIdx.x; i < la; i += kThreads) out[d0 + i] = A[a0 + i];
-    } else if (la == 0) {
-      for (uint32_t i = threadIdx.x; i < lb; i += kThreads) out[d0 + i] = B[b0 + i];
+    if (lb == 0 || la == 0) {  // one side only: a straight copy
+      const K* src = lb == 0 ? A + a0 : B + b0;
+      const uint32_t cnt = lb == 0 ? la : lb;
+      K v[kTileM / kThreads];
+#pragma unroll
+      for (int e = 0; e < kTileM / kThreads; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        v[e] = i < cnt ? src[i] : (K)0;
+      }
+#pragma unroll
+      for (int e = 0; e < kTileM / kThreads; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        if (i < cnt) out[d0 + i] = v[e];
+      }
     } else {
-      for (uint32_t i = threadIdx.x; i < la; i += kThreads) sm[i] = A[a0 + i];
-      for (uint32_t i = threadIdx.x; i < lb; i += kThreads) sm[la + i] = B[b0 + i];
+      {
+        K v[kTileM / kThreads];
+#pragma unroll
+        for (int e = 0; e < kTileM / kThreads; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          v[e] = i < la ? A[a0 + i] : (i < la + lb ? B[b0 + i - la] : (K)0);
+        }
+#pragma unroll
+        for (int e = 0; e < kTileM / kThreads; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          if (i < la + lb) sm[i] = v[e];
+        }
+      }
       __syncthreads();
       const K* SA = sm;
       const K* SB = sm + la;
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t);
+    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
     const Seg sg = stp->segs[k];
     const K* A = Aall + sg.in_off;
     const K* B = Ball + sg.aux_off;
@@ -436,15 +456,28 @@ __global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
     __syncthreads();
     const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
     const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
-    for (uint32_t i = threadIdx.x; i < la; i += kThreads) sin[pad32(i)] = A[a0 + i];
-    for (uint32_t i = threadIdx.x; i < lb; i += kThreads) sin[pad32(la + i)] = B[b0 + i];
-    if (threadIdx.x == 0) {
-      // the element just before this tile in merged order (its largest predecessor)
-      s_hasprev = d0 > 0;
-      K p = 0;
-      if (a0 > 0) p = A[a0 - 1];
-      if (b0 > 0 && B[b0 - 1] > p) p = B[b0 - 1];
-      s_prev = p;
+    {  // Full part then candidate part, every load in flight at once
+      K v[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        v[e] = i < la ? A[a0 + i] : (i < L ? B[b0 + i - la] : (K)0);
+      }
+      K pa = 0, pb = 0;
+      if (threadIdx.x == 0) {
+        // the element just before this tile in merged order (its largest predecessor)
+        if (a0 > 0) pa = A[a0 - 1];
+        if (b0 > 0) pb = B[b0 - 1];
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        if (i < L) sin[pad32(i)] = v[e];
+      }
+      if (threadIdx.x == 0) {
+        s_hasprev = d0 > 0;
+        s_prev = pb > pa ? pb : pa;
+      }
     }
     __syncthreads();
     // padded views of the Full part (SA) and the candidate part (SB)
