@@ -760,10 +760,15 @@ template <typename K>
 void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 int occupancy_join(int which) {
-  int b = 0;
-  if (which == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_join_count<K>, kThreads, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_join_emit<K>, kThreads, 0);
-  return b;
+  // largest shared-memory carveout first (see occupancy_of in wg_kern_sort.cu)
+  auto one = [](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0);
+    return b;
+  };
+  return which == 0 ? one(k_join_count<K>) : one(k_join_emit<K>);
 }
 void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }

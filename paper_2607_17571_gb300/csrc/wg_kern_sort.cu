@@ -597,18 +597,28 @@ void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaSt
   k_partition<K><<<grid, 256, 0, s>>>(consumer, mode, tile);
 }
 
+// Resident CTAs per SM of a persistent kernel.  The kernel first asks for the
+// largest shared-memory carveout: with the default split the SM would host
+// fewer CTAs than its registers allow.
+template <typename F>
+int occupancy_of(F kern) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0);
+  return b;
+}
+
 template <typename K>
 int occupancy_sort(int which) {
-  int b = 0;
   switch (which) {
-    case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_hist<K>, kThreads, 0); break;
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sort_pass<K>, kThreads, 0); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_unique_diff<K>, kThreads, 0); break;
-    case 3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_merge<K>, kThreads, 0); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_diff_merge<K>, kThreads, 0); break;
-    default: break;
+    case 0: return occupancy_of(k_sort_hist<K>);
+    case 1: return occupancy_of(k_sort_pass<K>);
+    case 2: return occupancy_of(k_unique_diff<K>);
+    case 3: return occupancy_of(k_merge<K>);
+    case 4: return occupancy_of(k_diff_merge<K>);
+    default: return 0;
   }
-  return b;
 }
 
 #define WG_INST(K)                                              \
