@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t deg(const uint32_t* off, uint32_t v) { retur
 
 // ------------------------------------------------------------------ join count
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_join_count(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
   __shared__ K sd[kTileD];
   __shared__ unsigned long long sp[kTileD];
   __shared__ unsigned long long s_scan[kWarps];

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 
 // ------------------------------------------------------------------ dedup + diff
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_unique_diff(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 4) k_unique_diff(Stage* stp) {
   __shared__ K sk[Padded<kTileC>::n];
   __shared__ K sf[kFWin];
   __shared__ unsigned long long s_scan[kWarps];
@@ -420,7 +420,7 @@ __device__ __forceinline__ unsigned long long mpath_tie(const K* A, unsigned lon
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_diff_merge(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
   constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
   __shared__ K sin[Padded<T>::n];  // Full part then candidate part; then Full' outputs
   __shared__ unsigned long long s_scan[kWarps];
