@@ -103,6 +103,12 @@ struct Inst {
 enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_HSCAN, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
                      S_NUM = S_PASS0 + kMaxPasses };
 
+// Tile of the join count: 3,072 / 2,048 delta tuples (static shared memory
+// holds the tuples and their 64-bit slab offsets, under 48 KB).
+template <typename K> struct CountTile { static constexpr int T = sizeof(K) == 4 ? 3072 : 2048; };
+// Full-relation window staged by dedup + diff (separate-stage mode).
+template <typename K> struct FWin { static constexpr int n = sizeof(K) == 4 ? 2048 : 1024; };
+
 // Tile of the fused dedup + set difference + merge: 16 KB of keys.
 template <typename K> struct FuseTile {
   static constexpr int T = sizeof(K) == 4 ? 4096 : 2048;
@@ -139,6 +145,7 @@ struct Dev {
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;
   uint32_t xseg;                      // sort each source's candidates on the low field only
+  uint32_t count_tile;                // delta tuples per join-count tile
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
 };

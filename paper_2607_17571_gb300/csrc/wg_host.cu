@@ -445,6 +445,7 @@ struct Engine : EngineBase {
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
     h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
     h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T; h.xseg = xseg ? 1 : 0;
+    h.count_tile = CountTile<K>::T;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;

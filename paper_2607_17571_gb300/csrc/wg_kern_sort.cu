@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_unique_diff(Stage* stp) {
   __shared__ K sk[Padded<kTileC>::n];
-  __shared__ K sf[kFWin];
+  __shared__ K sf[FWin<K>::n];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_lo, s_hi, s_excl;
   __shared__ K s_prev;
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_unique_diff(Stage* stp) {
     if (threadIdx.x == 32) s_hi = upper_bound_k(F, nf, sk[pad32(n - 1)]);
     __syncthreads();
     const unsigned long long lo = s_lo, hi = s_hi;
-    const bool staged = hi - lo <= (unsigned long long)kFWin;
-    if (staged) tile_to_smem<kFWin / kThreads>(sf, F + lo, (uint32_t)(hi - lo), Ident());
+    const bool staged = hi - lo <= (unsigned long long)FWin<K>::n;
+    if (staged) tile_to_smem<FWin<K>::n / kThreads>(sf, F + lo, (uint32_t)(hi - lo), Ident());
     __syncthreads();
 
     // classify a blocked run of keys: first copy and not in Full
