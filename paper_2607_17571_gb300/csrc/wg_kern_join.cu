@@ -23,7 +23,6 @@ namespace wg {
 
 constexpr int kPlanThreads = 1024;
 
-
 __device__ __forceinline__ unsigned long long scan1024(unsigned long long v, unsigned long long* sh,
                                                        unsigned long long* total) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -54,21 +53,10 @@ __device__ __forceinline__ unsigned long long scan1024(unsigned long long v, uns
 __device__ __forceinline__ uint32_t deg(const uint32_t* off, uint32_t v) { return off[v + 1] - off[v]; }
 
 // ------------------------------------------------------------------ join count
-__device__ __forceinline__ unsigned long long slab_size(const uint32_t* off, uint32_t kind,
-                                                        uint32_t iter, uint32_t x, uint32_t y) {
-  if (kind == KIND_TC) return deg(off, y);                            // T(x,y), E(y,z)
-  if (iter == 0) {                                                    // E(p,x), E(p,y), x != y
-    const unsigned long long d = deg(off, x);
-    return d ? d * (d - 1) : 0ull;
-  }
-  return (unsigned long long)deg(off, x) * deg(off, y);               // E(a,x), sg(a,b), E(b,y)
-}
-
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
-  constexpr int kItemsK = CountTile<K>::T / kThreads, kTileK = CountTile<K>::T;
-  __shared__ K sd[kTileK];
-  __shared__ unsigned long long sp[kTileK];
+  __shared__ K sd[kTileD];
+  __shared__ unsigned long long sp[kTileD];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_excl;
   __shared__ uint32_t s_t, s_bad;
@@ -92,35 +80,49 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
     const uint32_t* off = I->off;
     const uint32_t w = I->w, kind = I->kind, iter = I->iter;
     const K mask = (K)(((K)1 << w) - 1);
-    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileK;
-    const uint32_t n = (uint32_t)min((unsigned long long)kTileK, sg.n - start);
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileD;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTileD, sg.n - start);
     const K* p = D + sg.in_off + start;
-    tile_to_smem<kItemsK>(sd, p, n, Ident());
+    tile_to_smem<kItemsD>(sd, p, n, Ident());
     if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    const uint32_t b = threadIdx.x * kItemsK;
-    unsigned long long sum = 0;
-    uint32_t px = 0xFFFFFFFFu;
-    unsigned long long run = 0;
-#pragma unroll 4
-    for (int i = 0; i < kItemsK; ++i) {
+    const uint32_t b = threadIdx.x * kItemsD;
+    unsigned long long c[kItemsD], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kItemsD; ++i) {
+      c[i] = 0;
       if (b + i < n) {
         const K key = sd[b + i];
         const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
-        const unsigned long long c = slab_size(off, kind, iter, x, y);
-        sp[b + i] = c;
-        sum += c;
-        if (stp->xlen) {  // candidates per source x (Delta is sorted by x: one atomic per run)
+        if (kind == KIND_TC) {
+          c[i] = deg(off, y);                                  // T(x,y), E(y,z)
+        } else if (iter == 0) {
+          const unsigned long long d = deg(off, x);            // E(p,x), E(p,y), x != y
+          c[i] = d ? d * (d - 1) : 0;
+        } else {
+          c[i] = (unsigned long long)deg(off, x) * deg(off, y);  // E(a,x), sg(a,b), E(b,y)
+        }
+        sum += c[i];
+      }
+    }
+    if (stp->xlen) {
+      // candidates per source x (Delta is sorted by x: one atomic per run)
+      uint32_t px = 0xFFFFFFFFu;
+      unsigned long long run = 0;
+#pragma unroll
+      for (int i = 0; i < kItemsD; ++i) {
+        if (b + i < n) {
+          const uint32_t x = (uint32_t)(sd[b + i] >> w);
           if (x != px) {
             if (run) atomicAdd(stp->xlen + px, run);
             px = x;
             run = 0;
           }
-          run += c;
+          run += c[i];
         }
       }
+      if (run) atomicAdd(stp->xlen + px, run);
     }
-    if (run) atomicAdd(stp->xlen + px, run);
     unsigned long long tot;
     const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);
     const bool first = (t == sg.tile0);
@@ -137,14 +139,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
     }
     __syncthreads();
     if (s_bad) return;
-    unsigned long long runp = s_excl + texcl;
-#pragma unroll 4
-    for (int i = 0; i < kItemsK; ++i)
-      if (b + i < n) {
-        const unsigned long long c = sp[b + i];
-        sp[b + i] = runp;
-        runp += c;
-      }
+    unsigned long long run = s_excl + texcl;
+#pragma unroll
+    for (int i = 0; i < kItemsD; ++i)
+      if (b + i < n) { sp[b + i] = run; run += c[i]; }
     __syncthreads();
     unsigned long long* q = pos + sg.in_off + start;
     for (uint32_t i = threadIdx.x; i < n; i += kThreads) q[i] = sp[i];
@@ -154,16 +152,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
 
 // ------------------------------------------------------------------ join emit
 // Load-balanced over output positions: a tile is kTileC consecutive
-// candidates of one instance, a warp owns 32*kItemsC of them and lane l
-// produces every 32nd one starting at l.  Consecutive lanes write consecutive
-// candidates and read consecutive adjacency entries of the same slab, so both
-// sides are coalesced.  Each lane finds the delta tuple (join slab) of its
-// first candidate by binary search, then walks forward, keeping the slab's
-// CSR range in registers.
+// candidates of one instance.  Thread t produces the kItemsC consecutive
+// candidates [t*kItemsC, (t+1)*kItemsC) of the tile: one binary search finds
+// the delta tuple (join slab) holding its first candidate, then it walks the
+// slabs sequentially, keeping the slab's CSR range in registers.  Candidates
+// go through shared memory so that the global stores are coalesced.
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
-  __shared__ unsigned long long spos[kEmitWin];
-  __shared__ K skey[kEmitWin];
+__global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
+  constexpr int kStageBytes = kEmitWin * (8 + (int)sizeof(K));
+  constexpr int kOutBytes = kTileC * (int)sizeof(K) + (kTileC / 32 + 1) * (int)sizeof(K);
+  __shared__ __align__(16) unsigned char smem[kStageBytes > kOutBytes ? kStageBytes : kOutBytes];
+  unsigned long long* spos = (unsigned long long*)smem;
+  K* skey = (K*)(smem + kEmitWin * 8);
+  K* sout = (K*)smem;  // reused once every thread holds its candidates
   __shared__ unsigned long long s_i0, s_i1;
   __shared__ uint32_t s_t;
   Ctl* ctl = stp->ctl;
@@ -172,7 +173,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
   K* C = (K*)stp->out;
   const unsigned long long* pos_all = stp->pos;
   const uint32_t nseg = stp->nseg, ntiles = stp->ntiles;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
     const uint32_t t = claim_tile(stp, &s_t);
     if (t >= ntiles) return;
@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     __syncthreads();
     auto posat = [&](unsigned long long i) { return staged ? spos[i] : P[i0 + i]; };
     auto keyat = [&](unsigned long long i) { return staged ? skey[i] : Dq[i0 + i]; };
-    const uint32_t q0 = warp * 32 * kItemsC + lane;
+    K out[kItemsC];
+    const uint32_t q0 = threadIdx.x * kItemsC;
     if (q0 < nout) {
       const unsigned long long o = o0 + q0;
       unsigned long long lo = 0, hi = m;  // largest i with pos[i] <= o
@@ -223,39 +224,43 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
       K key = keyat(i);
       uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
       uint32_t ox = off[x], oy = off[y], dy = off[y + 1] - oy, dx = off[x + 1] - ox;
-      K* Cq = C + sg.out_off + o0;
-#pragma unroll 4
+#pragma unroll
       for (int e = 0; e < kItemsC; ++e) {
-        const uint32_t q = q0 + e * 32;
-        if (q >= nout) break;
-        const unsigned long long oe = o0 + q;
-        while (oe >= nextb) {  // the slab holding oe
-          ++i;
-          base = nextb;
-          nextb = i + 1 < m ? posat(i + 1) : ~0ull;
-          if (oe < nextb) {
-            key = keyat(i);
-            x = (uint32_t)(key >> w); y = (uint32_t)(key & mask);
-            ox = off[x]; oy = off[y]; dy = off[y + 1] - oy; dx = off[x + 1] - ox;
+        out[e] = 0;
+        const unsigned long long oe = o + e;
+        if (q0 + e < nout) {
+          while (oe >= nextb) {  // next non-empty slab
+            ++i;
+            base = nextb;
+            nextb = i + 1 < m ? posat(i + 1) : ~0ull;
+            if (oe < nextb) {
+              key = keyat(i);
+              x = (uint32_t)(key >> w); y = (uint32_t)(key & mask);
+              ox = off[x]; oy = off[y]; dy = off[y + 1] - oy; dx = off[x + 1] - ox;
+            }
+          }
+          const uint32_t r = (uint32_t)(oe - base);
+          if (kind == KIND_TC) {
+            out[e] = ((K)x << w) | (K)adj[oy + r];                       // T(x,y), E(y,z)
+          } else if (iter == 0) {
+            const uint32_t dm1 = dx - 1;                                  // distinct children of x
+            const uint32_t qa = r / dm1;
+            uint32_t qb = r - qa * dm1;
+            qb += qb >= qa;
+            out[e] = ((K)adj[ox + qa] << w) | (K)adj[ox + qb];
+          } else {
+            const uint32_t qa = r / dy, qb = r - qa * dy;                  // E(a,x), sg(a,b), E(b,y)
+            out[e] = ((K)adj[ox + qa] << w) | (K)adj[oy + qb];
           }
         }
-        const uint32_t r = (uint32_t)(oe - base);
-        K v;
-        if (kind == KIND_TC) {
-          v = ((K)x << w) | (K)adj[oy + r];                             // T(x,y), E(y,z)
-        } else if (iter == 0) {
-          const uint32_t dm1 = dx - 1;                                   // distinct children of x
-          const uint32_t qa = r / dm1;
-          uint32_t qb = r - qa * dm1;
-          qb += qb >= qa;
-          v = ((K)adj[ox + qa] << w) | (K)adj[ox + qb];
-        } else {
-          const uint32_t qa = r / dy, qb = r - qa * dy;                   // E(a,x), sg(a,b), E(b,y)
-          v = ((K)adj[ox + qa] << w) | (K)adj[oy + qb];
-        }
-        Cq[q] = v;
       }
     }
+    __syncthreads();  // staging arrays are dead: reuse the space for the output
+#pragma unroll
+    for (int e = 0; e < kItemsC; ++e) sout[pad32(q0 + e)] = out[e];
+    __syncthreads();
+    K* Cq = C + sg.out_off + o0;
+    for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
   }
 }
 
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     const Inst* I = valid ? dv->inst + q : nullptr;
     const bool act = valid && I->state == INST_ACTIVE;
     const unsigned long long nd = act ? I->n_delta : 0ull;
-    const unsigned long long nt = (nd + dv->count_tile - 1) / dv->count_tile;
+    const unsigned long long nt = (nd + kTileD - 1) / kTileD;
     unsigned long long tot;
     const unsigned long long ex = scan1024(nt, sh, &tot);
     if (valid) {
