@@ -17,6 +17,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/wg.h"
@@ -86,6 +87,7 @@ struct wg_ctx {
   std::map<int, std::unique_ptr<EngineBase>> batch;  // batch engines by key class
   std::vector<uint64_t> pending;                  // submitted, not yet admitted
   std::vector<uint64_t> completed;                // batch queries finished, not yet taken
+  cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
   unsigned long long* s_status = nullptr; size_t s_status_n = 0;
@@ -96,7 +98,7 @@ struct wg_ctx {
   uint32_t s_epoch = 0;
 };
 
-static int dev_alloc(wg_ctx* c, size_t bytes, void** out) {
+static int dev_alloc(wg_ctx* c, size_t bytes, void** out, cudaStream_t st) {
   *out = nullptr;
   if (bytes == 0) return WG_OK;
   bytes = round_up(bytes);
@@ -105,8 +107,8 @@ static int dev_alloc(wg_ctx* c, size_t bytes, void** out) {
                                     " bytes exceeds the memory budget");
   void* p = nullptr;
   if (c->alloc) {
-    p = c->alloc(bytes, (void*)c->stream, c->user);
-  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    p = c->alloc(bytes, (void*)st, c->user);
+  } else if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
   }
@@ -115,26 +117,41 @@ static int dev_alloc(wg_ctx* c, size_t bytes, void** out) {
   *out = p;
   return WG_OK;
 }
-static void dev_free(wg_ctx* c, void* p, size_t bytes) {
+static int dev_alloc(wg_ctx* c, size_t bytes, void** out) {
+  return dev_alloc(c, bytes, out, c->alloc_stream ? c->alloc_stream : c->stream);
+}
+static void dev_free(wg_ctx* c, void* p, size_t bytes, cudaStream_t st) {
   if (!p) return;
   bytes = round_up(bytes);
-  if (c->free_fn) c->free_fn(p, bytes, (void*)c->stream, c->user);
-  else cudaFreeAsync(p, c->stream);
+  if (c->free_fn) c->free_fn(p, bytes, (void*)st, c->user);
+  else cudaFreeAsync(p, st);
   c->used -= bytes;
 }
+static void dev_free(wg_ctx* c, void* p, size_t bytes) { dev_free(c, p, bytes, c->stream); }
+
+// Allocations made inside this scope are stream-ordered on `st` (an engine's
+// own stream), and their buffers are later freed on it.
+struct AllocScope {
+  wg_ctx* c;
+  cudaStream_t prev;
+  AllocScope(wg_ctx* c_, cudaStream_t st) : c(c_), prev(c_->alloc_stream) { c->alloc_stream = st; }
+  ~AllocScope() { c->alloc_stream = prev; }
+};
 
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t st = nullptr;  // the stream the buffer was allocated on
   int get(wg_ctx* c, size_t b) {
     if (b <= bytes && p) return WG_OK;
     release(c);
-    TRY(dev_alloc(c, b, &p));
+    st = c->alloc_stream ? c->alloc_stream : c->stream;
+    TRY(dev_alloc(c, b, &p, st));
     bytes = round_up(b);
     return WG_OK;
   }
   void release(wg_ctx* c) {
-    dev_free(c, p, bytes);
+    dev_free(c, p, bytes, st ? st : c->stream);
     p = nullptr;
     bytes = 0;
   }
@@ -387,6 +404,8 @@ struct Query {
 template <typename K>
 struct Engine : EngineBase {
   wg_ctx* c;
+  cudaStream_t st = nullptr;  // the engine's stream (the context stream for single queries)
+  bool own_st = false;
   bool single, fuse, xseg;
   uint32_t nv_cap = 0;  // vertices the x-grouped sort buffers can hold
   uint32_t n_slots, bits_, passes, dbits;
@@ -420,6 +439,7 @@ struct Engine : EngineBase {
   uint32_t slots() const override { return n_slots; }
 
   void release() override {
+    if (st) cudaStreamSynchronize(st);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr; graph = nullptr;
@@ -428,9 +448,24 @@ struct Engine : EngineBase {
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
                    &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b};
     for (DBuf* b : all) b->release(c);
+    if (own_st && st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+      st = nullptr;
+      own_st = false;
+    }
   }
 
   int init() {
+    if (!st) {
+      if (single) {
+        st = c->stream;
+      } else {  // batch engines run on their own stream, concurrently with each other
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        own_st = true;
+      }
+    }
+    AllocScope scope(c, st);
     TRY(b_dev.get(c, sizeof(Dev)));
     TRY(b_inst.get(c, sizeof(Inst) * n_slots));
     TRY(b_seg.get(c, sizeof(Seg) * n_slots * 6));
@@ -438,7 +473,7 @@ struct Engine : EngineBase {
     TRY(hist.get(c, sizeof(unsigned long long) * (size_t)n_slots * passes * kRadix));
     dv = (Dev*)b_dev.p;
     hi.assign(n_slots, Inst{});
-    CK(cudaMemsetAsync(b_inst.p, 0, sizeof(Inst) * n_slots, c->stream));
+    CK(cudaMemsetAsync(b_inst.p, 0, sizeof(Inst) * n_slots, st));
     std::memset(&h, 0, sizeof(h));
     h.inst = (Inst*)b_inst.p;
     Seg* s = (Seg*)b_seg.p;
@@ -450,7 +485,7 @@ struct Engine : EngineBase {
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
     h.ctl.iter_budget = 0xFFFFFFFFu;
-    CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, st));
     CK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
     g_count = grid_of(c, occupancy_join<K>(0));
     g_emit = grid_of(c, occupancy_join<K>(1));
@@ -476,7 +511,7 @@ struct Engine : EngineBase {
     h.segX = (Seg*)segx_b.p;
     h.tile_seg = (uint32_t*)tseg_b.p;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
-    CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
 
@@ -484,6 +519,7 @@ struct Engine : EngineBase {
   // retired results) is copied into the new buffers.
   int ensure(unsigned long long wantC, unsigned long long wantF, unsigned long long wantR,
              bool keep) {
+    AllocScope scope(c, st);
     wantC = std::max<unsigned long long>(wantC, 1ull << 16);
     wantF = std::max<unsigned long long>(wantF, 1ull << 16);
     wantR = single ? 0 : std::max<unsigned long long>(wantR, 1ull << 16);
@@ -510,10 +546,10 @@ struct Engine : EngineBase {
       if (rc == WG_OK) rc = np.get(c, wantC * 8);
       if (rc == WG_OK) rc = nk.get(c, (wantC / kTileC + std::max(n_slots, nv_cap) + 2) * kRadix * 8);
       if (rc != WG_OK) return undo(rc);
-      CK(cudaMemsetAsync(nk.p, 0, nk.bytes, c->stream));
+      CK(cudaMemsetAsync(nk.p, 0, nk.bytes, st));
       if (liveD)
         CK(cudaMemcpyAsync(nd[h.dphase].p, D[h.dphase].p, liveD * sizeof(K),
-                           cudaMemcpyDeviceToDevice, c->stream));
+                           cudaMemcpyDeviceToDevice, st));
       for (int i = 0; i < 2; ++i) {
         D[i].release(c); C[i].release(c);
         D[i] = nd[i]; C[i] = nc[i];
@@ -526,7 +562,7 @@ struct Engine : EngineBase {
         TRY(tseg_b.get(c, (capC / kTileC + nv_cap + 2) * 4));
       }
       h.ctl.epoch = 0;
-      if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+      if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
     }
     if (wantF > capF) {
       DBuf nf[2];
@@ -535,7 +571,7 @@ struct Engine : EngineBase {
       if (rc != WG_OK) { nf[0].release(c); nf[1].release(c); return rc; }
       if (liveF)
         CK(cudaMemcpyAsync(nf[h.fphase].p, F[h.fphase].p, liveF * sizeof(K),
-                           cudaMemcpyDeviceToDevice, c->stream));
+                           cudaMemcpyDeviceToDevice, st));
       for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
       capF = wantF;
     }
@@ -546,16 +582,16 @@ struct Engine : EngineBase {
         spl.release(c);
         TRY(st_s.get(c, tiles * 8));
         TRY(spl.get(c, (tiles + 1) * 8));
-        CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+        CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
         h.ctl.epoch = 0;
-        CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+        CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
       }
     }
     if (!single && wantR > capR) {
       DBuf nr;
       TRY(nr.get(c, wantR * sizeof(K)));  // nothing else is held on this path
       if (keep && h.r_used)
-        CK(cudaMemcpyAsync(nr.p, R.p, h.r_used * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(nr.p, R.p, h.r_used * sizeof(K), cudaMemcpyDeviceToDevice, st));
       R.release(c);
       R = nr;
       capR = wantR;
@@ -623,7 +659,7 @@ struct Engine : EngineBase {
     if (e != cudaSuccess) return set_err(WG_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     CK(cudaGraphInstantiate(&exec, graph, 0));
     h.cond = (unsigned long long)cond;
-    CK(cudaMemcpyAsync(&dv->cond, &h.cond, sizeof(h.cond), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&dv->cond, &h.cond, sizeof(h.cond), cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
 
@@ -632,22 +668,22 @@ struct Engine : EngineBase {
     h.ctl.iter_budget = budget;
     h.ctl.need_cand = h.ctl.need_full = h.ctl.need_res = 0;
     if (h.ctl.epoch > (1u << 22)) {  // clear lookback words before the epoch wraps
-      CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
-      CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+      CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
+      CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
       h.ctl.epoch = 0;
     }
-    CK(cudaMemcpyAsync(&dv->ctl, &h.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&dv->ctl, &h.ctl, sizeof(Ctl), cudaMemcpyHostToDevice, st));
     h.use_cond = use_cond ? 1 : 0;
-    CK(cudaMemcpyAsync(&dv->use_cond, &h.use_cond, 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&dv->use_cond, &h.use_cond, 4, cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
 
   int read_back() {
-    CK(cudaMemcpyAsync(&h.ctl, &dv->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&h.r_used, &dv->r_used, sizeof(h.r_used), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&h.dphase, &dv->dphase, 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(hi.data(), b_inst.p, sizeof(Inst) * n_slots, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(&h.ctl, &dv->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h.r_used, &dv->r_used, sizeof(h.r_used), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&h.dphase, &dv->dphase, 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hi.data(), b_inst.p, sizeof(Inst) * n_slots, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return WG_OK;
   }
 
@@ -656,20 +692,20 @@ struct Engine : EngineBase {
     if (host_loop) {
       TRY(put_ctl(budget, false));
       for (;;) {
-        launch_iteration(c->stream);
+        launch_iteration(st);
         launches_issued += kernels_per_iter();
         uint32_t cont = 0;
-        CK(cudaMemcpyAsync(&cont, &dv->ctl.cont, 4, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));  // the per-iteration host sync
+        CK(cudaMemcpyAsync(&cont, &dv->ctl.cont, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));  // the per-iteration host sync
         if (!cont) break;
       }
       CK(cudaGetLastError());
     } else {
       TRY(capture());
       TRY(put_ctl(budget, true));
-      CK(cudaGraphLaunch(exec, c->stream));
+      CK(cudaGraphLaunch(exec, st));
     }
-    CK(cudaEventRecord(ev_done, c->stream));
+    CK(cudaEventRecord(ev_done, st));
     in_flight = true;
     return WG_OK;
   }
@@ -696,6 +732,7 @@ struct Engine : EngineBase {
   // Buffers of the x-grouped sort for relations of up to nv vertices.
   int ensure_nv(uint32_t nv) {
     if (!xseg || nv <= nv_cap) return WG_OK;
+    AllocScope scope(c, st);
     xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c); tseg_b.release(c);
     TRY(xlen_b.get(c, (size_t)nv * 8));
     TRY(segx_b.get(c, (size_t)nv * sizeof(Seg)));
@@ -703,9 +740,9 @@ struct Engine : EngineBase {
     TRY(st_k.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8));
     tseg_b.release(c);
     TRY(tseg_b.get(c, (capC / kTileC + nv + 2) * 4));
-    CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, c->stream));
+    CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
     h.ctl.epoch = 0;
-    if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, c->stream));
+    if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
     nv_cap = nv;
     return put_pools();
   }
@@ -723,7 +760,7 @@ struct Engine : EngineBase {
     I.state = INST_FREE;
     I.n_delta = 0; I.n_full = 0;
     hi[slot] = I;
-    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
 
@@ -743,18 +780,18 @@ struct Engine : EngineBase {
     I.log_cap = log_cap;
     I.fresh = 1;
     hi[slot] = I;
-    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync((Inst*)b_inst.p + slot, &I, sizeof(Inst), cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
   int init_deltas(uint32_t first, uint32_t count) {
-    launch_init_diag<K>((Inst*)b_inst.p, first, count, D[h.dphase].p, c->stream);
+    launch_init_diag<K>((Inst*)b_inst.p, first, count, D[h.dphase].p, st);
     CK(cudaGetLastError());
     return WG_OK;
   }
   int reset_single() {
     h.dphase = 0; h.fphase = 0; h.r_used = 0;
-    CK(cudaMemcpyAsync(&dv->r_used, &h.r_used, sizeof(h.r_used), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(&dv->dphase, &h.dphase, 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(&dv->r_used, &h.r_used, sizeof(h.r_used), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(&dv->dphase, &h.dphase, 8, cudaMemcpyHostToDevice, st));
     return WG_OK;
   }
   const void* pool_ptr(uint32_t pool) const {
@@ -912,8 +949,15 @@ static int single_progress(wg_ctx* c, Query* q, bool block) {
 // ------------------------------------------------------------------ batches
 // Key classes of batch engines: 32-bit keys (fields <= 16 bits), 64-bit keys
 // with fields <= 24 bits, 64-bit keys with fields <= 32 bits.
-static int batch_class(const Relation* R) { return R->kb == 4 ? 0 : (R->w <= 24 ? 1 : 2); }
-static uint32_t class_bits(int cls) { return cls == 0 ? 32 : (cls == 1 ? 48 : 64); }
+// Queries are also split by size: small ones (<= kSmallVertices vertices) and
+// large ones run in different engines on different streams, so the short
+// iterations of small queries never wait for the long ones of large queries.
+constexpr uint32_t kSmallVertices = 4096;
+static int batch_class(const Relation* R) {
+  const int key = R->kb == 4 ? 0 : (R->w <= 24 ? 1 : 2);
+  return key * 2 + (R->nv > kSmallVertices ? 1 : 0);
+}
+static uint32_t class_bits(int cls) { return cls / 2 == 0 ? 32 : (cls / 2 == 1 ? 48 : 64); }
 constexpr uint32_t kBatchSlots = 1024;    // queries running at once per key class
 constexpr uint32_t kBatchLogCap = 1024;   // per-iteration delta sizes kept per query
 
@@ -1036,8 +1080,12 @@ static int batch_retire(wg_ctx* c, int cls) {
     q->candidates = done.cand_total;
     const uint32_t nlog = std::min<uint32_t>(done.iters_done + 1, E->log_cap);
     q->log.assign(nlog, 0);
-    CK(cudaMemcpyAsync(q->log.data(), done.log, nlog * 8, cudaMemcpyDeviceToHost, c->stream));
-    int rc = q->res_own.get(c, std::max<size_t>(done.n_full, 1) * sizeof(K));
+    CK(cudaMemcpyAsync(q->log.data(), done.log, nlog * 8, cudaMemcpyDeviceToHost, E->st));
+    int rc;
+    {
+      AllocScope scope(c, E->st);
+      rc = q->res_own.get(c, std::max<size_t>(done.n_full, 1) * sizeof(K));
+    }
     if (rc != WG_OK) {
       q->state = WG_FAILED;
       q->error = rc;
@@ -1047,7 +1095,7 @@ static int batch_retire(wg_ctx* c, int cls) {
     }
     if (done.n_full)
       CK(cudaMemcpyAsync(q->res_own.p, (const K*)E->pool_ptr(done.res_pool) + done.res_off,
-                         done.n_full * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
+                         done.n_full * sizeof(K), cudaMemcpyDeviceToDevice, E->st));
     q->res_ptr = q->res_own.p;
     q->state = done.state == INST_DONE ? WG_DONE : WG_FAILED;
     q->error = done.state == INST_DONE ? WG_OK : WG_E_ITER_CAP;
@@ -1056,8 +1104,8 @@ static int batch_retire(wg_ctx* c, int cls) {
   }
   // every retired result has been copied out: the retire pool starts over
   E->h.r_used = 0;
-  CK(cudaMemcpyAsync(&E->dv->r_used, &E->h.r_used, 8, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(&E->dv->r_used, &E->h.r_used, 8, cudaMemcpyHostToDevice, E->st));
+  CK(cudaStreamSynchronize(E->st));
   return WG_OK;
 }
 
@@ -1081,13 +1129,14 @@ static void batch_fail_all(wg_ctx* c, int cls, int rc) {
 // One scheduling round: finish the launch in flight (grow or preempt after an
 // overflow, retire finished queries), admit queued queries, launch again.
 template <typename K>
-static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
+static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch, bool* progressed) {
   auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
   if (E->in_flight) {
     if (!wait_launch) {
       cudaError_t e = cudaEventQuery(E->ev_done);
       if (e == cudaErrorNotReady) return WG_OK;
     }
+    *progressed = true;
     CK(cudaEventSynchronize(E->ev_done));
     E->in_flight = false;
     TRY(E->read_back());
@@ -1114,14 +1163,44 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
   TRY(batch_admit<K>(c, cls));
   bool any = false;
   for (const Inst& I : E->hi) any |= I.state == INST_ACTIVE;
-  if (any) TRY(E->launch(iters, false));
+  if (any) {
+    TRY(E->launch(iters, false));
+    *progressed = true;
+  }
   return WG_OK;
 }
 
-static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch) {
+static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch,
+                           bool* progressed) {
   if (!c->batch[cls]) return WG_OK;
-  return c->batch[cls]->kb() == 4 ? batch_round<uint32_t>(c, cls, iters, wait_launch)
-                                   : batch_round<unsigned long long>(c, cls, iters, wait_launch);
+  return c->batch[cls]->kb() == 4
+             ? batch_round<uint32_t>(c, cls, iters, wait_launch, progressed)
+             : batch_round<unsigned long long>(c, cls, iters, wait_launch, progressed);
+}
+
+static bool batch_busy(wg_ctx* c) {
+  for (auto& kv : c->batch) {
+    if (!kv.second) continue;
+    const bool fl = kv.second->kb() == 4 ? static_cast<Engine<uint32_t>*>(kv.second.get())->in_flight
+                                         : static_cast<Engine<unsigned long long>*>(kv.second.get())->in_flight;
+    if (fl) return true;
+  }
+  return false;
+}
+
+// One serving round over every batch engine, without waiting on one engine
+// while another could run: engines whose launch finished are retired,
+// admitted and relaunched; if none had finished, wait briefly and retry.
+static int serve_round(wg_ctx* c, uint32_t iters) {
+  for (int spin = 0;; ++spin) {
+    bool progressed = false;
+    for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, iters, false, &progressed));
+    if (progressed || !batch_busy(c)) return WG_OK;
+    if (spin > 200000) {  // ~10 s without any engine finishing a launch
+      return set_err(WG_E_DEVICE_TIMEOUT, "no batch launch finished");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
 }
 
 static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
@@ -1137,7 +1216,8 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   // start with pools worth about a third of the free budget; they grow later
   // only as far as the budget allows (then the largest instance is preempted)
   const double per_key = 4.0 * R->kb + 8.5 + 2.0 * R->kb + R->kb / 4.0;
-  const double avail = (double)(c->budget - c->used) / 3.0;
+  const bool small = (cls & 1) == 0;  // small-query engines need far smaller pools
+  const double avail = (double)(c->budget - c->used) / (small ? 8.0 : 3.0);
   const unsigned long long capC = std::max<unsigned long long>(1ull << 20, (unsigned long long)(avail / per_key));
   if (R->kb == 4)
     return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 4, false);
@@ -1368,7 +1448,7 @@ int wg_submit(wg_ctx* c, const wg_request* reqs, size_t n, wg_query* ids) {
 int wg_serve_step(wg_ctx* c, uint32_t iters, size_t* n_running) {
   if (!c) return set_err(WG_E_INVAL, "ctx is NULL");
   if (iters == 0) iters = 0xFFFFFFFFu;
-  for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, iters, true));
+  TRY(serve_round(c, iters));
   if (n_running) {
     size_t r = 0;
     for (auto& kv : c->queries) r += kv.second->batch && kv.second->state == WG_RUNNING;
@@ -1394,10 +1474,13 @@ static Query* find_q(wg_ctx* c, wg_query id) {
 static int progress(wg_ctx* c, Query* q, bool block) {
   if (q->state == WG_DONE || q->state == WG_FAILED) return WG_OK;
   if (q->batch) {
-    // drive the batch engine until this query is retired
-    do {
-      for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, 0xFFFFFFFFu, block));
-    } while (block && q->state != WG_DONE && q->state != WG_FAILED);
+    // drive the batch engines until this query is retired
+    if (!block) {
+      bool progressed = false;
+      for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, 0xFFFFFFFFu, false, &progressed));
+      return WG_OK;
+    }
+    while (q->state != WG_DONE && q->state != WG_FAILED) TRY(serve_round(c, 0xFFFFFFFFu));
     return WG_OK;
   }
   return q->eng->kb() == 4 ? single_progress<uint32_t>(c, q, block)
