@@ -1218,7 +1218,7 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   const double per_key = 4.0 * R->kb + 8.5 + 2.0 * R->kb + R->kb / 4.0;
   const bool small = (cls & 1) == 0;  // small-query engines need far smaller pools
   const double avail = (double)(c->budget - c->used) / (small ? 8.0 : 3.0);
-  const unsigned long long capC = std::max<unsigned long long>(1ull << 20, (unsigned long long)(avail / per_key));
+  const unsigned long long capC = std::max<unsigned long long>(1ull << 16, (unsigned long long)(avail / per_key));
   if (R->kb == 4)
     return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 4, false);
   return static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 4, false);

@@ -128,9 +128,9 @@ def test_preemption_under_small_budget():
 
 def test_query_larger_than_budget_fails_cleanly():
     from paper_2607_17571_gb300 import wg
-    g = I.er_graph(8000, 24000, 5)             # ~5e7 tuples: far beyond an 80 MB budget
+    g = I.er_graph(10000, 30000, 5)            # ~9e7 tuples: far beyond a 160 MB budget
     small = I.er_graph(200, 500, 6)
-    with wg.Context(0, mem_budget=80 << 20) as c:
+    with wg.Context(0, mem_budget=160 << 20) as c:
         big_rel, small_rel = c.load(g.src, g.dst), c.load(small.src, small.dst)
         hb, hs = c.submit([(wg.WG_TC, big_rel), (wg.WG_TC, small_rel)])
         with pytest.raises(wg.WgError) as e:
