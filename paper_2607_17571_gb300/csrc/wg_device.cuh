@@ -115,6 +115,12 @@ template <typename K> struct FuseTile {
   static constexpr int E = T / kThreads;
 };
 
+// x-grouped sort: relations of up to kXSegMaxVertices vertices, segment
+// records built by chunks of kXChunk source vertices.
+constexpr uint32_t kXSegMaxVertices = 1u << 18;
+constexpr uint32_t kXChunk = 256;
+constexpr uint32_t kXChunks = kXSegMaxVertices / kXChunk;
+
 // Device-resident state of one engine: pools, the instance table, the stage
 // records the plan kernels write, and the graph conditional handle.  Pools are
 // reached through this block only, so growing a pool never re-captures the graph.
@@ -141,6 +147,7 @@ struct Dev {
   unsigned long long* xlen;           // candidates per source vertex (x-grouped sort)
   Seg* segX;                          // one sort segment per source vertex
   uint32_t* tile_seg;                 // tile -> x-segment map of the x-grouped sort
+  unsigned long long* xsum;           // [kXChunks][2]: candidates and tiles per chunk of x
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;

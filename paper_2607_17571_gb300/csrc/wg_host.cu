@@ -68,7 +68,6 @@ struct EngineBase;
 
 // Largest vertex count for which single TC queries sort per source vertex
 // (per-vertex digit histograms: 512 counters of 8 bytes per vertex and pass).
-constexpr uint32_t kXSegMaxVertices = 1u << 18;
 
 // ------------------------------------------------------------------ context
 struct wg_ctx {
@@ -413,7 +412,7 @@ struct Engine : EngineBase {
   Dev h{};             // host mirror (read back after each run)
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
-  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b, xsum_b;
   unsigned long long capC = 0, capF = 0, capR = 0;
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
@@ -423,7 +422,7 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 1 : 0); }
+  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 2 : 0); }
 
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
          bool xseg_)
@@ -446,7 +445,7 @@ struct Engine : EngineBase {
     if (ev_done) cudaEventDestroy(ev_done);
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
-                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b};
+                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b, &xsum_b};
     for (DBuf* b : all) b->release(c);
     if (own_st && st) {
       cudaStreamSynchronize(st);
@@ -510,6 +509,7 @@ struct Engine : EngineBase {
     h.xlen = (unsigned long long*)xlen_b.p;
     h.segX = (Seg*)segx_b.p;
     h.tile_seg = (uint32_t*)tseg_b.p;
+    h.xsum = (unsigned long long*)xsum_b.p;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, st));
     return WG_OK;
@@ -735,6 +735,7 @@ struct Engine : EngineBase {
     AllocScope scope(c, st);
     xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c); tseg_b.release(c);
     TRY(xlen_b.get(c, (size_t)nv * 8));
+    if (!xsum_b.p) TRY(xsum_b.get(c, (size_t)kXChunks * 2 * 8));
     TRY(segx_b.get(c, (size_t)nv * sizeof(Seg)));
     TRY(hist.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8));
     TRY(st_k.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8));
@@ -1228,7 +1229,15 @@ template <typename K>
 static int copy_result(wg_ctx* c, Query* q, unsigned long long* dst, bool host) {
   const size_t n = q->n_tuples;
   if (!n) return WG_OK;
-  const size_t chunk = host ? (size_t)1 << 24 : n;
+  // a page-locked destination takes large DMA chunks; pageable memory is
+  // staged by the driver anyway, so keep the device buffer small there
+  bool locked = false;
+  if (host) {
+    cudaPointerAttributes pa{};
+    locked = cudaPointerGetAttributes(&pa, dst) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+    cudaGetLastError();  // pageable pointers are not an error
+  }
+  const size_t chunk = host ? (size_t)1 << (locked ? 26 : 24) : n;
   DBuf tmp;
   if (host) TRY(tmp.get(c, std::min(n, chunk) * 8));
   for (size_t at = 0; at < n; at += chunk) {

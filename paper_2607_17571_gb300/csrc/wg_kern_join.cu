@@ -152,21 +152,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
 
 // ------------------------------------------------------------------ join emit
 // Load-balanced over output positions: a tile is kTileC consecutive
-// candidates of one instance.  Thread t produces the kItemsC consecutive
-// candidates [t*kItemsC, (t+1)*kItemsC) of the tile: one binary search finds
-// the delta tuple (join slab) holding its first candidate, then it walks the
-// slabs sequentially, keeping the slab's CSR range in registers.  Candidates
-// go through shared memory so that the global stores are coalesced.
+// candidates of one instance, made in three rounds of memory traffic.
+//  1. The delta tuples whose slabs cover the tile -- from the slab owner of
+//     the tile's first candidate to that of the next tile's first -- become a
+//     slab table in shared memory: tile-relative slab start, and the CSR
+//     offsets the slab reads (every load of the round in flight at once).
+//  2. Thread t walks the table for its kItemsC consecutive candidates
+//     (shared memory only), then issues all their adjacency loads at once.
+//  3. Candidates go through shared memory so the global stores coalesce.
+// A tile covering more than kEmitWin delta tuples (long runs of empty slabs)
+// walks the delta tuples in global memory instead.
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
-  constexpr int kStageBytes = kEmitWin * (8 + (int)sizeof(K));
-  constexpr int kOutBytes = kTileC * (int)sizeof(K) + (kTileC / 32 + 1) * (int)sizeof(K);
-  __shared__ __align__(16) unsigned char smem[kStageBytes > kOutBytes ? kStageBytes : kOutBytes];
-  unsigned long long* spos = (unsigned long long*)smem;
-  K* skey = (K*)(smem + kEmitWin * 8);
-  K* sout = (K*)smem;  // reused once every thread holds its candidates
+__global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
+  constexpr int kSlabBytes = kEmitWin * 4 * (int)sizeof(uint32_t);
+  constexpr int kOutBytes = Padded<kTileC>::n * (int)sizeof(K);
+  __shared__ __align__(16) unsigned char smem[kSlabBytes > kOutBytes ? kSlabBytes : kOutBytes];
+  uint32_t* s_start = (uint32_t*)smem;  // slab's first candidate, relative to the tile
+  uint32_t* s_x = s_start + kEmitWin;   // TC: x            SG: off[x]
+  uint32_t* s_a = s_x + kEmitWin;       // TC: adj index of the slab's candidate 0 of the tile
+                                        // SG: off[y] (recursive rule)
+  uint32_t* s_d = s_a + kEmitWin;       // SG: divisor that splits a slab index in two
+  K* sout = (K*)smem;                   // reused once every thread holds its candidates
   __shared__ unsigned long long s_i0, s_i1;
-  __shared__ uint32_t s_t;
+  __shared__ uint32_t s_r0, s_t;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   const K* D = (const K*)stp->in;
@@ -188,9 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
     const unsigned long long o0 = (unsigned long long)(t - sg.tile0) * kTileC;
     const unsigned long long o1 = min(o0 + kTileC, sg.aux_n);
     const uint32_t nout = (uint32_t)(o1 - o0);
-    // delta tuples whose slabs cover [o0, o1): from the slab owner of o0 to
-    // (at most) the slab owner of o1; tuples past the last owner start at or
-    // after o1 and are never chosen
+    // delta tuples i0..i1: every slab before i0 ends at or before o0 and
+    // every slab after i1 starts after o1
     if (stp->splits) {
       const bool last = t == sg.tile0 + sg.ntiles - 1;
       if (threadIdx.x == 0) s_i0 = stp->splits[t];
@@ -202,60 +209,138 @@ __global__ void __launch_bounds__(kThreads) k_join_emit(Stage* stp) {
     __syncthreads();
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
     const bool staged = m <= (unsigned long long)kEmitWin;
-    if (staged) {
-      tile_to_smem<kEmitWin / kThreads>(spos, P + i0, (uint32_t)m, Ident());
-      tile_to_smem<kEmitWin / kThreads>(skey, Dq + i0, (uint32_t)m, Ident());
+    if (staged) {  // round 1: the slab table
+      constexpr int kPer = kEmitWin / kThreads;
+      unsigned long long p[kPer];
+      K key[kPer];
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        p[e] = i < m ? P[i0 + i] : 0ull;
+        key[e] = i < m ? Dq[i0 + i] : (K)0;
+      }
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        if (i < m) {
+          const uint32_t x = (uint32_t)(key[e] >> w), y = (uint32_t)(key[e] & mask);
+          // slab i0 starts at or before o0 (r0 of its candidates precede the
+          // tile); slabs after it start inside (o0, o1]
+          const uint32_t r0 = i == 0 ? (uint32_t)(o0 - p[e]) : 0u;
+          s_start[i] = i == 0 ? 0u : (uint32_t)(p[e] - o0);
+          if (kind == KIND_TC) {
+            s_x[i] = x;
+            s_a[i] = off[y] + r0;                                 // T(x,y), E(y,z)
+          } else {
+            const uint32_t ox = off[x];
+            s_x[i] = ox;
+            if (iter == 0) {
+              s_a[i] = 0;
+              s_d[i] = off[x + 1] - ox - 1;                       // distinct children of x
+            } else {
+              const uint32_t oy = off[y];
+              s_a[i] = oy;
+              s_d[i] = off[y + 1] - oy;                           // E(a,x), sg(a,b), E(b,y)
+            }
+            if (i == 0) s_r0 = r0;
+          }
+        }
+      }
     }
     __syncthreads();
-    auto posat = [&](unsigned long long i) { return staged ? spos[i] : P[i0 + i]; };
-    auto keyat = [&](unsigned long long i) { return staged ? skey[i] : Dq[i0 + i]; };
     K out[kItemsC];
     const uint32_t q0 = threadIdx.x * kItemsC;
-    if (q0 < nout) {
+#pragma unroll
+    for (int e = 0; e < kItemsC; ++e) out[e] = 0;
+    if (q0 < nout && staged) {  // round 2: walk the table, then the adjacency loads
+      uint32_t u[kItemsC], v[kItemsC];  // TC: x, adj index; SG: two adj indices
+      uint32_t lo = 0, hi = (uint32_t)m;  // largest i with s_start[i] <= q0
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_start[mid] <= q0) lo = mid; else hi = mid;
+      }
+      uint32_t i = lo;
+      uint32_t nxt = i + 1 < m ? s_start[i + 1] : 0xFFFFFFFFu;
+#pragma unroll
+      for (int e = 0; e < kItemsC; ++e) {
+        const uint32_t j = q0 + e;
+        u[e] = 0;
+        v[e] = 0;
+        if (j < nout) {
+          while (j >= nxt) {  // skip to the slab holding j (empty slabs share a start)
+            ++i;
+            nxt = i + 1 < m ? s_start[i + 1] : 0xFFFFFFFFu;
+          }
+          const uint32_t r = j - s_start[i];
+          if (kind == KIND_TC) {
+            u[e] = s_x[i];
+            v[e] = s_a[i] + r;
+          } else {
+            const uint32_t rr = r + (i == 0 ? s_r0 : 0u), d = s_d[i];
+            const uint32_t qa = rr / d;
+            uint32_t qb = rr - qa * d;
+            if (iter == 0) {
+              qb += qb >= qa;
+              u[e] = s_x[i] + qa;
+              v[e] = s_x[i] + qb;
+            } else {
+              u[e] = s_x[i] + qa;
+              v[e] = s_a[i] + qb;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kItemsC; ++e) {
+        if (q0 + e < nout) {
+          if (kind == KIND_TC) out[e] = ((K)u[e] << w) | (K)adj[v[e]];
+          else out[e] = ((K)adj[u[e]] << w) | (K)adj[v[e]];
+        }
+      }
+    } else if (q0 < nout) {  // many empty slabs: walk the delta tuples in global memory
       const unsigned long long o = o0 + q0;
       unsigned long long lo = 0, hi = m;  // largest i with pos[i] <= o
       while (hi - lo > 1) {
         const unsigned long long mid = (lo + hi) >> 1;
-        if (posat(mid) <= o) lo = mid; else hi = mid;
+        if (P[i0 + mid] <= o) lo = mid; else hi = mid;
       }
       unsigned long long i = lo;
-      unsigned long long base = posat(i);
-      unsigned long long nextb = i + 1 < m ? posat(i + 1) : ~0ull;
-      K key = keyat(i);
+      unsigned long long base = P[i0 + i];
+      unsigned long long nextb = i + 1 < m ? P[i0 + i + 1] : ~0ull;
+      K key = Dq[i0 + i];
       uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
       uint32_t ox = off[x], oy = off[y], dy = off[y + 1] - oy, dx = off[x + 1] - ox;
 #pragma unroll
       for (int e = 0; e < kItemsC; ++e) {
-        out[e] = 0;
         const unsigned long long oe = o + e;
         if (q0 + e < nout) {
-          while (oe >= nextb) {  // next non-empty slab
+          while (oe >= nextb) {
             ++i;
             base = nextb;
-            nextb = i + 1 < m ? posat(i + 1) : ~0ull;
+            nextb = i + 1 < m ? P[i0 + i + 1] : ~0ull;
             if (oe < nextb) {
-              key = keyat(i);
+              key = Dq[i0 + i];
               x = (uint32_t)(key >> w); y = (uint32_t)(key & mask);
               ox = off[x]; oy = off[y]; dy = off[y + 1] - oy; dx = off[x + 1] - ox;
             }
           }
           const uint32_t r = (uint32_t)(oe - base);
           if (kind == KIND_TC) {
-            out[e] = ((K)x << w) | (K)adj[oy + r];                       // T(x,y), E(y,z)
+            out[e] = ((K)x << w) | (K)adj[oy + r];
           } else if (iter == 0) {
-            const uint32_t dm1 = dx - 1;                                  // distinct children of x
+            const uint32_t dm1 = dx - 1;
             const uint32_t qa = r / dm1;
             uint32_t qb = r - qa * dm1;
             qb += qb >= qa;
             out[e] = ((K)adj[ox + qa] << w) | (K)adj[ox + qb];
           } else {
-            const uint32_t qa = r / dy, qb = r - qa * dy;                  // E(a,x), sg(a,b), E(b,y)
+            const uint32_t qa = r / dy, qb = r - qa * dy;
             out[e] = ((K)adj[ox + qa] << w) | (K)adj[oy + qb];
           }
         }
       }
     }
-    __syncthreads();  // staging arrays are dead: reuse the space for the output
+    __syncthreads();  // round 3: the slab table is dead, stage the candidates
 #pragma unroll
     for (int e = 0; e < kItemsC; ++e) sout[pad32(q0 + e)] = out[e];
     __syncthreads();
@@ -302,7 +387,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     s.nseg = N; s.ntiles = (uint32_t)s_carry; s.ctr = 0; s.epoch = ++ctl.epoch;
     s.passes = dv->passes; s.dbits = dv->dbits; s.shift = 0; s.pass = 0;
     s.xlen = dv->xseg ? dv->xlen : nullptr;
-    s.hist_n = (unsigned long long)(dv->xseg ? nvx : N) * dv->passes * kRadix;
+    // (x-grouped: the segment builder zeroes the rows of non-empty sources)
+    s.hist_n = dv->xseg ? 0ull : (unsigned long long)N * dv->passes * kRadix;
   }
 }
 
@@ -311,55 +397,77 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
 // so sorting each x-group on the destination field sorts the whole array.
 // Every source vertex becomes one sort segment: offsets and tile ranges from
 // the per-x candidate totals the count kernel accumulated.
-__global__ void __launch_bounds__(kPlanThreads) k_xseg_build(Dev* dv) {
-  constexpr int kPer = 16;
-  __shared__ unsigned long long sh[32];
-  __shared__ unsigned long long s_len, s_tiles;
+// Pass 1: candidates and tiles of each chunk of kXChunk source vertices.
+__global__ void __launch_bounds__(kXChunk) k_xseg_sum(Dev* dv) {
+  __shared__ unsigned long long sh[kXChunk / 32];
+  if (dv->ctl.abort) return;
+  const Inst& I = dv->inst[0];
+  const uint32_t nv = I.state == INST_ACTIVE ? I.nv : 0u;
+  const uint32_t x = blockIdx.x * kXChunk + threadIdx.x;
+  if (blockIdx.x * kXChunk >= nv) return;
+  const unsigned long long len = x < nv ? dv->xlen[x] : 0ull;
+  unsigned long long tl, tt;
+  block_excl_scan(len, sh, &tl);
+  block_excl_scan((len + kTileC - 1) / kTileC, sh, &tt);
+  if (threadIdx.x == 0) {
+    dv->xsum[2 * blockIdx.x] = tl;
+    dv->xsum[2 * blockIdx.x + 1] = tt;
+  }
+}
+
+// Pass 2: one sort segment per source vertex (offsets from the chunk sums
+// before it plus a scan inside the chunk), the tile -> segment map, and zeroed
+// radix-histogram rows for the sources that have candidates.  The chunk that
+// holds the last vertex points the sort stages at the new segments.
+__global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
+  __shared__ unsigned long long sh[kXChunk / 32];
+  __shared__ unsigned long long slen[kXChunk];
   Ctl& ctl = dv->ctl;
   if (ctl.abort) return;
   const Inst& I = dv->inst[0];
   const uint32_t nv = I.state == INST_ACTIVE ? I.nv : 0u;
-  if (threadIdx.x == 0) { s_len = I.c_off; s_tiles = 0; }
-  __syncthreads();
-  for (uint32_t base = 0; base < nv; base += kPer * kPlanThreads) {
-    const uint32_t x0 = base + threadIdx.x * kPer;
-    unsigned long long len[kPer], sl = 0, stl = 0;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      len[i] = x0 + i < nv ? dv->xlen[x0 + i] : 0ull;
-      sl += len[i];
-      stl += (len[i] + kTileC - 1) / kTileC;
-    }
-    unsigned long long tl, tt;
-    const unsigned long long el = scan1024(sl, sh, &tl);
-    const unsigned long long et = scan1024(stl, sh, &tt);
-    unsigned long long off = s_len + el, tile = s_tiles + et;
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      if (x0 + i < nv) {
-        Seg g{};
-        g.in_off = off; g.n = len[i]; g.out_off = off;
-        g.tile0 = (uint32_t)tile; g.ntiles = (uint32_t)((len[i] + kTileC - 1) / kTileC);
-        g.inst = 0;
-        dv->segX[x0 + i] = g;
-        for (uint32_t j = 0; j < g.ntiles; ++j) dv->tile_seg[tile + j] = x0 + i;
-        off += len[i];
-        tile += g.ntiles;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) { s_len += tl; s_tiles += tt; }
-    __syncthreads();
+  const uint32_t nchunks = nv ? (nv + kXChunk - 1) / kXChunk : 1u;
+  const uint32_t b = blockIdx.x;
+  if (b >= nchunks) return;
+  unsigned long long pl = 0, pt = 0, tl, tt;
+  for (uint32_t j = threadIdx.x; j < b; j += kXChunk) {
+    pl += dv->xsum[2 * j];
+    pt += dv->xsum[2 * j + 1];
   }
-  if (threadIdx.x == 0) {
+  block_excl_scan(pl, sh, &pl);
+  block_excl_scan(pt, sh, &pt);
+  const uint32_t x = b * kXChunk + threadIdx.x;
+  const unsigned long long len = x < nv ? dv->xlen[x] : 0ull;
+  const unsigned long long nt = (len + kTileC - 1) / kTileC;
+  const unsigned long long el = block_excl_scan(len, sh, &tl);
+  const unsigned long long et = block_excl_scan(nt, sh, &tt);
+  slen[threadIdx.x] = len;
+  if (x < nv) {
+    const unsigned long long off = I.c_off + pl + el;
+    const uint32_t tile0 = (uint32_t)(pt + et);
+    Seg g{};
+    g.in_off = off; g.n = len; g.out_off = off;
+    g.tile0 = tile0; g.ntiles = (uint32_t)nt; g.inst = 0;
+    dv->segX[x] = g;
+    for (uint32_t j = 0; j < (uint32_t)nt; ++j) dv->tile_seg[tile0 + j] = x;
+  }
+  __syncthreads();
+  // histogram rows of this chunk's non-empty sources start from zero
+  const uint32_t row = dv->passes * kRadix;
+  const uint32_t nx = min(kXChunk, nv - min(nv, b * kXChunk));
+  unsigned long long* hrow = dv->hist + (unsigned long long)b * kXChunk * row;
+  for (uint32_t i = threadIdx.x; i < nx * row; i += kXChunk)
+    if (slen[i / row]) hrow[i] = 0;
+  if (b == nchunks - 1 && threadIdx.x == 0) {
+    const uint32_t ntiles = (uint32_t)(pt + tt);
     const int ids[2] = {S_HIST, S_HSCAN};
     for (int k = 0; k < 2; ++k) {
       dv->st[ids[k]].segs = dv->segX; dv->st[ids[k]].nseg = nv;
-      dv->st[ids[k]].ntiles = (uint32_t)s_tiles; dv->st[ids[k]].tile_seg = dv->tile_seg;
+      dv->st[ids[k]].ntiles = ntiles; dv->st[ids[k]].tile_seg = dv->tile_seg;
     }
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
-      dv->st[S_PASS0 + p].ntiles = (uint32_t)s_tiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
+      dv->st[S_PASS0 + p].ntiles = ntiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
     }
   }
 }
@@ -774,7 +882,10 @@ void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_merge(Dev* dv, cudaStream_t s) { k_plan_merge<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_post(Dev* dv, cudaStream_t s) { k_plan_post<<<1, kPlanThreads, 0, s>>>(dv); }
-void launch_xseg_build(Dev* dv, cudaStream_t s) { k_xseg_build<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_xseg_build(Dev* dv, cudaStream_t s) {
+  k_xseg_sum<<<kXChunks, kXChunk, 0, s>>>(dv);
+  k_xseg_fill<<<kXChunks, kXChunk, 0, s>>>(dv);
+}
 template <typename K>
 void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s) {
   if (count) k_init_diag<K><<<count < 4096 ? count : 4096, 256, 0, s>>>(inst, first, count, (K*)dpool);

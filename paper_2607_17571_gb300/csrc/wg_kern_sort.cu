@@ -71,12 +71,14 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
 }
 
 // Exclusive scan of every (segment, pass) row of the digit histogram: the
-// global start of each digit bucket.  One warp per row.
+// global start of each digit bucket.  One warp per row; rows of empty
+// segments are skipped (nothing zeroed or read them).
 __global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
   if (*(volatile uint32_t*)&stp->ctl->abort) return;
   const uint32_t rows = stp->nseg * stp->passes;
   const uint32_t lane = threadIdx.x & 31;
   for (uint32_t r = blockIdx.x * kWarps + (threadIdx.x >> 5); r < rows; r += gridDim.x * kWarps) {
+    if (stp->segs[r / stp->passes].n == 0) continue;  // no keys: the row is never read
     unsigned long long* h = stp->hist + (unsigned long long)r * kRadix;
     unsigned long long v[kRadix / 32], s = 0;
 #pragma unroll

@@ -125,6 +125,14 @@ def _u32(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
 
 
+def pinned(n: int, dtype=np.uint64) -> np.ndarray:
+    """A page-locked host array of n elements (torch's pinned allocator): the
+    reusable host side of result copies and of edge uploads."""
+    import torch
+    t = torch.empty(n * np.dtype(dtype).itemsize, dtype=torch.uint8, pin_memory=True)
+    return t.numpy().view(dtype)  # the array keeps the pinned storage alive
+
+
 def sort_keys_noalloc(ptr: int, n: int, key_bytes: int, bits: int, stream_ptr=None):
     """wg_sort_keys_noalloc: in-place sort with the library's static scratch
     (no context, no allocation); asynchronous on the given stream."""
@@ -147,16 +155,23 @@ class Query:
         _check(rc, "wg_wait")
         return self.poll()
 
-    def result(self) -> np.ndarray:
-        """Sorted packed keys (src << 32) | dst, uint64, on the host."""
+    def result(self, out: np.ndarray = None) -> np.ndarray:
+        """Sorted packed keys (src << 32) | dst, uint64, on the host.
+
+        `out` (optional): a host uint64 array of at least the result size to
+        copy into -- e.g. a reusable buffer from `pinned()`, which the copy
+        reaches at DMA speed.  Returns the filled prefix."""
         n = c_size_t()
         rc = self.ctx.lib.wg_result_copy(self.ctx.h, self.id, None, 0, byref(n))
         if rc not in (WG_OK, WG_E_CAPACITY):
             _check(rc, "wg_result_copy")
-        out = np.empty(n.value, dtype=np.uint64)
+        if out is None:
+            out = np.empty(n.value, dtype=np.uint64)
+        elif out.dtype != np.uint64 or not out.flags.c_contiguous or out.shape[0] < n.value:
+            raise ValueError("out must be a contiguous uint64 array of at least the result size")
         _check(self.ctx.lib.wg_result_copy(self.ctx.h, self.id, out.ctypes.data_as(c_void_p),
                                            out.shape[0], byref(n)), "wg_result_copy")
-        return out
+        return out[: n.value]
 
     def result_device(self, out_ptr: int, cap: int) -> int:
         n = c_size_t()

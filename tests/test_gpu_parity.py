@@ -177,3 +177,23 @@ def test_repeat_is_deterministic_and_reuses_engine(ctx):
         q.free()
     rel.free()
     assert all(np.array_equal(outs[0], o) for o in outs[1:])
+
+
+def test_result_into_pinned_buffer(ctx):
+    # the reusable page-locked result buffer: same bytes as a fresh array,
+    # larger-than-needed buffers return the filled prefix, short ones are refused
+    from paper_2607_17571_gb300 import wg
+    g = I.er_graph(400, 1200, 21)
+    want = oracle_tc(g.src, g.dst)
+    src, dst = wg.pinned(len(g.src), np.uint32), wg.pinned(len(g.dst), np.uint32)
+    src[:], dst[:] = g.src, g.dst
+    rel = ctx.load(src, dst)
+    q = ctx.tc(rel)
+    q.wait()
+    buf = wg.pinned(want.keys.shape[0] + 5)
+    got = q.result(out=buf)
+    assert got.shape == want.keys.shape and np.array_equal(got, want.keys)
+    with pytest.raises(ValueError):
+        q.result(out=wg.pinned(want.keys.shape[0] - 1))
+    q.free()
+    rel.free()
