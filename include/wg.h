@@ -201,9 +201,11 @@ void wg_query_free(wg_ctx* ctx, wg_query q);
  * run on the context stream, use context scratch, and synchronise the stream
  * before returning sizes.
  *
- * wg_sort_keys: stable LSD radix sort of n keys on their low `bits` bits
- * (1..64; higher bits must be zero), in place (Sec. Buffer Routing and
- * Adaptive Radix Sort: histogram, prefix sum, scatter per digit). */
+ * wg_sort_keys: LSD radix sort of n keys on their low `bits` bits (1..64;
+ * higher bits must be zero), in place (Sec. Buffer Routing and Adaptive Radix
+ * Sort: histogram, prefix sum, scatter per digit).  Every pass after the
+ * first is stable; keys equal on the sorted bits are identical, so the
+ * result is the unique sorted sequence. */
 int wg_sort_keys(wg_ctx* ctx, void* d_keys, size_t n, int key_bytes, uint32_t bits);
 /* wg_unique_diff: out = { c in sorted `cand` : c differs from its predecessor
  * and c is not in sorted `full` } in input order (Sec. Fused Deduplication and
@@ -221,8 +223,8 @@ int wg_merge_disjoint(wg_ctx* ctx, const void* d_a, size_t na, const void* d_b, 
  * cannot allocate device memory -- code running inside another runtime's
  * memory arena, or a process that must not call cudaMalloc or any allocator
  * (PyTorch's included), e.g. to keep its device footprint fixed.  It performs
- * the same sort as wg_sort_keys (stable LSD radix sort of n keys on their low
- * `bits` bits, in place; key_bytes = 4 or 8; higher bits must be zero) but takes
+ * the same sort as wg_sort_keys (LSD radix sort of n keys on their low `bits`
+ * bits, in place; key_bytes = 4 or 8; higher bits must be zero) but takes
  * no context and allocates nothing: its scratch (stage records, digit
  * histograms, lookback words and the ping-pong key buffer, about 8.6 MB) is one
  * fixed static device array that every GPU loading the library holds until the

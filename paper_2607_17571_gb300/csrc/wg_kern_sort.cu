@@ -136,18 +136,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
       const uint32_t idx = wbase + i * 32;
       key[i] = idx < n ? p[idx] : (K)0;
     }
-    // stable rank within the warp: peers with the same digit, in (i, lane) order
+    if (pass == 0) {
+      // first pass: the input order carries nothing, so any order of equal
+      // digits is correct -- one shared atomic per key gives its rank.  Keys
+      // that tie on every sorted bit are identical (the bits above are zero),
+      // so the sorted output equals that of a stable sort.
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i) {
-      const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      uint32_t before = 0;
-      if (d != 0xFFFFFFFFu) before = whist[warp][d];
-      rank[i] = before + __popc(peers & lt_mask);
-      __syncwarp();
-      if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
-        whist[warp][d] = before + __popc(peers);
-      __syncwarp();
+      for (int i = 0; i < kItemsC; ++i)
+        rank[i] = wbase + i * 32 < n ? atomicAdd(&whist[warp][digit(key[i], shift, mask)], 1u) : 0u;
+    } else {
+      // later passes: stable rank within the warp -- peers with the same
+      // digit, in (i, lane) order
+#pragma unroll
+      for (int i = 0; i < kItemsC; ++i) {
+        const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (d != 0xFFFFFFFFu) before = whist[warp][d];
+        rank[i] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
+          whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+      }
     }
     __syncthreads();
 
@@ -503,17 +514,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
       bool has = q0 > 0 || s_hasprev;
       K prev = q0 > 0 ? (i > 0 ? SA(i - 1) : (K)0) : s_prev;
       if (q0 > 0 && j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
+      // merge heads in registers: one shared load per step.  SA(la) is still
+      // inside sin (la + lb <= T); an exhausted B side reads as the largest
+      // key, so the A side wins every comparison until it is exhausted too.
+      K a = SA(i), b = j < lb ? SB(j) : ~(K)0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         val[e] = 0;
         if (q0 + e < L) {
-          const bool takeA = i < la && (j >= lb || SA(i) <= SB(j));
-          const K v = takeA ? SA(i) : SB(j);
+          const bool takeA = i < la && a <= b;
+          K v;
           if (takeA) {
-            ++i;
+            v = a;
+            a = SA(++i);
             kept |= 1u << e;
           } else {
+            v = b;
             ++j;
+            b = j < lb ? SB(j) : ~(K)0;
             if (!has || v != prev) { kept |= 1u << e; isN |= 1u << e; }
           }
           val[e] = v;
@@ -553,7 +571,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
     }
     __syncthreads();
     K* fo = Fall + sg.out2_off + a0 + exN;
-    for (uint32_t i = threadIdx.x; i < totK; i += kThreads) fo[i] = sin[pad32(i)];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      if (i < totK) fo[i] = sin[pad32(i)];
+    }
     if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = exN + totN;
   }
 }
