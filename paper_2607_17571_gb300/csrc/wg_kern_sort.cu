@@ -432,151 +432,215 @@ __device__ __forceinline__ unsigned long long mpath_tie(const K* A, unsigned lon
   return lo;
 }
 
+// Per-tile state a CTA keeps between classifying a tile and writing it out.
+struct FuseMeta {
+  unsigned long long a0;  // Full elements before the tile
+  uint32_t t, k;          // tile, segment
+  uint32_t totK, totN;    // kept elements (Full' part) and new tuples of the tile
+  uint32_t first, last;   // first / last tile of its segment
+};
+
+// Classify tile t into slot `sb`: load its Full and candidate parts, merge,
+// mark kept and new elements, publish the tile's new-tuple count, and leave
+// the kept elements in Full' order in sbuf plus, per thread, where its kept
+// run starts, how many new tuples precede it, and its two masks.
+template <typename K>
+__device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, uint32_t* smask,
+                                              uint32_t* spre, FuseMeta* meta,
+                                              unsigned long long* s_scan,
+                                              unsigned long long* s_a0, unsigned long long* s_a1,
+                                              K* s_prev, uint32_t* s_hasprev) {
+  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
+  const K* Aall = (const K*)stp->in;     // Full
+  const K* Ball = (const K*)stp->aux;    // sorted candidates
+  const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
+  const Seg sg = stp->segs[k];
+  const K* A = Aall + sg.in_off;
+  const K* B = Ball + sg.aux_off;
+  const unsigned long long na = sg.n, nb = sg.aux_n;
+  const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * T;
+  const unsigned long long d1 = min(d0 + (unsigned long long)T, na + nb);
+  const bool last = t == sg.tile0 + sg.ntiles - 1;
+  if (stp->splits) {
+    if (threadIdx.x == 0) *s_a0 = stp->splits[t];
+    if (threadIdx.x == 32) *s_a1 = last ? na : stp->splits[t + 1];
+  } else {
+    if (threadIdx.x == 0) *s_a0 = mpath_tie(A, na, B, nb, d0);
+    if (threadIdx.x == 32) *s_a1 = mpath_tie(A, na, B, nb, d1);
+  }
+  __syncthreads();
+  const unsigned long long a0 = *s_a0, a1 = *s_a1, b0 = d0 - a0, b1 = d1 - a1;
+  const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
+  {  // Full part then candidate part, every load in flight at once
+    K v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      v[e] = i < la ? A[a0 + i] : (i < L ? B[b0 + i - la] : (K)0);
+    }
+    K pa = 0, pb = 0;
+    if (threadIdx.x == 0) {
+      // the element just before this tile in merged order (its largest predecessor)
+      if (a0 > 0) pa = A[a0 - 1];
+      if (b0 > 0) pb = B[b0 - 1];
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      if (i < L) sbuf[pad32(i)] = v[e];
+    }
+    if (threadIdx.x == 0) {
+      *s_hasprev = d0 > 0;
+      *s_prev = pb > pa ? pb : pa;
+    }
+  }
+  __syncthreads();
+  // padded views of the Full part (SA) and the candidate part (SB)
+  auto SA = [&](uint32_t i) { return sbuf[pad32(i)]; };
+  auto SB = [&](uint32_t j) { return sbuf[pad32(la + j)]; };
+  // blocked: thread owns merged positions [q0, q0 + E)
+  const uint32_t q0 = threadIdx.x * E;
+  K val[E];
+  uint32_t isN = 0, kept = 0;   // bit i: output i is a new tuple / is kept
+  if (q0 < L) {
+    uint32_t i, j;
+    {  // merge path inside the tile (Full first on ties)
+      uint32_t lo = q0 > lb ? q0 - lb : 0, hi = q0 < la ? q0 : la;
+      while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (SA(m) <= SB(q0 - 1 - m)) lo = m + 1; else hi = m;
+      }
+      i = lo;
+      j = q0 - i;
+    }
+    bool has = q0 > 0 || *s_hasprev;
+    K prev = q0 > 0 ? (i > 0 ? SA(i - 1) : (K)0) : *s_prev;
+    if (q0 > 0 && j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
+    // merge heads in registers: one shared load per step.  SA(la) is still
+    // inside sbuf (la + lb <= T); an exhausted B side reads as the largest
+    // key, so the A side wins every comparison until it is exhausted too.
+    K a = SA(i), b = j < lb ? SB(j) : ~(K)0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      val[e] = 0;
+      if (q0 + e < L) {
+        const bool takeA = i < la && a <= b;
+        K v;
+        if (takeA) {
+          v = a;
+          a = SA(++i);
+          kept |= 1u << e;
+        } else {
+          v = b;
+          ++j;
+          b = j < lb ? SB(j) : ~(K)0;
+          if (!has || v != prev) { kept |= 1u << e; isN |= 1u << e; }
+        }
+        val[e] = v;
+        prev = v;
+        has = true;
+      }
+    }
+  }
+  // one scan for both counts: N in the high half, kept in the low half
+  unsigned long long tot;
+  const unsigned long long both = ((unsigned long long)__popc(isN) << 32) | __popc(kept);
+  const unsigned long long ex = block_excl_scan(both, s_scan, &tot);  // ends with a barrier:
+  const uint32_t totN = (uint32_t)(tot >> 32), totK = (uint32_t)tot;  // sbuf reads are done
+  const bool first = (t == sg.tile0);
+  if (threadIdx.x == 0) {
+    st_put(stp->status + t, st_pack(stp->epoch, first ? FLAG_INC : FLAG_AGG, totN));
+    meta->a0 = a0; meta->t = t; meta->k = k; meta->totK = totK; meta->totN = totN;
+    meta->first = first; meta->last = last;
+  }
+  // kept elements in Full' order, at tile-local positions
+  uint32_t wk = (uint32_t)ex;
+#pragma unroll
+  for (int e = 0; e < E; ++e)
+    if (kept >> e & 1u) sbuf[pad32(wk++)] = val[e];
+  smask[threadIdx.x] = (isN << 16) | kept;           // E <= 16
+  spre[threadIdx.x] = ((uint32_t)(ex >> 32) << 16) | (uint32_t)ex;  // both < 2^16 (T <= 4096)
+}
+
+// Write out a classified tile once its new-tuple prefix exN is known.
+template <typename K>
+__device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint32_t* smask,
+                                           const uint32_t* spre, const FuseMeta& m,
+                                           unsigned long long exN) {
+  constexpr int E = FuseTile<K>::E;
+  const Seg& sg = stp->segs[m.k];
+  K* Nall = (K*)stp->out;                // new delta
+  K* Fall = (K*)stp->out2;               // Full'
+  // new tuples are few: each thread stores its own run of them directly
+  const uint32_t mk = smask[threadIdx.x], pr = spre[threadIdx.x];
+  const uint32_t kept = mk & 0xFFFFu, isN = mk >> 16;
+  uint32_t wk = pr & 0xFFFFu;
+  K* no = Nall + sg.out_off + exN + (pr >> 16);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (kept >> e & 1u) {
+      if (isN >> e & 1u) *no++ = sbuf[pad32(wk)];
+      ++wk;
+    }
+  }
+  K* fo = Fall + sg.out2_off + m.a0 + exN;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = threadIdx.x + e * kThreads;
+    if (i < m.totK) fo[i] = sbuf[pad32(i)];
+  }
+  if (threadIdx.x == 0 && m.last) stp->segs[m.k].res = exN + m.totN;
+}
+
+// Software-pipelined over two tiles: a CTA classifies its next tile (and
+// publishes that tile's count) before it looks back for the previous one, so
+// the predecessors the lookback waits on have had one tile time to publish.
+// Deadlock-free: publishing a tile's count never waits, so the oldest
+// unfinished tile can always complete its lookback.
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
-  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
-  __shared__ K sin[Padded<T>::n];  // Full part then candidate part; then Full' outputs
+  constexpr int T = FuseTile<K>::T;
+  static_assert(FuseTile<K>::E <= 16 && T <= 65535, "masks and prefixes are packed in 16 bits");
+  __shared__ K sbuf[2][Padded<T>::n];  // tile input, then its kept elements in Full' order
+  __shared__ uint32_t smask[2][kThreads], spre[2][kThreads];
+  __shared__ FuseMeta smeta[2];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_a0, s_a1, s_excl;
   __shared__ K s_prev;
   __shared__ uint32_t s_hasprev, s_t, s_bad;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
-  const K* Aall = (const K*)stp->in;     // Full
-  const K* Ball = (const K*)stp->aux;    // sorted candidates
-  K* Nall = (K*)stp->out;                // new delta
-  K* Fall = (K*)stp->out2;               // Full'
-  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
-  unsigned long long* status = stp->status;
+  const uint32_t ntiles = stp->ntiles;
+  uint32_t cur = 0;
+  uint32_t t = claim_tile(stp, &s_t);
+  if (t >= ntiles) return;
+  fuse_classify<K>(stp, t, sbuf[0], smask[0], spre[0], &smeta[0], s_scan, &s_a0, &s_a1, &s_prev,
+                   &s_hasprev);
   for (;;) {
-    const uint32_t t = claim_tile(stp, &s_t);
-    if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
-    const Seg sg = stp->segs[k];
-    const K* A = Aall + sg.in_off;
-    const K* B = Ball + sg.aux_off;
-    const unsigned long long na = sg.n, nb = sg.aux_n;
-    const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * T;
-    const unsigned long long d1 = min(d0 + (unsigned long long)T, na + nb);
-    const bool last = t == sg.tile0 + sg.ntiles - 1;
-    if (stp->splits) {
-      if (threadIdx.x == 0) { s_a0 = stp->splits[t]; s_bad = 0; }
-      if (threadIdx.x == 32) s_a1 = last ? na : stp->splits[t + 1];
-    } else {
-      if (threadIdx.x == 0) { s_a0 = mpath_tie(A, na, B, nb, d0); s_bad = 0; }
-      if (threadIdx.x == 32) s_a1 = mpath_tie(A, na, B, nb, d1);
-    }
-    __syncthreads();
-    const unsigned long long a0 = s_a0, a1 = s_a1, b0 = d0 - a0, b1 = d1 - a1;
-    const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
-    {  // Full part then candidate part, every load in flight at once
-      K v[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const uint32_t i = threadIdx.x + e * kThreads;
-        v[e] = i < la ? A[a0 + i] : (i < L ? B[b0 + i - la] : (K)0);
-      }
-      K pa = 0, pb = 0;
-      if (threadIdx.x == 0) {
-        // the element just before this tile in merged order (its largest predecessor)
-        if (a0 > 0) pa = A[a0 - 1];
-        if (b0 > 0) pb = B[b0 - 1];
-      }
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const uint32_t i = threadIdx.x + e * kThreads;
-        if (i < L) sin[pad32(i)] = v[e];
-      }
-      if (threadIdx.x == 0) {
-        s_hasprev = d0 > 0;
-        s_prev = pb > pa ? pb : pa;
-      }
-    }
-    __syncthreads();
-    // padded views of the Full part (SA) and the candidate part (SB)
-    auto SA = [&](uint32_t i) { return sin[pad32(i)]; };
-    auto SB = [&](uint32_t j) { return sin[pad32(la + j)]; };
-    // blocked: thread owns merged positions [q0, q0 + E)
-    const uint32_t q0 = threadIdx.x * E;
-    K val[E];
-    uint32_t isN = 0, kept = 0;   // bit i: output i is a new tuple / is kept
-    if (q0 < L) {
-      uint32_t i, j;
-      {  // merge path inside the tile (Full first on ties)
-        uint32_t lo = q0 > lb ? q0 - lb : 0, hi = q0 < la ? q0 : la;
-        while (lo < hi) {
-          const uint32_t m = (lo + hi) >> 1;
-          if (SA(m) <= SB(q0 - 1 - m)) lo = m + 1; else hi = m;
-        }
-        i = lo;
-        j = q0 - i;
-      }
-      bool has = q0 > 0 || s_hasprev;
-      K prev = q0 > 0 ? (i > 0 ? SA(i - 1) : (K)0) : s_prev;
-      if (q0 > 0 && j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
-      // merge heads in registers: one shared load per step.  SA(la) is still
-      // inside sin (la + lb <= T); an exhausted B side reads as the largest
-      // key, so the A side wins every comparison until it is exhausted too.
-      K a = SA(i), b = j < lb ? SB(j) : ~(K)0;
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        val[e] = 0;
-        if (q0 + e < L) {
-          const bool takeA = i < la && a <= b;
-          K v;
-          if (takeA) {
-            v = a;
-            a = SA(++i);
-            kept |= 1u << e;
-          } else {
-            v = b;
-            ++j;
-            b = j < lb ? SB(j) : ~(K)0;
-            if (!has || v != prev) { kept |= 1u << e; isN |= 1u << e; }
-          }
-          val[e] = v;
-          prev = v;
-          has = true;
-        }
-      }
-    }
-    // one scan for both counts: N in the high half, kept in the low half
-    unsigned long long tot;
-    const unsigned long long both = ((unsigned long long)__popc(isN) << 32) | __popc(kept);
-    const unsigned long long ex = block_excl_scan(both, s_scan, &tot);
-    const unsigned long long totN = tot >> 32, totK = tot & 0xFFFFFFFFull;
-    const bool first = (t == sg.tile0);
-    if (threadIdx.x == 0)
-      st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, totN));
-    if (!first && threadIdx.x < 32) {
-      const unsigned long long e = lookback_scalar(status, t, sg.tile0, epoch, ctl);
+    // next tile first (claim_tile's barriers also publish smeta[cur])
+    const uint32_t tn = claim_tile(stp, &s_t);
+    const bool more = tn < ntiles;
+    if (more)
+      fuse_classify<K>(stp, tn, sbuf[cur ^ 1], smask[cur ^ 1], spre[cur ^ 1], &smeta[cur ^ 1],
+                       s_scan, &s_a0, &s_a1, &s_prev, &s_hasprev);
+    const FuseMeta m = smeta[cur];
+    if (threadIdx.x == 0) s_bad = 0;
+    if (!m.first && threadIdx.x < 32) {
+      const unsigned long long e =
+          lookback_scalar(stp->status, m.t, stp->segs[m.k].tile0, stp->epoch, ctl);
       if (threadIdx.x == 0) {
         s_excl = e;
         if (*(volatile uint32_t*)&ctl->abort) s_bad = 1;
-        st_put(status + t, st_pack(epoch, FLAG_INC, e + totN));
+        st_put(stp->status + m.t, st_pack(stp->epoch, FLAG_INC, e + m.totN));
       }
-    } else if (first && threadIdx.x == 0) {
+    } else if (m.first && threadIdx.x == 0) {
       s_excl = 0;
     }
-    __syncthreads();  // all reads of sin are done
+    __syncthreads();  // the kept elements, masks and s_excl of the previous tile are visible
     if (s_bad) return;
-    const unsigned long long exN = s_excl;
-    uint32_t wk = (uint32_t)(ex & 0xFFFFFFFFull);
-    // new tuples are few: each thread stores its own run of them directly
-    K* no = Nall + sg.out_off + exN + (ex >> 32);
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if (kept >> e & 1u) sin[pad32(wk++)] = val[e];
-      if (isN >> e & 1u) *no++ = val[e];
-    }
-    __syncthreads();
-    K* fo = Fall + sg.out2_off + a0 + exN;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      const uint32_t i = threadIdx.x + e * kThreads;
-      if (i < totK) fo[i] = sin[pad32(i)];
-    }
-    if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = exN + totN;
+    fuse_write<K>(stp, sbuf[cur], smask[cur], spre[cur], m, s_excl);
+    if (!more) return;
+    cur ^= 1;
   }
 }
 
