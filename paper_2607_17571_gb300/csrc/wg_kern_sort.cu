@@ -96,127 +96,175 @@ __global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
 }
 
 // ------------------------------------------------------------------ one radix pass
+struct PassMeta {
+  uint32_t t, k, n, first;  // tile, segment, keys in the tile, first tile of its segment
+};
+
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
-  __shared__ K sk[kTileC];
-  __shared__ uint32_t whist[kWarps][kRadix];     // per-warp counts -> prefix over warps
-  __shared__ uint32_t tstart[kRadix];            // digit start inside the tile
-  __shared__ unsigned long long gdst[kRadix];    // global base of each digit minus tstart
-  __shared__ unsigned long long s_scan[kWarps];
-  __shared__ uint32_t s_t, s_bad;
-  Ctl* ctl = stp->ctl;
-  if (*(volatile uint32_t*)&ctl->abort) return;
-  const K* in = (const K*)stp->in;
-  K* out = (K*)stp->out;
-  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u;
-  const uint32_t nseg = stp->nseg, ntiles = stp->ntiles, epoch = stp->epoch;
-  const uint32_t pass = stp->pass, passes = stp->passes;
-  unsigned long long* status = stp->status;
+struct PassSmem {
+  static constexpr int kSlots = sizeof(K) == 4 ? 2 : 1;  // two tiles in flight fit for 32-bit keys
+  K sk[kSlots][kTileC];                 // a ranked tile in digit order
+  uint32_t whist[kWarps][kRadix];       // per-warp counts -> prefix over warps
+  uint32_t tstart[kSlots][kRadix];      // digit start inside the tile
+  uint32_t tcnt[kSlots][kRadix];        // digit count of the tile
+  unsigned long long gdst[kRadix];      // global base of each digit minus tstart
+  unsigned long long s_scan[kWarps];
+  PassMeta meta[kSlots];
+  uint32_t s_t, s_bad;
+};
+
+// Rank tile t into slot `sl`: load, rank every key within its digit, publish
+// the tile's digit counts and place the keys in digit order in shared memory.
+// Nothing here waits for another tile.
+template <typename K>
+__device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, uint32_t t, int sl) {
+  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u, pass = stp->pass;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
+  const Seg sg = stp->segs[k];
+  const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+  const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+  const K* p = (const K*)stp->in + sg.in_off + start;
+  for (uint32_t i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&S.whist[0][0])[i] = 0;
+  if (threadIdx.x == 0) S.s_bad = 0;
+  __syncthreads();
 
-  for (;;) {
-    const uint32_t t = claim_tile(stp, &s_t);
-    if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
-    const Seg sg = stp->segs[k];
-    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
-    const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
-    const K* p = in + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&whist[0][0])[i] = 0;
-    if (threadIdx.x == 0) s_bad = 0;
-    __syncthreads();
-
-    // warp-striped load: warp w owns keys [w*32*kItemsC, (w+1)*32*kItemsC)
-    K key[kItemsC];
-    uint32_t rank[kItemsC];
-    const uint32_t wbase = warp * 32 * kItemsC + lane;
+  // warp-striped load: warp w owns keys [w*32*kItemsC, (w+1)*32*kItemsC)
+  K key[kItemsC];
+  uint32_t rank[kItemsC];
+  const uint32_t wbase = warp * 32 * kItemsC + lane;
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i) {
-      const uint32_t idx = wbase + i * 32;
-      key[i] = idx < n ? p[idx] : (K)0;
-    }
-    if (pass == 0) {
-      // first pass: the input order carries nothing, so any order of equal
-      // digits is correct -- one shared atomic per key gives its rank.  Keys
-      // that tie on every sorted bit are identical (the bits above are zero),
-      // so the sorted output equals that of a stable sort.
-#pragma unroll
-      for (int i = 0; i < kItemsC; ++i)
-        rank[i] = wbase + i * 32 < n ? atomicAdd(&whist[warp][digit(key[i], shift, mask)], 1u) : 0u;
-    } else {
-      // later passes: stable rank within the warp -- peers with the same
-      // digit, in (i, lane) order
-#pragma unroll
-      for (int i = 0; i < kItemsC; ++i) {
-        const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d != 0xFFFFFFFFu) before = whist[warp][d];
-        rank[i] = before + __popc(peers & lt_mask);
-        __syncwarp();
-        if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
-          whist[warp][d] = before + __popc(peers);
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-
-    // thread d owns digit d: prefix over warps, tile count, publish aggregate
-    const uint32_t d = threadIdx.x;
-    uint32_t cnt = 0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t c = whist[w][d];
-      whist[w][d] = cnt;
-      cnt += c;
-    }
-    const bool first = (t == sg.tile0);
-    unsigned long long* my = status + (unsigned long long)t * kRadix + d;
-    st_put(my, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, cnt));
-    unsigned long long tot;
-    const unsigned long long ts = block_excl_scan(cnt, s_scan, &tot);
-    tstart[d] = (uint32_t)ts;
-    // per-digit lookback over earlier tiles of this segment
-    unsigned long long excl = 0;
-    if (!first) {
-      long long j = (long long)t - 1;
-      for (;;) {
-        unsigned long long s = st_get(status + (unsigned long long)j * kRadix + d);
-        uint32_t spins = 0;
-        while (!st_ready(s, epoch)) {
-          if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) break;
-          __nanosleep(64);
-          s = st_get(status + (unsigned long long)j * kRadix + d);
-        }
-        if (!st_ready(s, epoch)) {
-          if (!*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
-          s_bad = 1;
-          break;
-        }
-        excl += s & kValMask;
-        if (((s >> 38) & 3u) == FLAG_INC || j == (long long)sg.tile0) break;
-        --j;
-      }
-      st_put(my, st_pack(epoch, FLAG_INC, excl + cnt));
-    }
-    const unsigned long long* hbase =
-        stp->hist + ((unsigned long long)k * passes + pass) * kRadix;
-    gdst[d] = sg.out_off + hbase[d] + excl - ts;
-    __syncthreads();
-    if (s_bad) return;  // a lookback gave up: the run is void, write nothing
-
-    // scatter into shared memory in digit order, then stream runs out
+  for (int i = 0; i < kItemsC; ++i) {
+    const uint32_t idx = wbase + i * 32;
+    key[i] = idx < n ? p[idx] : (K)0;
+  }
+  if (pass == 0) {
+    // first pass: the input order carries nothing, so any order of equal
+    // digits is correct -- one shared atomic per key gives its rank.  Keys
+    // that tie on every sorted bit are identical (the bits above are zero),
+    // so the sorted output equals that of a stable sort.
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i)
-      if (wbase + i * 32 < n) {
-        const uint32_t dg = digit(key[i], shift, mask);
-        sk[tstart[dg] + whist[warp][dg] + rank[i]] = key[i];
+      rank[i] = wbase + i * 32 < n ? atomicAdd(&S.whist[warp][digit(key[i], shift, mask)], 1u) : 0u;
+  } else {
+    // later passes: stable rank within the warp -- peers with the same
+    // digit, in (i, lane) order
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = 0;
+      if (d != 0xFFFFFFFFu) before = S.whist[warp][d];
+      rank[i] = before + __popc(peers & lt_mask);
+      __syncwarp();
+      if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
+        S.whist[warp][d] = before + __popc(peers);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // thread d owns digit d: prefix over warps, tile count, publish it
+  const uint32_t d = threadIdx.x;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = S.whist[w][d];
+    S.whist[w][d] = cnt;
+    cnt += c;
+  }
+  const bool first = (t == sg.tile0);
+  st_put(stp->status + (unsigned long long)t * kRadix + d,
+         st_pack(stp->epoch, first ? FLAG_INC : FLAG_AGG, cnt));
+  unsigned long long tot;
+  const unsigned long long ts = block_excl_scan(cnt, S.s_scan, &tot);
+  S.tstart[sl][d] = (uint32_t)ts;
+  S.tcnt[sl][d] = cnt;
+  if (threadIdx.x == 0) S.meta[sl] = PassMeta{t, k, n, first ? 1u : 0u};
+  __syncthreads();
+  // the tile in digit order: a key's place inside the tile needs no global offset
+#pragma unroll
+  for (int i = 0; i < kItemsC; ++i)
+    if (wbase + i * 32 < n) {
+      const uint32_t dg = digit(key[i], shift, mask);
+      S.sk[sl][S.tstart[sl][dg] + S.whist[warp][dg] + rank[i]] = key[i];
+    }
+}
+
+// Global offsets of the tile in slot `sl` by per-digit lookback, then stream
+// its digit runs out.  False when a lookback gave up (the run is void).
+template <typename K>
+__device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
+  __syncthreads();  // the slot's keys, counts and meta are visible
+  const PassMeta m = S.meta[sl];
+  const Seg& sg = stp->segs[m.k];
+  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u, epoch = stp->epoch;
+  Ctl* ctl = stp->ctl;
+  unsigned long long* status = stp->status;
+  const uint32_t d = threadIdx.x;
+  unsigned long long excl = 0;
+  if (!m.first) {  // per-digit lookback over earlier tiles of this segment
+    const unsigned long long tile0 = sg.tile0;
+    long long j = (long long)m.t - 1;
+    for (;;) {
+      unsigned long long s = st_get(status + (unsigned long long)j * kRadix + d);
+      uint32_t spins = 0;
+      while (!st_ready(s, epoch)) {
+        if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) break;
+        __nanosleep(64);
+        s = st_get(status + (unsigned long long)j * kRadix + d);
       }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) {
-      const K v = sk[i];
-      out[gdst[digit(v, shift, mask)] + i] = v;
+      if (!st_ready(s, epoch)) {
+        if (!*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
+        S.s_bad = 1;
+        break;
+      }
+      excl += s & kValMask;
+      if (((s >> 38) & 3u) == FLAG_INC || j == (long long)tile0) break;
+      --j;
+    }
+    st_put(status + (unsigned long long)m.t * kRadix + d,
+           st_pack(epoch, FLAG_INC, excl + S.tcnt[sl][d]));
+  }
+  const unsigned long long* hbase =
+      stp->hist + ((unsigned long long)m.k * stp->passes + stp->pass) * kRadix;
+  S.gdst[d] = sg.out_off + hbase[d] + excl - S.tstart[sl][d];
+  __syncthreads();
+  if (S.s_bad) return false;
+  K* out = (K*)stp->out;
+  for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
+    const K v = S.sk[sl][i];
+    out[S.gdst[digit(v, shift, mask)] + i] = v;
+  }
+  return true;
+}
+
+// One LSD pass (onesweep-style).  With two slots (32-bit keys) a CTA ranks and
+// publishes its next tile before it looks back for the previous one, so the
+// predecessors have had one tile time to publish.  Deadlock-free: ranking and
+// publishing never wait, so the oldest unfinished tile can always complete.
+template <typename K>
+__global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
+  __shared__ PassSmem<K> S;
+  if (*(volatile uint32_t*)&stp->ctl->abort) return;
+  const uint32_t ntiles = stp->ntiles;
+  uint32_t t = claim_tile(stp, &S.s_t);
+  if (t >= ntiles) return;
+  pass_rank<K>(stp, S, t, 0);
+  int cur = 0;
+  for (;;) {
+    if (PassSmem<K>::kSlots == 2) {
+      const uint32_t tn = claim_tile(stp, &S.s_t);
+      const bool more = tn < ntiles;
+      if (more) pass_rank<K>(stp, S, tn, cur ^ 1);
+      if (!pass_write<K>(stp, S, cur) || !more) return;
+      cur ^= 1;
+    } else {
+      if (!pass_write<K>(stp, S, 0)) return;
+      const uint32_t tn = claim_tile(stp, &S.s_t);
+      if (tn >= ntiles) return;
+      pass_rank<K>(stp, S, tn, 0);
     }
   }
 }
