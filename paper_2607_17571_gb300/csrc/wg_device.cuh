@@ -22,7 +22,6 @@ constexpr int kTileD = kThreads * kItemsD;    // 2048 delta tuples per tile
 constexpr int kTileM = 4096;                  // merge output tile
 constexpr int kRadix = 256;                   // digit buckets (digits of <= 8 bits)
 constexpr int kMaxPasses = 8;
-constexpr int kEmitWin = 2048;                // delta tuples staged in smem by emit
 constexpr int kFWin = 2048;                   // full-relation keys staged by dedup/diff
 constexpr uint32_t kSpinLimit = 1u << 22;     // polls before a lookback gives up
 

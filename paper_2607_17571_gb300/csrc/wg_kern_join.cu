@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
   __shared__ unsigned long long sp[kTileD];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_excl;
+  __shared__ unsigned long long s_xl[kThreads];  // candidates per source of the tile
   __shared__ uint32_t s_t, s_bad;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
     const K* p = D + sg.in_off + start;
     tile_to_smem<kItemsD>(sd, p, n, Ident());
     if (threadIdx.x == 0) s_bad = 0;
+    s_xl[threadIdx.x] = 0;
     __syncthreads();
     const uint32_t b = threadIdx.x * kItemsD;
     unsigned long long c[kItemsD], sum = 0;
@@ -105,26 +107,38 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
         sum += c[i];
       }
     }
+    // candidates per source x.  Delta is sorted by x, so the tile's sources
+    // span [x_lo, x_hi] and each thread sees runs of one x: a run adds into a
+    // shared counter when the span is narrow (one global atomic per source
+    // after the scan), else straight into global memory.
+    const uint32_t x_lo = (uint32_t)(sd[0] >> w), x_hi = (uint32_t)(sd[n - 1] >> w);
+    const bool narrow = x_hi - x_lo < (uint32_t)kThreads;
     if (stp->xlen) {
-      // candidates per source x (Delta is sorted by x: one atomic per run)
       uint32_t px = 0xFFFFFFFFu;
       unsigned long long run = 0;
+      auto flush = [&]() {
+        if (!run) return;
+        if (narrow) atomicAdd(&s_xl[px - x_lo], run);
+        else atomicAdd(stp->xlen + px, run);
+      };
 #pragma unroll
       for (int i = 0; i < kItemsD; ++i) {
         if (b + i < n) {
           const uint32_t x = (uint32_t)(sd[b + i] >> w);
           if (x != px) {
-            if (run) atomicAdd(stp->xlen + px, run);
+            flush();
             px = x;
             run = 0;
           }
           run += c[i];
         }
       }
-      if (run) atomicAdd(stp->xlen + px, run);
+      flush();
     }
     unsigned long long tot;
-    const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);
+    const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);  // barriers: s_xl is complete
+    if (stp->xlen && narrow && threadIdx.x <= x_hi - x_lo && s_xl[threadIdx.x])
+      atomicAdd(stp->xlen + x_lo + threadIdx.x, s_xl[threadIdx.x]);
     const bool first = (t == sg.tile0);
     if (threadIdx.x == 0) st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, tot));
     if (!first && threadIdx.x < 32) {
@@ -152,29 +166,32 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
 
 // ------------------------------------------------------------------ join emit
 // Load-balanced over output positions: a tile is kTileC consecutive
-// candidates of one instance, made in three rounds of memory traffic.
-//  1. The delta tuples whose slabs cover the tile -- from the slab owner of
-//     the tile's first candidate to that of the next tile's first -- become a
-//     slab table in shared memory: tile-relative slab start, and the CSR
-//     offsets the slab reads (every load of the round in flight at once).
-//  2. Thread t walks the table for its kItemsC consecutive candidates
-//     (shared memory only), then issues all their adjacency loads at once.
-//  3. Candidates go through shared memory so the global stores coalesce.
-// A tile covering more than kEmitWin delta tuples (long runs of empty slabs)
-// walks the delta tuples in global memory instead.
+// candidates of one instance.  The delta tuples whose slabs cover the tile --
+// from the slab owner of the tile's first candidate to that of the next
+// tile's first -- are taken in chunks of EmitWin<K>::n:
+//  1. a chunk becomes a slab table in shared memory: tile-relative slab
+//     start and the CSR offsets the slab reads (every load of the round in
+//     flight at once);
+//  2. thread t walks the table for those of its kItemsC consecutive
+//     candidates that the chunk covers (shared memory only), then issues all
+//     their adjacency loads at once and stages the candidates.
+// Most tiles take one chunk; a long run of empty slabs (sinks) takes more.
+// The staged tile leaves with coalesced stores.
+template <typename K> struct EmitWin {
+  static constexpr int n = sizeof(K) == 4 ? 1536 : 512;  // table + staging < 48 KB
+};
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
-  constexpr int kSlabBytes = kEmitWin * 4 * (int)sizeof(uint32_t);
-  constexpr int kOutBytes = Padded<kTileC>::n * (int)sizeof(K);
-  __shared__ __align__(16) unsigned char smem[kSlabBytes > kOutBytes ? kSlabBytes : kOutBytes];
-  uint32_t* s_start = (uint32_t*)smem;  // slab's first candidate, relative to the tile
-  uint32_t* s_x = s_start + kEmitWin;   // TC: x            SG: off[x]
-  uint32_t* s_a = s_x + kEmitWin;       // TC: adj index of the slab's candidate 0 of the tile
-                                        // SG: off[y] (recursive rule)
-  uint32_t* s_d = s_a + kEmitWin;       // SG: divisor that splits a slab index in two
-  K* sout = (K*)smem;                   // reused once every thread holds its candidates
+  constexpr int W = EmitWin<K>::n;
+  __shared__ uint32_t s_start[W];  // slab's first candidate, relative to the tile
+  __shared__ uint32_t s_x[W];      // TC: x            SG: off[x]
+  __shared__ uint32_t s_a[W];      // TC: adj index of the slab's candidate 0 of the tile
+                                   // SG: off[y] (recursive rule)
+  __shared__ uint32_t s_d[W];      // SG: divisor that splits a slab index in two
+  __shared__ K sout[Padded<kTileC>::n];
   __shared__ unsigned long long s_i0, s_i1;
-  __shared__ uint32_t s_r0, s_t;
+  __shared__ uint32_t s_r0, s_ce, s_t;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   const K* D = (const K*)stp->in;
@@ -190,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     const uint32_t* off = I->off;
     const uint32_t* adj = I->adj;
     const uint32_t w = I->w, kind = I->kind, iter = I->iter;
+    const bool tc = kind == KIND_TC;
     const K mask = (K)(((K)1 << w) - 1);
     const unsigned long long* P = pos_all + sg.in_off;
     const K* Dq = D + sg.in_off;
@@ -208,142 +226,102 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     }
     __syncthreads();
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
-    const bool staged = m <= (unsigned long long)kEmitWin;
-    if (staged) {  // round 1: the slab table
-      constexpr int kPer = kEmitWin / kThreads;
-      unsigned long long p[kPer];
-      K key[kPer];
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) {
-        const uint32_t i = threadIdx.x + e * kThreads;
-        p[e] = i < m ? P[i0 + i] : 0ull;
-        key[e] = i < m ? Dq[i0 + i] : (K)0;
-      }
-#pragma unroll
-      for (int e = 0; e < kPer; ++e) {
-        const uint32_t i = threadIdx.x + e * kThreads;
-        if (i < m) {
-          const uint32_t x = (uint32_t)(key[e] >> w), y = (uint32_t)(key[e] & mask);
-          // slab i0 starts at or before o0 (r0 of its candidates precede the
-          // tile); slabs after it start inside (o0, o1]
-          const uint32_t r0 = i == 0 ? (uint32_t)(o0 - p[e]) : 0u;
-          s_start[i] = i == 0 ? 0u : (uint32_t)(p[e] - o0);
-          if (kind == KIND_TC) {
-            s_x[i] = x;
-            s_a[i] = off[y] + r0;                                 // T(x,y), E(y,z)
-          } else {
-            const uint32_t ox = off[x];
-            s_x[i] = ox;
-            if (iter == 0) {
-              s_a[i] = 0;
-              s_d[i] = off[x + 1] - ox - 1;                       // distinct children of x
-            } else {
-              const uint32_t oy = off[y];
-              s_a[i] = oy;
-              s_d[i] = off[y + 1] - oy;                           // E(a,x), sg(a,b), E(b,y)
-            }
-            if (i == 0) s_r0 = r0;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    K out[kItemsC];
     const uint32_t q0 = threadIdx.x * kItemsC;
+    for (unsigned long long c0 = 0; c0 < m; c0 += W) {
+      const uint32_t mc = (uint32_t)min((unsigned long long)W, m - c0);
+      {  // round 1: the chunk's slab table
+        constexpr int kPer = (W + kThreads - 1) / kThreads;
+        unsigned long long p[kPer];
+        K key[kPer];
 #pragma unroll
-    for (int e = 0; e < kItemsC; ++e) out[e] = 0;
-    if (q0 < nout && staged) {  // round 2: walk the table, then the adjacency loads
-      uint32_t u[kItemsC], v[kItemsC];  // TC: x, adj index; SG: two adj indices
-      uint32_t lo = 0, hi = (uint32_t)m;  // largest i with s_start[i] <= q0
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_start[mid] <= q0) lo = mid; else hi = mid;
-      }
-      uint32_t i = lo;
-      uint32_t nxt = i + 1 < m ? s_start[i + 1] : 0xFFFFFFFFu;
+        for (int e = 0; e < kPer; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          p[e] = i < mc ? P[i0 + c0 + i] : 0ull;
+          key[e] = i < mc ? Dq[i0 + c0 + i] : (K)0;
+        }
+        if (threadIdx.x == 0)  // the chunk covers candidates [its first slab's start, s_ce)
+          s_ce = c0 + mc < m ? (uint32_t)(P[i0 + c0 + mc] - o0) : nout;
 #pragma unroll
-      for (int e = 0; e < kItemsC; ++e) {
-        const uint32_t j = q0 + e;
-        u[e] = 0;
-        v[e] = 0;
-        if (j < nout) {
-          while (j >= nxt) {  // skip to the slab holding j (empty slabs share a start)
-            ++i;
-            nxt = i + 1 < m ? s_start[i + 1] : 0xFFFFFFFFu;
-          }
-          const uint32_t r = j - s_start[i];
-          if (kind == KIND_TC) {
-            u[e] = s_x[i];
-            v[e] = s_a[i] + r;
-          } else {
-            const uint32_t rr = r + (i == 0 ? s_r0 : 0u), d = s_d[i];
-            const uint32_t qa = rr / d;
-            uint32_t qb = rr - qa * d;
-            if (iter == 0) {
-              qb += qb >= qa;
-              u[e] = s_x[i] + qa;
-              v[e] = s_x[i] + qb;
+        for (int e = 0; e < kPer; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          if (i < mc) {
+            const bool head = c0 == 0 && i == 0;  // the slab owning the tile's first candidate
+            const uint32_t x = (uint32_t)(key[e] >> w), y = (uint32_t)(key[e] & mask);
+            // slab i0 starts at or before o0 (r0 of its candidates precede the
+            // tile); slabs after it start inside (o0, o1]
+            const uint32_t r0 = head ? (uint32_t)(o0 - p[e]) : 0u;
+            s_start[i] = head ? 0u : (uint32_t)(p[e] - o0);
+            if (tc) {
+              s_x[i] = x;
+              s_a[i] = off[y] + r0;                                 // T(x,y), E(y,z)
             } else {
-              u[e] = s_x[i] + qa;
-              v[e] = s_a[i] + qb;
+              const uint32_t ox = off[x];
+              s_x[i] = ox;
+              if (iter == 0) {
+                s_a[i] = 0;
+                s_d[i] = off[x + 1] - ox - 1;                       // distinct children of x
+              } else {
+                const uint32_t oy = off[y];
+                s_a[i] = oy;
+                s_d[i] = off[y + 1] - oy;                           // E(a,x), sg(a,b), E(b,y)
+              }
+              if (head) s_r0 = r0;
             }
           }
         }
       }
-#pragma unroll
-      for (int e = 0; e < kItemsC; ++e) {
-        if (q0 + e < nout) {
-          if (kind == KIND_TC) out[e] = ((K)u[e] << w) | (K)adj[v[e]];
-          else out[e] = ((K)adj[u[e]] << w) | (K)adj[v[e]];
+      __syncthreads();
+      // round 2: this thread's candidates inside the chunk's range
+      const uint32_t cs = s_start[0], ce = s_ce;
+      const uint32_t j0 = max(q0, cs), j1 = min(q0 + kItemsC, ce);
+      if (j0 < j1) {
+        uint32_t u[kItemsC], v[kItemsC];  // TC: x, adj index; SG: two adj indices
+        uint32_t lo = 0, hi = mc;         // largest i with s_start[i] <= j0
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (s_start[mid] <= j0) lo = mid; else hi = mid;
         }
-      }
-    } else if (q0 < nout) {  // many empty slabs: walk the delta tuples in global memory
-      const unsigned long long o = o0 + q0;
-      unsigned long long lo = 0, hi = m;  // largest i with pos[i] <= o
-      while (hi - lo > 1) {
-        const unsigned long long mid = (lo + hi) >> 1;
-        if (P[i0 + mid] <= o) lo = mid; else hi = mid;
-      }
-      unsigned long long i = lo;
-      unsigned long long base = P[i0 + i];
-      unsigned long long nextb = i + 1 < m ? P[i0 + i + 1] : ~0ull;
-      K key = Dq[i0 + i];
-      uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
-      uint32_t ox = off[x], oy = off[y], dy = off[y + 1] - oy, dx = off[x + 1] - ox;
+        uint32_t i = lo;
+        uint32_t nxt = i + 1 < mc ? s_start[i + 1] : 0xFFFFFFFFu;
 #pragma unroll
-      for (int e = 0; e < kItemsC; ++e) {
-        const unsigned long long oe = o + e;
-        if (q0 + e < nout) {
-          while (oe >= nextb) {
-            ++i;
-            base = nextb;
-            nextb = i + 1 < m ? P[i0 + i + 1] : ~0ull;
-            if (oe < nextb) {
-              key = Dq[i0 + i];
-              x = (uint32_t)(key >> w); y = (uint32_t)(key & mask);
-              ox = off[x]; oy = off[y]; dy = off[y + 1] - oy; dx = off[x + 1] - ox;
+        for (int e = 0; e < kItemsC; ++e) {
+          const uint32_t j = q0 + e;
+          u[e] = 0;
+          v[e] = 0;
+          if (j >= j0 && j < j1) {
+            while (j >= nxt) {  // skip to the slab holding j (empty slabs share a start)
+              ++i;
+              nxt = i + 1 < mc ? s_start[i + 1] : 0xFFFFFFFFu;
+            }
+            const uint32_t r = j - s_start[i];
+            if (tc) {
+              u[e] = s_x[i];
+              v[e] = s_a[i] + r;
+            } else {
+              const uint32_t rr = r + (c0 == 0 && i == 0 ? s_r0 : 0u), d = s_d[i];
+              const uint32_t qa = rr / d;
+              uint32_t qb = rr - qa * d;
+              if (iter == 0) {
+                qb += qb >= qa;
+                u[e] = s_x[i] + qa;
+                v[e] = s_x[i] + qb;
+              } else {
+                u[e] = s_x[i] + qa;
+                v[e] = s_a[i] + qb;
+              }
             }
           }
-          const uint32_t r = (uint32_t)(oe - base);
-          if (kind == KIND_TC) {
-            out[e] = ((K)x << w) | (K)adj[oy + r];
-          } else if (iter == 0) {
-            const uint32_t dm1 = dx - 1;
-            const uint32_t qa = r / dm1;
-            uint32_t qb = r - qa * dm1;
-            qb += qb >= qa;
-            out[e] = ((K)adj[ox + qa] << w) | (K)adj[ox + qb];
-          } else {
-            const uint32_t qa = r / dy, qb = r - qa * dy;
-            out[e] = ((K)adj[ox + qa] << w) | (K)adj[oy + qb];
-          }
+        }
+#pragma unroll
+        for (int e = 0; e < kItemsC; ++e) {
+          const uint32_t j = q0 + e;
+          if (j >= j0 && j < j1)
+            sout[pad32(j)] = tc ? (((K)u[e] << w) | (K)adj[v[e]])
+                                : (((K)adj[u[e]] << w) | (K)adj[v[e]]);
         }
       }
+      __syncthreads();  // the table is read; the next chunk may overwrite it
     }
-    __syncthreads();  // round 3: the slab table is dead, stage the candidates
-#pragma unroll
-    for (int e = 0; e < kItemsC; ++e) sout[pad32(q0 + e)] = out[e];
-    __syncthreads();
     K* Cq = C + sg.out_off + o0;
     for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
   }
