@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
   __shared__ unsigned long long sp[kTileD];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_excl;
-  __shared__ unsigned long long s_xl[kThreads];  // candidates per source of the tile
+  __shared__ uint32_t s_xprev, s_xnext;  // sources of the delta tuples around the tile
   __shared__ uint32_t s_t, s_bad;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
@@ -85,8 +85,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
     const uint32_t n = (uint32_t)min((unsigned long long)kTileD, sg.n - start);
     const K* p = D + sg.in_off + start;
     tile_to_smem<kItemsD>(sd, p, n, Ident());
-    if (threadIdx.x == 0) s_bad = 0;
-    s_xl[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      s_bad = 0;
+      s_xprev = start > 0 ? (uint32_t)(p[-1] >> w) : 0xFFFFFFFFu;
+      s_xnext = start + n < sg.n ? (uint32_t)(p[n] >> w) : 0xFFFFFFFFu;
+    }
     __syncthreads();
     const uint32_t b = threadIdx.x * kItemsD;
     unsigned long long c[kItemsD], sum = 0;
@@ -107,38 +110,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
         sum += c[i];
       }
     }
-    // candidates per source x.  Delta is sorted by x, so the tile's sources
-    // span [x_lo, x_hi] and each thread sees runs of one x: a run adds into a
-    // shared counter when the span is narrow (one global atomic per source
-    // after the scan), else straight into global memory.
-    const uint32_t x_lo = (uint32_t)(sd[0] >> w), x_hi = (uint32_t)(sd[n - 1] >> w);
-    const bool narrow = x_hi - x_lo < (uint32_t)kThreads;
-    if (stp->xlen) {
-      uint32_t px = 0xFFFFFFFFu;
-      unsigned long long run = 0;
-      auto flush = [&]() {
-        if (!run) return;
-        if (narrow) atomicAdd(&s_xl[px - x_lo], run);
-        else atomicAdd(stp->xlen + px, run);
-      };
-#pragma unroll
-      for (int i = 0; i < kItemsD; ++i) {
-        if (b + i < n) {
-          const uint32_t x = (uint32_t)(sd[b + i] >> w);
-          if (x != px) {
-            flush();
-            px = x;
-            run = 0;
-          }
-          run += c[i];
-        }
-      }
-      flush();
-    }
     unsigned long long tot;
-    const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);  // barriers: s_xl is complete
-    if (stp->xlen && narrow && threadIdx.x <= x_hi - x_lo && s_xl[threadIdx.x])
-      atomicAdd(stp->xlen + x_lo + threadIdx.x, s_xl[threadIdx.x]);
+    const unsigned long long texcl = block_excl_scan(sum, s_scan, &tot);
     const bool first = (t == sg.tile0);
     if (threadIdx.x == 0) st_put(status + t, st_pack(epoch, first ? FLAG_INC : FLAG_AGG, tot));
     if (!first && threadIdx.x < 32) {
@@ -157,6 +130,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
 #pragma unroll
     for (int i = 0; i < kItemsD; ++i)
       if (b + i < n) { sp[b + i] = run; run += c[i]; }
+    if (stp->xlen) {
+      // candidates per source x.  Delta is sorted by x, so x's tuples are one
+      // run and its total is (prefix at the run's end) - (prefix at its
+      // start): one atomic where the run starts, one where it ends.
+      unsigned long long r = s_excl + texcl;
+#pragma unroll
+      for (int i = 0; i < kItemsD; ++i) {
+        if (b + i < n) {
+          const uint32_t x = (uint32_t)(sd[b + i] >> w);
+          const uint32_t xp = b + i > 0 ? (uint32_t)(sd[b + i - 1] >> w) : s_xprev;
+          const uint32_t xn = b + i + 1 < n ? (uint32_t)(sd[b + i + 1] >> w) : s_xnext;
+          if (x != xp) atomicAdd(stp->xlen + x, 0ull - r);
+          r += c[i];
+          if (x != xn) atomicAdd(stp->xlen + x, r);
+        }
+      }
+    }
     __syncthreads();
     unsigned long long* q = pos + sg.in_off + start;
     for (uint32_t i = threadIdx.x; i < n; i += kThreads) q[i] = sp[i];
