@@ -46,6 +46,8 @@ def _load():
                                        ctypes.c_int, u64pp, szp,
                                        ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, u32p]
+        lib.oracle_triangles.restype = ctypes.c_uint64
+        lib.oracle_triangles.argtypes = [u32p, u32p, ctypes.c_size_t, ctypes.c_int]
         lib.oracle_free.restype = None
         lib.oracle_free.argtypes = [ctypes.c_void_p]
         _lib = lib
@@ -124,3 +126,12 @@ def oracle_tc_rows(src, dst, sources, n_threads: int = 1, log_cap: int = 4096):
     keys = np.ctypeslib.as_array(kp, shape=(nk.value + 1,))[: nk.value].copy()
     lib.oracle_free(kp)
     return keys, row_len[: sources.shape[0]], log_sum, int(mx.value)
+
+
+def oracle_triangles(src, dst, n_threads: int = 1) -> int:
+    """Number of tuples of triangle(a,b,c) <- edge(a,b), edge(b,c), edge(c,a)
+    (Sec. Generalization, "Triangle Counting"); edges are a set."""
+    lib = _load()
+    src, dst = _u32(src), _u32(dst)
+    assert src.shape == dst.shape
+    return int(lib.oracle_triangles(_ptr32(src), _ptr32(dst), src.shape[0], int(n_threads)))

@@ -29,6 +29,9 @@
 // Binary-Search Join.  Full is a std::set<uint64_t>.  Nothing is blocked,
 // fused or reordered beyond the five steps above.
 //
+// oracle_triangles counts the tuples of the non-recursive triangle rule
+// (Sec. Generalization, "Triangle Counting") with the same range lookup.
+//
 // oracle_tc_rows runs the same five steps on the rows T(x, .) of chosen
 // sources x, one row at a time: the TC recursive rule never changes the first
 // component, so row x of T, and row x of every Delta^i, depend only on row x of
@@ -137,6 +140,33 @@ Result sg(const std::vector<Key>& E, uint32_t max_iters) {
   });
 }
 
+// Triangle counting (Sec. Generalization, "Triangle Counting"): the number of
+// tuples of  triangle(a,b,c) <- edge(a,b), edge(b,c), edge(c,a),  a single
+// non-recursive pass.  Each (a,b) in E takes the edges (b,c) from the
+// binary-search range lookup and tests edge(c,a) by binary search in E.  The
+// edges are split over threads; each thread counts its own share.
+uint64_t triangles(const std::vector<Key>& E, int n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  std::vector<uint64_t> part(n_threads, 0);
+  auto work = [&](int t) {
+    uint64_t n = 0;
+    for (size_t i = t; i < E.size(); i += n_threads) {
+      const uint32_t a = src_of(E[i]), b = dst_of(E[i]);
+      auto [lo, hi] = edges_from(E, b);
+      for (size_t j = lo; j < hi; ++j)
+        if (std::binary_search(E.begin(), E.end(), pack(dst_of(E[j]), a))) ++n;
+    }
+    part[t] = n;
+  };
+  std::vector<std::thread> ths;
+  for (int t = 1; t < n_threads; ++t) ths.emplace_back(work, t);
+  work(0);
+  for (auto& th : ths) th.join();
+  uint64_t n = 0;
+  for (uint64_t v : part) n += v;
+  return n;
+}
+
 int export_result(const Result& r, uint64_t** keys, size_t* n_keys, uint64_t** log,
                   size_t* n_log, uint32_t* iters) {
   *n_keys = r.full.size();
@@ -214,5 +244,10 @@ int oracle_tc_rows(const uint32_t* src, const uint32_t* dst, size_t n, const uin
 }
 
 void oracle_free(void* p) { std::free(p); }
+
+// Number of tuples of triangle(a,b,c) over the edge set {(src[i], dst[i])}.
+uint64_t oracle_triangles(const uint32_t* src, const uint32_t* dst, size_t n, int n_threads) {
+  return triangles(edge_set(src, dst, n), n_threads);
+}
 
 }  // extern "C"

@@ -150,6 +150,18 @@ def rmat_dag(scale: int, n_edges: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05))
                                     abcd=list(abcd)))
 
 
+def rmat_sym(scale: int, n_pairs: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05)) -> EdgeList:
+    """Undirected R-MAT graph as a symmetric edge list: the ``n_pairs``
+    distinct pairs u < v of ``rmat_dag`` in both directions (2 * n_pairs
+    edges, no self-loops) -- the shape of the undirected graphs triangle
+    counting runs on."""
+    g = rmat_dag(scale, n_pairs, seed, abcd)
+    src = np.concatenate([g.src, g.dst])
+    dst = np.concatenate([g.dst, g.src])
+    return EdgeList(src, dst, dict(family="rmat_sym", scale=scale, n_pairs=n_pairs, seed=seed,
+                                   abcd=list(abcd)))
+
+
 def rmat_dag16(scale: int, n_edges: int, seed: int, abcd=(0.57, 0.19, 0.19, 0.05)) -> EdgeList:
     """The rmat_dag recipe (quadrant recursion, random relabel, src < dst,
     distinct, exactly ``n_edges``) drawing 16-bit uniforms: one splitmix64
@@ -338,4 +350,6 @@ def workload(name: str) -> EdgeList:
         return sg_forest(60_000, 40, 2.0, 0.01, seed=3)
     if name == "tc_rmat15_100k":  # a smaller skewed case (profiling captures)
         return rmat_dag(15, 100_000, seed=2)
+    if name == "tri_rmat16_800k":  # triangle counting: undirected, 800k directed edges
+        return rmat_sym(16, 400_000, seed=6)
     raise KeyError(name)

@@ -71,3 +71,12 @@ def test_batch_sizes():
     assert np.all(m >= np.round(1.2 * n) - 1) and np.all(m <= np.round(3.0 * n) + 1)
     # log-uniform: the median sits near sqrt(64 * 16384) = 1024
     assert 700 < np.median(n) < 1500
+
+
+def test_rmat_sym_is_symmetric_loop_free_and_distinct():
+    g = I.rmat_sym(10, 2000, 4)
+    assert len(g) == 4000
+    k = (g.src.astype(np.uint64) << np.uint64(32)) | g.dst
+    assert len(np.unique(k)) == 4000 and not np.any(g.src == g.dst)
+    rev = (g.dst.astype(np.uint64) << np.uint64(32)) | g.src
+    assert np.array_equal(np.sort(k), np.sort(rev))
