@@ -429,6 +429,110 @@ def run_batch(args):
     return 0
 
 
+def run_triangles(args):
+    """Triangle counting (Sec. Generalization, "Triangle Counting") on an
+    undirected R-MAT graph (2^16 nodes, 400k pairs = 800k directed edges)
+    standing in for the paper's SNAP graphs.  One step = one wg_triangles call
+    on the resident relation.  Its edges and CSR (~3.5 MB) live in L2, so the
+    probe is latency-bound, not HBM-bound: the line reports milliseconds per
+    count and two-paths probed per second, with no HBM roofline."""
+    import torch
+
+    import oracle
+    from paper_2607_17571_gb300 import inputs as I
+    from paper_2607_17571_gb300 import wg
+
+    g = I.workload("tri_rmat16_800k")
+    n = len(g)
+    deg = np.bincount(g.src, minlength=int(max(g.src.max(), g.dst.max())) + 1)
+    paths = int(deg[g.dst].astype(np.int64).sum())   # two-paths (a,b,c): sum of deg(b)
+    if args.impl == "reference":  # the oracle as it stands, on the host cores
+        threads = os.cpu_count()
+        for _ in range(args.warmup if args.warmup < 1 else 1):
+            oracle.oracle_triangles(g.src, g.dst, n_threads=threads)
+        dts = []
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            want = oracle.oracle_triangles(g.src, g.dst, n_threads=threads)
+            dts.append(time.perf_counter() - t)
+        v = paths / statistics.mean(dts)
+        print(json.dumps({"impl": "reference", "metric": "triangle count: two-paths probed/s",
+                          "value": v, "unit": "two-paths/s", "n_gpus": 1, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(dts), 1),
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "u64", "data": "synthetic",
+                          "config": {"workload": "tri_rmat16_800k", "triangles": want},
+                          "cpu_baseline": {"value": v, "unit": "two-paths/s", "cores": threads,
+                                           "kind": "oracle", "sample": "whole count"},
+                          "e2e": {"value": v, "unit": "two-paths/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return 0
+    torch.cuda.set_device(0)
+    ctx = wg.Context(0)
+    stream = ctx.torch_stream
+    rel = ctx.load(g.src, g.dst)
+    count = None
+    for _ in range(args.warmup):
+        count = ctx.triangles(rel)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    ms = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        count = ctx.triangles(rel)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = statistics.mean(ms)
+    # end to end: pinned edge list -> relation load -> count -> 8-byte result
+    src_h, dst_h = wg.pinned(n, np.uint32), wg.pinned(n, np.uint32)
+    src_h[:], dst_h[:] = g.src, g.dst
+    e2e_ms = []
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r2 = ctx.load(src_h, dst_h)
+        c2 = ctx.triangles(r2)
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+        r2.free()
+        assert c2 == count
+    cpu = None
+    if not args.no_cpu_baseline:
+        threads = os.cpu_count()
+        t = time.perf_counter()
+        want = oracle.oracle_triangles(g.src, g.dst, n_threads=threads)
+        dt = time.perf_counter() - t
+        cpu = dict(value=paths / dt, unit="two-paths/s", cores=threads, kind="oracle",
+                   sample=f"whole count ({want} triangles, {dt:.1f} s)", matches=want == count)
+    e2e_mean = statistics.mean(e2e_ms)
+    line = {"metric": "triangle count: two-paths probed/s", "value": paths / (t_ms / 1e3),
+            "unit": "two-paths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t_ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "tri_rmat16_800k",
+                       "desc": "undirected R-MAT(.57,.19,.19,.05) 2^16 nodes, 400k distinct pairs "
+                               "in both directions, seed 6", "edges": n,
+                       "max_degree": int(deg.max()), "two_paths": paths, "triangles": count,
+                       "l2": "flushed between steps (256 MB write); edges and CSR fit in L2"},
+            "roofline": None,
+            "e2e": {"value": paths / (e2e_mean / 1e3), "unit": "two-paths/s",
+                    "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8,
+                    "ms_per_step": round(e2e_mean, 2)},
+            "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": 3 * args.steps}  # join count, partition, probe
+    print(json.dumps(line))
+    rel.free()
+    ctx.close()
+    return 0
+
+
 def run_serve(args):
     """Open-loop Poisson arrivals of a mixed TC / SG request stream (see
     inputs.serve_request), served under a fixed device-memory budget: the
@@ -563,7 +667,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tc_rmat17_400k",
-                    choices=sorted(WORKLOADS) + ["batch4096", "serve"])
+                    choices=sorted(WORKLOADS) + ["batch4096", "serve", "tri_rmat16_800k"])
     ap.add_argument("--n-queries", type=int, default=4096)
     ap.add_argument("--batch-iters", type=int, default=4)
     ap.add_argument("--rates", default="100,200,500,1000,2000,5000")
@@ -585,6 +689,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "tri_rmat16_800k":
+        return run_triangles(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

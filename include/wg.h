@@ -218,6 +218,20 @@ int wg_unique_diff(wg_ctx* ctx, const void* d_cand, size_t n, const void* d_full
 int wg_merge_disjoint(wg_ctx* ctx, const void* d_a, size_t na, const void* d_b, size_t nb,
                       void* d_out, int key_bytes);
 
+/* ---- triangle counting ----------------------------------------------------
+ * wg_triangles: *count = the number of tuples (a, b, c) of
+ *     triangle(a,b,c) <- edge(a,b), edge(b,c), edge(c,a)
+ * over the relation's edge set (Sec. Generalization, "Triangle Counting"; a
+ * single non-recursive pass).  Each edge (a,b) takes its deg(b) two-paths
+ * from the join count, and each two-path (a,b,c) is tested for edge(c,a) by
+ * binary search in c's sorted adjacency (the binary-search join).  A directed
+ * 3-cycle gives 3 tuples, an undirected triangle (both directions of each
+ * edge) 6, a self-loop (a,a,a) 1.  Synchronous on the context stream; scratch
+ * is |E| * 8 bytes plus 8 bytes per 4,096 two-paths.  Errors: WG_E_INVAL (bad
+ * argument or relation), WG_E_NOMEM / WG_E_BUDGET, WG_E_CAPACITY (more than
+ * 2^44 two-paths), WG_E_DEVICE_TIMEOUT. */
+int wg_triangles(wg_ctx* ctx, wg_rel edges, uint64_t* count);
+
 /* ---- allocation-free radix sort ------------------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot allocate device memory -- code running inside another runtime's

@@ -78,6 +78,8 @@ struct Stage {
   uint32_t ctr;                 // dynamic tile counter (zeroed by the writer)
   uint32_t epoch;
   uint32_t shift, dbits, pass, passes;
+  unsigned long long* probe;    // join emit, triangle mode: count of candidates (a,b,c)
+                                // with E(c,a) (nothing is written)
 };
 
 // One fixpoint instance (a query in flight).

@@ -171,7 +171,11 @@ template <typename K> struct EmitWin {
   static constexpr int n = sizeof(K) == 4 ? 1536 : 512;  // table + staging < 48 KB
 };
 
-template <typename K>
+// kProbe (triangle counting, Sec. Generalization "Triangle Counting"): the
+// delta is E itself and every candidate (a, b, c) of E(a,b), E(b,c) is tested
+// for E(c,a) by binary search in c's sorted adjacency -- the binary-search
+// join probe -- and only the number of hits is kept.
+template <typename K, bool kProbe>
 __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
   constexpr int W = EmitWin<K>::n;
   __shared__ uint32_t s_start[W];  // slab's first candidate, relative to the tile
@@ -179,7 +183,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
   __shared__ uint32_t s_a[W];      // TC: adj index of the slab's candidate 0 of the tile
                                    // SG: off[y] (recursive rule)
   __shared__ uint32_t s_d[W];      // SG: divisor that splits a slab index in two
-  __shared__ K sout[Padded<kTileC>::n];
+  __shared__ K sout[kProbe ? 1 : Padded<kTileC>::n];
+  __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_i0, s_i1;
   __shared__ uint32_t s_r0, s_ce, s_t;
   Ctl* ctl = stp->ctl;
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     __syncthreads();
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
     const uint32_t q0 = threadIdx.x * kItemsC;
+    unsigned long long hits = 0;  // triangle mode
     for (unsigned long long c0 = 0; c0 < m; c0 += W) {
       const uint32_t mc = (uint32_t)min((unsigned long long)W, m - c0);
       {  // round 1: the chunk's slab table
@@ -302,18 +308,57 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
             }
           }
         }
+        if constexpr (kProbe) {
+          // candidate (a = u, b, c = adj[v]): is (c, a) an edge?  Four binary
+          // searches at a time, in lockstep, so their loads overlap
 #pragma unroll
-        for (int e = 0; e < kItemsC; ++e) {
-          const uint32_t j = q0 + e;
-          if (j >= j0 && j < j1)
-            sout[pad32(j)] = tc ? (((K)u[e] << w) | (K)adj[v[e]])
-                                : (((K)adj[u[e]] << w) | (K)adj[v[e]]);
+          for (int h = 0; h < kItemsC; h += 4) {
+            uint32_t a[4], lo[4], hi[4], end[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              const uint32_t j = q0 + h + g;
+              const bool ok = j >= j0 && j < j1;
+              const uint32_t c = ok ? adj[v[h + g]] : 0u;
+              a[g] = u[h + g];
+              lo[g] = ok ? off[c] : 0u;
+              end[g] = ok ? off[c + 1] : 0u;
+              hi[g] = end[g];
+            }
+            for (;;) {  // at most log2(max degree) + 1 rounds
+              bool any = false;
+#pragma unroll
+              for (int g = 0; g < 4; ++g) {
+                if (lo[g] < hi[g]) {
+                  const uint32_t mid = (lo[g] + hi[g]) >> 1;
+                  if (adj[mid] < a[g]) lo[g] = mid + 1; else hi[g] = mid;
+                  any = true;
+                }
+              }
+              if (!any) break;
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g) hits += lo[g] < end[g] && adj[lo[g]] == a[g];
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < kItemsC; ++e) {
+            const uint32_t j = q0 + e;
+            if (j >= j0 && j < j1)
+              sout[pad32(j)] = tc ? (((K)u[e] << w) | (K)adj[v[e]])
+                                  : (((K)adj[u[e]] << w) | (K)adj[v[e]]);
+          }
         }
       }
       __syncthreads();  // the table is read; the next chunk may overwrite it
     }
-    K* Cq = C + sg.out_off + o0;
-    for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
+    if constexpr (kProbe) {
+      unsigned long long tot;
+      block_excl_scan(hits, s_scan, &tot);
+      if (threadIdx.x == 0 && tot) atomicAdd(stp->probe, tot);
+    } else {
+      K* Cq = C + sg.out_off + o0;
+      for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
+    }
   }
 }
 
@@ -833,7 +878,9 @@ __global__ void k_result_map(const K* F, unsigned long long n, uint32_t w, const
 template <typename K>
 void launch_join_count(Stage* st, int grid, cudaStream_t s) { k_join_count<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
-void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, false><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_tri_probe(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, true><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 int occupancy_join(int which) {
   // largest shared-memory carveout first (see occupancy_of in wg_kern_sort.cu)
@@ -844,7 +891,8 @@ int occupancy_join(int which) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0);
     return b;
   };
-  return which == 0 ? one(k_join_count<K>) : one(k_join_emit<K>);
+  return which == 0 ? one(k_join_count<K>) : which == 1 ? one(k_join_emit<K, false>)
+                                                         : one(k_join_emit<K, true>);
 }
 void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
@@ -878,6 +926,7 @@ void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint3
 #define WG_INST(K)                                                                          \
   template void launch_join_count<K>(Stage*, int, cudaStream_t);                            \
   template void launch_join_emit<K>(Stage*, int, cudaStream_t);                             \
+  template void launch_tri_probe<K>(Stage*, int, cudaStream_t);                             \
   template int occupancy_join<K>(int);                                                      \
   template void launch_init_diag<K>(Inst*, uint32_t, uint32_t, void*, cudaStream_t);        \
   template void launch_rank_edges<K>(const uint32_t*, const uint32_t*, unsigned long long,  \

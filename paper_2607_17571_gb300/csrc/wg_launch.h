@@ -29,7 +29,8 @@ template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq,
 // join and engine control (wg_kern_join.cu)
 template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
-template <typename K> int occupancy_join(int which);  // 0 count, 1 emit
+template <typename K> void launch_tri_probe(Stage* st, int grid, cudaStream_t s);
+template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 triangle probe
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);

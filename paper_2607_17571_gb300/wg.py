@@ -81,6 +81,7 @@ SIGNATURES = {
     "wg_merge_disjoint": (c_int, [c_void_p, c_void_p, c_size_t, c_void_p, c_size_t, c_void_p,
                                   c_int]),
     "wg_sort_keys_noalloc": (c_int, [c_void_p, c_size_t, c_int, c_uint32, c_void_p]),
+    "wg_triangles": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
 }
 WG_NOALLOC_MAX_KEYS = 1 << 20
 
@@ -290,6 +291,13 @@ class Context:
         o = _opts(**opts)
         _check(self.lib.wg_tc(self.h, rel.id, byref(o), byref(q)), "wg_tc")
         return Query(self, q.value)
+
+    def triangles(self, rel: Relation) -> int:
+        """wg_triangles: number of tuples of triangle(a,b,c) <- edge(a,b),
+        edge(b,c), edge(c,a) over the relation (synchronous)."""
+        n = c_uint64()
+        _check(self.lib.wg_triangles(self.h, rel.id, byref(n)), "wg_triangles")
+        return int(n.value)
 
     def sg(self, rel: Relation, **opts) -> Query:
         q = c_uint64()
