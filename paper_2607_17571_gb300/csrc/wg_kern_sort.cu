@@ -520,11 +520,14 @@ __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, u
   const unsigned long long a0 = *s_a0, a1 = *s_a1, b0 = d0 - a0, b1 = d1 - a1;
   const uint32_t la = (uint32_t)(a1 - a0), lb = (uint32_t)(b1 - b0), L = la + lb;
   {  // Full part then candidate part, every load in flight at once
+    const K* pa0 = A + a0;
+    const K* pb0 = B + b0;
     K v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const uint32_t i = threadIdx.x + e * kThreads;
-      v[e] = i < la ? A[a0 + i] : (i < L ? B[b0 + i - la] : (K)0);
+      const K* src = i < la ? pa0 + i : pb0 + (i - la);
+      v[e] = i < L ? *src : (K)0;
     }
     K pa = 0, pb = 0;
     if (threadIdx.x == 0) {
@@ -561,32 +564,38 @@ __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, u
       i = lo;
       j = q0 - i;
     }
-    bool has = q0 > 0 || *s_hasprev;
-    K prev = q0 > 0 ? (i > 0 ? SA(i - 1) : (K)0) : *s_prev;
-    if (q0 > 0 && j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
-    // merge heads in registers: one shared load per step.  SA(la) is still
-    // inside sbuf (la + lb <= T); an exhausted B side reads as the largest
-    // key, so the A side wins every comparison until it is exhausted too.
+    // the merged predecessor of position q0; with none (the segment's first
+    // element) the complement of that element, so it counts as different
+    K prev;
+    if (q0 > 0) {
+      prev = i > 0 ? SA(i - 1) : (K)0;
+      if (j > 0 && SB(j - 1) > prev) prev = SB(j - 1);
+    } else if (*s_hasprev) {
+      prev = *s_prev;
+    } else {
+      prev = ~((la > 0 && (lb == 0 || SA(0) <= SB(0))) ? SA(0) : SB(0));
+    }
+    // branch-free merge, heads in registers: each step reads the next element
+    // of the side that advanced (index <= L <= T: inside sbuf).  An exhausted
+    // B side reads as the largest key, so A wins every comparison until it is
+    // exhausted too; an exhausted A side is never taken (i < la fails).
     K a = SA(i), b = j < lb ? SB(j) : ~(K)0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       val[e] = 0;
       if (q0 + e < L) {
         const bool takeA = i < la && a <= b;
-        K v;
-        if (takeA) {
-          v = a;
-          a = SA(++i);
-          kept |= 1u << e;
-        } else {
-          v = b;
-          ++j;
-          b = j < lb ? SB(j) : ~(K)0;
-          if (!has || v != prev) { kept |= 1u << e; isN |= 1u << e; }
-        }
+        const K v = takeA ? a : b;
+        const K w = sbuf[pad32(takeA ? i + 1 : la + j + 1)];
+        i += takeA ? 1u : 0u;
+        j += takeA ? 0u : 1u;
+        a = takeA ? w : a;
+        b = takeA ? b : (j < lb ? w : ~(K)0);
+        const bool isnew = !takeA && v != prev;
+        kept |= (takeA || isnew ? 1u : 0u) << e;
+        isN |= (isnew ? 1u : 0u) << e;
         val[e] = v;
         prev = v;
-        has = true;
       }
     }
   }
@@ -619,17 +628,15 @@ __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint
   const Seg& sg = stp->segs[m.k];
   K* Nall = (K*)stp->out;                // new delta
   K* Fall = (K*)stp->out2;               // Full'
-  // new tuples are few: each thread stores its own run of them directly
+  // new tuples are few: each thread stores its own run of them directly,
+  // visiting only the set bits (a new tuple's place among the kept elements
+  // is the number of kept bits below it)
   const uint32_t mk = smask[threadIdx.x], pr = spre[threadIdx.x];
-  const uint32_t kept = mk & 0xFFFFu, isN = mk >> 16;
-  uint32_t wk = pr & 0xFFFFu;
+  const uint32_t kept = mk & 0xFFFFu, wk0 = pr & 0xFFFFu;
   K* no = Nall + sg.out_off + exN + (pr >> 16);
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    if (kept >> e & 1u) {
-      if (isN >> e & 1u) *no++ = sbuf[pad32(wk)];
-      ++wk;
-    }
+  for (uint32_t nb = mk >> 16; nb; nb &= nb - 1) {
+    const uint32_t e = __ffs(nb) - 1;
+    *no++ = sbuf[pad32(wk0 + __popc(kept & ((1u << e) - 1u)))];
   }
   K* fo = Fall + sg.out2_off + m.a0 + exN;
 #pragma unroll
