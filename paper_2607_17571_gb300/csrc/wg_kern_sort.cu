@@ -42,10 +42,17 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
     for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
     tile_to_smem<kItemsC>(sk, p, n, Pad32());
     __syncthreads();
-    // blocked order keeps equal neighbours together: count digit runs, one
-    // shared atomic per run (clustered high digits cost one atomic per run)
+    // the lowest digit of the candidates is close to random: one shared
+    // atomic per key, read in striped order (conflict-free)
+#pragma unroll
+    for (int e = 0; e < kItemsC; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      if (i < n) atomicAdd(&sh[digit(sk[pad32(i)], 0, mask)], 1u);
+    }
+    // higher digits come in runs (sorted adjacency lists, one source per
+    // slab): blocked order keeps equal neighbours together, one atomic per run
     const uint32_t b = threadIdx.x * kItemsC;
-    for (uint32_t ps = 0; ps < passes; ++ps) {
+    for (uint32_t ps = 1; ps < passes; ++ps) {
       const uint32_t shift = ps * dbits;
       uint32_t prev = 0xFFFFFFFFu, run = 0;
 #pragma unroll
