@@ -533,6 +533,77 @@ def run_triangles(args):
     return 0
 
 
+def run_ablations(args):
+    """The paper's engineering ablations (Sec. Evaluation)
+    on one TC workload: each variant is the same fixpoint with one design
+    choice reverted, timed like the main bench (CUDA events, L2 flushed), and
+    every variant's result is checked against the default's.  Variants:
+    default (device loop, fused dedup/diff/merge, adaptive width, ping-pong),
+    separate stages, host-driven loop (one launch per kernel, one host sync per
+    iteration), full-width radix sort, copy-back instead of ping-pong."""
+    import torch
+
+    from paper_2607_17571_gb300 import inputs as I
+    from paper_2607_17571_gb300 import wg
+
+    torch.cuda.set_device(0)
+    name = args.ablate_workload
+    g = I.workload(name)
+    ctx = wg.Context(0)
+    stream = ctx.torch_stream
+    rel = ctx.load(g.src, g.dst)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
+    variants = [("default", {}), ("separate_stages", dict(separate_stages=True)),
+                ("host_loop", dict(loop=wg.WG_LOOP_HOST)), ("full_width", dict(full_width=True)),
+                ("copy_back", dict(copy_back=True))]
+    ref, out = None, []
+    clocks = Clocks(0)
+    clocks.start()
+    for vname, opts in variants:
+        q = ctx.tc(rel, **opts)
+        q.wait()
+        res = q.result()
+        q.free()
+        if ref is None:
+            ref = res
+        same = bool(np.array_equal(res, ref))
+        for _ in range(max(0, args.warmup - 1)):
+            q = ctx.tc(rel, **opts)
+            q.wait()
+            q.free()
+        ms = []
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            q = ctx.tc(rel, **opts)
+            st = q.wait()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            q.free()
+        out.append({"variant": vname, "ms": round(statistics.mean(ms), 3),
+                    "tuples_per_s": st.n_tuples / (statistics.mean(ms) / 1e3),
+                    "same_result": same, "gpu_launches": st.gpu_launches})
+        del res
+    clk = clocks.stop()
+    base = out[0]["ms"]
+    for o in out:
+        o["slowdown_vs_default"] = round(o["ms"] / base, 3)
+    line = {"metric": "ablations: fixpoint ms per variant", "value": base, "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": base,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": name, "desc": WORKLOADS[name]["desc"],
+                       "l2": "flushed between steps (256 MB write)"},
+            "variants": out, "clocks": clk}
+    print(json.dumps(line))
+    rel.free()
+    ctx.close()
+    return 0
+
+
 def run_serve(args):
     """Open-loop Poisson arrivals of a mixed TC / SG request stream (see
     inputs.serve_request), served under a fixed device-memory budget: the
@@ -667,7 +738,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tc_rmat17_400k",
-                    choices=sorted(WORKLOADS) + ["batch4096", "serve", "tri_rmat16_800k"])
+                    choices=sorted(WORKLOADS) + ["batch4096", "serve", "tri_rmat16_800k",
+                                                 "ablations"])
+    ap.add_argument("--ablate-workload", default="tc_rmat17_400k", choices=sorted(WORKLOADS))
     ap.add_argument("--n-queries", type=int, default=4096)
     ap.add_argument("--batch-iters", type=int, default=4)
     ap.add_argument("--rates", default="100,200,500,1000,2000,5000")
@@ -691,6 +764,8 @@ def main():
         return run_serve(args)
     if args.workload == "tri_rmat16_800k":
         return run_triangles(args)
+    if args.workload == "ablations":
+        return run_ablations(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -73,6 +73,15 @@ enum wg_loop {
                                       paper's separate stages (Secs. Fused Deduplication and
                                       Set Difference, Disjoint Merge) instead of one fused
                                       merge-path pass that also writes the merged relation */
+#define WG_FLAG_FULL_WIDTH 2u      /* ablation: radix-sort every key bit (32 or 64) instead of
+                                      only the significant bits, and no per-source sort (the
+                                      fixed-width baseline of Sec. Buffer Routing and Adaptive
+                                      Radix Sort); same result */
+#define WG_FLAG_COPY_BACK 4u       /* ablation (single queries, fused stages): copy the merged
+                                      relation back into the Full buffer every iteration
+                                      instead of swapping the two buffers (the copy-back
+                                      baseline of the paper's ping-pong evaluation); same
+                                      result */
 
 typedef struct wg_opts {
   uint32_t max_iters;    /* iteration cap; 0 = 1<<20 */

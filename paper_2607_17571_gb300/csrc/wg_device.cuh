@@ -153,6 +153,8 @@ struct Dev {
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;
   uint32_t xseg;                      // sort each source's candidates on the low field only
+  uint32_t copyback;                  // single fused engine: copy Full' back into the Full
+                                      // buffer each iteration instead of swapping buffers
   uint32_t count_tile;                // delta tuples per join-count tile
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;

@@ -433,6 +433,7 @@ struct EngineBase {
   virtual uint32_t slots() const = 0;
   virtual bool fused() const = 0;
   virtual bool xgrouped() const = 0;
+  virtual bool copyback() const = 0;
   virtual void release() = 0;
 };
 
@@ -486,16 +487,18 @@ struct Engine : EngineBase {
   uint32_t regrows = 0;
   int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 2 : 0); }
 
+  bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
-         bool xseg_)
+         bool xseg_, bool copy_back_ = false)
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
-        log_cap(logcap) {
+        log_cap(logcap), copy_back(copy_back_) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
   int kb() const override { return (int)sizeof(K); }
   bool fused() const override { return fuse; }
   bool xgrouped() const override { return xseg; }
+  bool copyback() const override { return copy_back; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -541,6 +544,7 @@ struct Engine : EngineBase {
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
     h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
     h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T; h.xseg = xseg ? 1 : 0;
+    h.copyback = copy_back && single && fuse ? 1 : 0;
     h.count_tile = CountTile<K>::T;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
@@ -863,14 +867,15 @@ struct Engine : EngineBase {
 };
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
-                              uint32_t logcap, bool fuse, bool xseg, int* rc) {
+                              uint32_t logcap, bool fuse, bool xseg, int* rc,
+                              bool copyback = false) {
   EngineBase* e;
   if (kb == 4) {
-    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg);
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback);
     *rc = x->init();
     e = x;
   } else {
-    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg);
+    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg, copyback);
     *rc = x->init();
     e = x;
   }
@@ -922,7 +927,7 @@ static int single_start(wg_ctx* c, Query* q) {
           for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
           if (E->fuse) {
             names.push_back({"dedup_diff_merge", (nc + 2 * nf + 2 * nn) * kb});
-            names.push_back({"retire_copy", 0.0});
+            names.push_back({"retire_copy", E->copyback() ? 2 * (nf + nn) * kb : 0.0});
           } else {
             names.push_back({"dedup_diff", (nc + nn) * kb});
             names.push_back({"merge", 2 * (nf + nn) * kb});
@@ -1457,21 +1462,23 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   TRY(make_query(c, kind, edges, opts, &q));
   Relation* R = q->rel;
   const bool fuse = !(q->opts.flags & WG_FLAG_SEPARATE_STAGES);
+  const bool full_width = (q->opts.flags & WG_FLAG_FULL_WIDTH) != 0;
+  const bool copyback = fuse && (q->opts.flags & WG_FLAG_COPY_BACK) != 0;
   // TC candidates leave the join grouped by source: sort each group on the
   // destination field only (per-vertex histograms bound the vertex count)
-  const bool xseg = kind == WG_TC && R->nv <= kXSegMaxVertices;
-  const uint32_t bits = xseg ? R->w : 2 * R->w;
+  const bool xseg = !full_width && kind == WG_TC && R->nv <= kXSegMaxVertices;
+  const uint32_t bits = full_width ? 8u * R->kb : xseg ? R->w : 2 * R->w;
   // reuse an idle engine of the same key width, pass plan and stage layout
   for (size_t i = 0; i < c->idle.size(); ++i)
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
-        c->idle[i]->xgrouped() == xseg) {
+        c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
       break;
     }
   int rc = WG_OK;
   if (!q->own) {
-    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc);
+    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc, copyback);
     if (!e) { c->queries.erase(q->id); return rc; }
     q->own.reset(e);
   }

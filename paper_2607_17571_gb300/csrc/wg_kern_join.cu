@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
       done = I->iter >= 1 && nn == 0;
       fin = done || I->iter >= I->max_iters;
       toR = fin && !single;
-      if (toR) { rsz = nf; mt = (nf + kTileM - 1) / kTileM; }
+      if (toR || dv->copyback) { rsz = nf; mt = (nf + kTileM - 1) / kTileM; }
     }
     unsigned long long tr, tt, ta;
     const unsigned long long exr = scan1024(rsz, sh, &tr);
@@ -779,8 +779,10 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
       const unsigned long long fo = dv->segF[q].out2_off;
       Seg m{};
       m.in_off = fo; m.n = rsz; m.aux_off = 0; m.aux_n = 0; m.res = 0; m.out2_off = 0;
-      m.out_off = s_r + exr; m.tile0 = (uint32_t)(s_t + ext); m.ntiles = (uint32_t)mt;
-      m.inst = q; m.flags = 1u;
+      // the retire copy (batch: to the result pool) or, copying back, Full'
+      // onto the same offsets of the Full buffer
+      m.out_off = dv->copyback ? fo : s_r + exr; m.tile0 = (uint32_t)(s_t + ext);
+      m.ntiles = (uint32_t)mt; m.inst = q; m.flags = 1u;
       dv->segM[q] = m;
       if (act) {
         const uint32_t it = I->iter;
@@ -792,7 +794,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
         if (fin) {
           I->state = done ? INST_DONE : INST_ITERCAP;
           I->iters_done = it;
-          I->res_pool = toR ? 2u : (fph ^ 1u);
+          I->res_pool = toR ? 2u : dv->copyback ? fph : (fph ^ 1u);
           I->res_off = toR ? s_r + exr : fo;
           I->n_delta = 0;
         } else {
@@ -808,12 +810,13 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
   }
   if (threadIdx.x == 0) {
     Stage m{};
-    m.in = dv->F[fph ^ 1]; m.aux = nullptr; m.out = dv->R; m.out2 = dv->R;
+    m.in = dv->F[fph ^ 1]; m.aux = nullptr; m.out = dv->R;
+    m.out2 = dv->copyback ? dv->F[fph] : dv->R;
     m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
     m.ntiles = (uint32_t)s_t; m.ctr = 0;
     dv->st[S_MERGE] = m;
     dv->r_used = s_r;
-    dv->fphase = fph ^ 1u;
+    dv->fphase = dv->copyback ? fph : fph ^ 1u;
     dv->dphase = dph ^ 1u;
     ctl.n_active = (uint32_t)s_act;
     ctl.launch_iters += 1;

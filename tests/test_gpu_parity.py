@@ -197,3 +197,17 @@ def test_result_into_pinned_buffer(ctx):
         q.result(out=wg.pinned(want.keys.shape[0] - 1))
     q.free()
     rel.free()
+
+
+@pytest.mark.parametrize("flags", [dict(full_width=True), dict(copy_back=True),
+                                   dict(full_width=True, copy_back=True),
+                                   dict(copy_back=True, separate_stages=True)])
+def test_ablation_variants_same_result(ctx, flags):
+    # the engineering ablations change the layout or the number of passes,
+    # never the result, the iteration count or the per-iteration delta sizes
+    for g in (I.er_graph(1000, 3000, 1), I.path(70), I.random_small(300, 900, 5)):
+        check(ctx, "tc", g.src, g.dst, **flags)
+    f = I.sg_forest(3000, 6, 2.0, 0.01, 8)
+    check(ctx, "sg", f.src, f.dst, **flags)
+    ids = I.er_graph(400, 1500, 2)
+    check(ctx, "tc", ids.src.astype(np.uint64) * 9_999_991 % (1 << 32), ids.dst, **flags)
