@@ -540,7 +540,9 @@ def run_ablations(args):
     every variant's result is checked against the default's.  Variants:
     default (device loop, fused dedup/diff/merge, adaptive width, ping-pong),
     separate stages, host-driven loop (one launch per kernel, one host sync per
-    iteration), full-width radix sort, copy-back instead of ping-pong."""
+    iteration), full-width radix sort, copy-back instead of ping-pong, and a
+    linear-probing hash join in place of the sorted-array join (SURVEY NEXT
+    row 2; its table is built once per relation, outside the timed steps)."""
     import torch
 
     from paper_2607_17571_gb300 import inputs as I
@@ -549,17 +551,18 @@ def run_ablations(args):
     torch.cuda.set_device(0)
     name = args.ablate_workload
     g = I.workload(name)
-    ctx = wg.Context(0)
-    stream = ctx.torch_stream
-    rel = ctx.load(g.src, g.dst)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
     variants = [("default", {}), ("separate_stages", dict(separate_stages=True)),
                 ("host_loop", dict(loop=wg.WG_LOOP_HOST)), ("full_width", dict(full_width=True)),
-                ("copy_back", dict(copy_back=True))]
+                ("copy_back", dict(copy_back=True)), ("hash_join", dict(hash_join=True))]
     ref, out = None, []
     clocks = Clocks(0)
     clocks.start()
     for vname, opts in variants:
+        # one context per variant: its engine's pools are freed before the next
+        ctx = wg.Context(0)
+        stream = ctx.torch_stream
+        rel = ctx.load(g.src, g.dst)
         q = ctx.tc(rel, **opts)
         q.wait()
         res = q.result()
@@ -583,10 +586,21 @@ def run_ablations(args):
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
             q.free()
+        # the join's share (count + emit) from one profiled run: the paper's
+        # "count-and-join time" of its hash vs binary-search comparison
+        q = ctx.tc(rel, profile=True, **opts)
+        q.wait()
+        prof = {p["name"]: p["total_ms"] for p in q.profile()}
+        q.free()
         out.append({"variant": vname, "ms": round(statistics.mean(ms), 3),
                     "tuples_per_s": st.n_tuples / (statistics.mean(ms) / 1e3),
+                    "join_count_emit_ms": round(prof.get("join_count", 0.0) +
+                                                prof.get("join_emit", 0.0), 3),
                     "same_result": same, "gpu_launches": st.gpu_launches})
         del res
+        rel.free()
+        ctx.close()
+        torch.cuda.empty_cache()
     clk = clocks.stop()
     base = out[0]["ms"]
     for o in out:
@@ -599,8 +613,6 @@ def run_ablations(args):
                        "l2": "flushed between steps (256 MB write)"},
             "variants": out, "clocks": clk}
     print(json.dumps(line))
-    rel.free()
-    ctx.close()
     return 0
 
 

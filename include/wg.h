@@ -82,6 +82,12 @@ enum wg_loop {
                                       instead of swapping the two buffers (the copy-back
                                       baseline of the paper's ping-pong evaluation); same
                                       result */
+#define WG_FLAG_HASH_JOIN 8u       /* ablation (TC queries): look up E(y, .) in a linear-probing
+                                      hash table of E keyed by source (built once per relation,
+                                      compare-and-swap inserts) and emit one delta tuple per
+                                      thread, instead of the CSR range lookup and the
+                                      load-balanced emit (Sec. Data Skew in Hash-Based Join);
+                                      same result.  Ignored by SG queries and by wg_submit */
 
 typedef struct wg_opts {
   uint32_t max_iters;    /* iteration cap; 0 = 1<<20 */

@@ -80,7 +80,19 @@ struct Stage {
   uint32_t shift, dbits, pass, passes;
   unsigned long long* probe;    // join emit, triangle mode: count of candidates (a,b,c)
                                 // with E(c,a) (nothing is written)
+  const unsigned long long* htab;  // hash-join ablation: linear-probing table of E (or NULL)
+  unsigned long long hmask;        // table slots - 1 (a power of two minus one)
 };
+
+// Hash-join ablation (the hash-based join the paper's sorted-array join
+// replaces, Sec. "Data Skew in Hash-Based Join"): E in an open-addressing
+// table with linear probing, entry = (src rank << 32) | dst rank, keyed by
+// the source, empty slots all ones.  Every edge of a source lies in the
+// cluster that starts at its hash slot, before the first empty slot.
+constexpr unsigned long long kHashEmpty = ~0ull;
+__device__ __forceinline__ unsigned long long hash_slot(uint32_t key, unsigned long long mask) {
+  return (((unsigned long long)key * 0x9E3779B97F4A7C15ull) >> 29) & mask;
+}
 
 // One fixpoint instance (a query in flight).
 struct Inst {
@@ -149,6 +161,8 @@ struct Dev {
   Seg* segX;                          // one sort segment per source vertex
   uint32_t* tile_seg;                 // tile -> x-segment map of the x-grouped sort
   unsigned long long* xsum;           // [kXChunks][2]: candidates and tiles per chunk of x
+  const unsigned long long* htab;     // hash-join ablation: the relation's table (or NULL)
+  unsigned long long hmask;
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;

@@ -361,8 +361,12 @@ struct Relation {
   uint32_t nv = 0, w = 1;
   int kb = 4;
   DBuf keys, off, adj, V;
+  DBuf htab;                      // hash-join ablation: E in a linear-probing table (lazy)
+  unsigned long long hmask = 0;
   uint64_t peak_cand = 0, peak_full = 0;  // capacities seen by earlier queries
-  void release(wg_ctx* c) { keys.release(c); off.release(c); adj.release(c); V.release(c); }
+  void release(wg_ctx* c) {
+    keys.release(c); off.release(c); adj.release(c); V.release(c); htab.release(c);
+  }
 };
 
 template <typename K>
@@ -434,6 +438,7 @@ struct EngineBase {
   virtual bool fused() const = 0;
   virtual bool xgrouped() const = 0;
   virtual bool copyback() const = 0;
+  virtual bool hashjoin() const = 0;
   virtual void release() = 0;
 };
 
@@ -485,13 +490,14 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 2 : 0); }
+  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
+  bool hash_join = false;  // join through the relation's hash table (ablation)
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
-         bool xseg_, bool copy_back_ = false)
+         bool xseg_, bool copy_back_ = false, bool hash_join_ = false)
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
-        log_cap(logcap), copy_back(copy_back_) {
+        log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
@@ -499,6 +505,7 @@ struct Engine : EngineBase {
   bool fused() const override { return fuse; }
   bool xgrouped() const override { return xseg; }
   bool copyback() const override { return copy_back; }
+  bool hashjoin() const override { return hash_join; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -683,8 +690,12 @@ struct Engine : EngineBase {
     mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s); mark();
     launch_plan_cand(dv, s);
     if (xseg) launch_xseg_build(dv, s);
-    launch_partition<K>(dv->st + S_EMIT, 1, kTileC, c->num_sms * 4, s);
-    mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
+    if (hash_join) {
+      mark(); launch_join_emit_hash<K>(dv->st + S_EMIT, g_emit, s); mark();
+    } else {
+      launch_partition<K>(dv->st + S_EMIT, 1, kTileC, c->num_sms * 4, s);
+      mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
+    }
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
     launch_sort_hscan(dv->st + S_HSCAN, c->num_sms, s);
     for (uint32_t p = 0; p < passes; ++p) {
@@ -795,6 +806,16 @@ struct Engine : EngineBase {
     return WG_OK;
   }
 
+  // Hash-join ablation: the table the join stages read.
+  int put_htab(const void* tab, unsigned long long mask) {
+    h.htab = (const unsigned long long*)tab;
+    h.hmask = mask;
+    CK(cudaMemcpyAsync((char*)dv + offsetof(Dev, htab), (char*)&h + offsetof(Dev, htab),
+                       offsetof(Dev, hmask) + sizeof(h.hmask) - offsetof(Dev, htab),
+                       cudaMemcpyHostToDevice, st));
+    return WG_OK;
+  }
+
   // Buffers of the x-grouped sort for relations of up to nv vertices.
   int ensure_nv(uint32_t nv) {
     if (!xseg || nv <= nv_cap) return WG_OK;
@@ -868,14 +889,15 @@ struct Engine : EngineBase {
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
                               uint32_t logcap, bool fuse, bool xseg, int* rc,
-                              bool copyback = false) {
+                              bool copyback = false, bool hashjoin = false) {
   EngineBase* e;
   if (kb == 4) {
-    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback);
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback, hashjoin);
     *rc = x->init();
     e = x;
   } else {
-    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg, copyback);
+    auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg, copyback,
+                                             hashjoin);
     *rc = x->init();
     e = x;
   }
@@ -1464,6 +1486,28 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   const bool fuse = !(q->opts.flags & WG_FLAG_SEPARATE_STAGES);
   const bool full_width = (q->opts.flags & WG_FLAG_FULL_WIDTH) != 0;
   const bool copyback = fuse && (q->opts.flags & WG_FLAG_COPY_BACK) != 0;
+  const bool hashjoin = kind == WG_TC && (q->opts.flags & WG_FLAG_HASH_JOIN) != 0;
+  if (hashjoin && !R->htab.p) {
+    // the table of E, built once per relation like its CSR: at most half full
+    unsigned long long cap = 1024;
+    while (cap < 2 * (unsigned long long)R->ne) cap <<= 1;
+    int brc = R->htab.get(c, cap * 8);
+    if (brc == WG_OK && cudaMemsetAsync(R->htab.p, 0xFF, cap * 8, c->stream) != cudaSuccess)
+      brc = set_err(WG_E_CUDA, "hash table clear");
+    if (brc == WG_OK) {
+      R->hmask = cap - 1;
+      if (R->kb == 4)
+        launch_hash_build<uint32_t>((const uint32_t*)R->keys.p, R->ne, R->w,
+                                    (unsigned long long*)R->htab.p, R->hmask, grid_of(c, 8),
+                                    c->stream);
+      else
+        launch_hash_build<unsigned long long>((const unsigned long long*)R->keys.p, R->ne, R->w,
+                                              (unsigned long long*)R->htab.p, R->hmask,
+                                              grid_of(c, 8), c->stream);
+      if (cudaGetLastError() != cudaSuccess) brc = set_err(WG_E_CUDA, "hash table build");
+    }
+    if (brc != WG_OK) { R->htab.release(c); c->queries.erase(q->id); return brc; }
+  }
   // TC candidates leave the join grouped by source: sort each group on the
   // destination field only (per-vertex histograms bound the vertex count)
   const bool xseg = !full_width && kind == WG_TC && R->nv <= kXSegMaxVertices;
@@ -1471,18 +1515,26 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   // reuse an idle engine of the same key width, pass plan and stage layout
   for (size_t i = 0; i < c->idle.size(); ++i)
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
-        c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback) {
+        c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
+        c->idle[i]->hashjoin() == hashjoin) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
       break;
     }
   int rc = WG_OK;
   if (!q->own) {
-    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc, copyback);
+    EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc, copyback,
+                               hashjoin);
     if (!e) { c->queries.erase(q->id); return rc; }
     q->own.reset(e);
   }
   q->eng = q->own.get();
+  if (hashjoin) {  // this relation's table, in the host mirror too (pool regrowth rewrites it)
+    const int hr = R->kb == 4
+        ? static_cast<Engine<uint32_t>*>(q->eng)->put_htab(R->htab.p, R->hmask)
+        : static_cast<Engine<unsigned long long>*>(q->eng)->put_htab(R->htab.p, R->hmask);
+    if (hr != WG_OK) { c->queries.erase(q->id); return hr; }
+  }
   if (R->kb == 4) {
     auto* E = static_cast<Engine<uint32_t>*>(q->eng);
     E->regrows = 0; E->launches_issued = 0;

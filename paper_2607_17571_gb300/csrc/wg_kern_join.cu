@@ -52,6 +52,69 @@ __device__ __forceinline__ unsigned long long scan1024(unsigned long long v, uns
 
 __device__ __forceinline__ uint32_t deg(const uint32_t* off, uint32_t v) { return off[v + 1] - off[v]; }
 
+// Hash-join ablation: number of entries with source y, walking y's cluster
+// one dependent load at a time (the serialized probe chain of a hub).
+__device__ __forceinline__ uint32_t hash_count(const unsigned long long* T,
+                                               unsigned long long mask, uint32_t y) {
+  uint32_t n = 0;
+  unsigned long long s = hash_slot(y, mask);
+  for (unsigned long long step = 0; step <= mask; ++step) {
+    const unsigned long long e = T[s];
+    if (e == kHashEmpty) break;
+    n += (uint32_t)(e >> 32) == y;
+    s = (s + 1) & mask;
+  }
+  return n;
+}
+
+// Build the table: one thread per edge claims a slot by compare-and-swap,
+// moving to the next slot after every failure (the retry chains of a hub).
+template <typename K>
+__global__ void k_hash_build(const K* E, unsigned long long ne, uint32_t w,
+                             unsigned long long* T, unsigned long long mask) {
+  const K fmask = (K)(((K)1 << w) - 1);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t src = (uint32_t)(E[i] >> w), dst = (uint32_t)(E[i] & fmask);
+    const unsigned long long entry = ((unsigned long long)src << 32) | dst;
+    unsigned long long s = hash_slot(src, mask);
+    for (unsigned long long step = 0; step <= mask; ++step) {  // the table is at most half full
+      if (atomicCAS(T + s, kHashEmpty, entry) == kHashEmpty) break;
+      s = (s + 1) & mask;
+    }
+  }
+}
+
+// Hash-join emit (TC): one thread per delta tuple (x, y) walks y's cluster
+// again and writes (x, z) for every entry (y, z) into its slab -- the usual
+// GPU hash join, not load-balanced over outputs.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_join_emit_hash(Stage* stp) {
+  if (*(volatile uint32_t*)&stp->ctl->abort) return;
+  const K* D = (const K*)stp->in;
+  K* C = (K*)stp->out;
+  for (uint32_t k = 0; k < stp->nseg; ++k) {
+    const Seg sg = stp->segs[k];
+    const Inst* I = stp->inst + sg.inst;
+    const uint32_t w = I->w;
+    const K mask = (K)(((K)1 << w) - 1);
+    const unsigned long long* P = stp->pos + sg.in_off;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         i < sg.n; i += (unsigned long long)gridDim.x * blockDim.x) {
+      const K key = D[sg.in_off + i];
+      const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
+      K* o = C + sg.out_off + P[i];
+      unsigned long long s = hash_slot(y, stp->hmask);
+      for (unsigned long long step = 0; step <= stp->hmask; ++step) {
+        const unsigned long long e = stp->htab[s];
+        if (e == kHashEmpty) break;
+        if ((uint32_t)(e >> 32) == y) *o++ = ((K)x << w) | (K)(uint32_t)e;
+        s = (s + 1) & stp->hmask;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ join count
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
@@ -100,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
         const K key = sd[b + i];
         const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
         if (kind == KIND_TC) {
-          c[i] = deg(off, y);                                  // T(x,y), E(y,z)
+          c[i] = stp->htab ? hash_count(stp->htab, stp->hmask, y) : deg(off, y);  // T(x,y), E(y,z)
         } else if (iter == 0) {
           const unsigned long long d = deg(off, x);            // E(p,x), E(p,y), x != y
           c[i] = d ? d * (d - 1) : 0;
@@ -400,6 +463,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     s.nseg = N; s.ntiles = (uint32_t)s_carry; s.ctr = 0; s.epoch = ++ctl.epoch;
     s.passes = dv->passes; s.dbits = dv->dbits; s.shift = 0; s.pass = 0;
     s.xlen = dv->xseg ? dv->xlen : nullptr;
+    s.htab = dv->htab; s.hmask = dv->hmask;
     // (x-grouped: the segment builder zeroes the rows of non-empty sources)
     s.hist_n = dv->xseg ? 0ull : (unsigned long long)N * dv->passes * kRadix;
   }
@@ -556,6 +620,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     base.passes = dv->passes; base.dbits = dv->dbits;
     Stage e = base;
     e.in = dv->D[dv->dphase]; e.out = dv->C[0]; e.segs = dv->segE; e.splits = dv->splits;
+    e.htab = dv->htab; e.hmask = dv->hmask;
     dv->st[S_EMIT] = e;
     Stage h = base;
     h.in = dv->C[0];
@@ -885,6 +950,13 @@ void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, fals
 template <typename K>
 void launch_tri_probe(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, true><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
+void launch_join_emit_hash(Stage* st, int grid, cudaStream_t s) { k_join_emit_hash<K><<<grid, kThreads, 0, s>>>(st); }
+template <typename K>
+void launch_hash_build(const K* E, unsigned long long ne, uint32_t w, unsigned long long* T,
+                       unsigned long long mask, int grid, cudaStream_t s) {
+  if (ne) k_hash_build<K><<<grid, 256, 0, s>>>(E, ne, w, T, mask);
+}
+template <typename K>
 int occupancy_join(int which) {
   // largest shared-memory carveout first (see occupancy_of in wg_kern_sort.cu)
   auto one = [](auto kern) {
@@ -930,6 +1002,9 @@ void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint3
   template void launch_join_count<K>(Stage*, int, cudaStream_t);                            \
   template void launch_join_emit<K>(Stage*, int, cudaStream_t);                             \
   template void launch_tri_probe<K>(Stage*, int, cudaStream_t);                             \
+  template void launch_join_emit_hash<K>(Stage*, int, cudaStream_t);                        \
+  template void launch_hash_build<K>(const K*, unsigned long long, uint32_t,                 \
+                                     unsigned long long*, unsigned long long, int, cudaStream_t); \
   template int occupancy_join<K>(int);                                                      \
   template void launch_init_diag<K>(Inst*, uint32_t, uint32_t, void*, cudaStream_t);        \
   template void launch_rank_edges<K>(const uint32_t*, const uint32_t*, unsigned long long,  \

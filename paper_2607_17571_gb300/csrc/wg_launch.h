@@ -30,6 +30,10 @@ template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq,
 template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_tri_probe(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_join_emit_hash(Stage* st, int grid, cudaStream_t s);
+template <typename K>
+void launch_hash_build(const K* E, unsigned long long ne, uint32_t w, unsigned long long* T,
+                       unsigned long long mask, int grid, cudaStream_t s);
 template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 triangle probe
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);

@@ -25,6 +25,7 @@ WG_LOOP_DEVICE, WG_LOOP_HOST = 0, 1
 WG_FLAG_SEPARATE_STAGES = 1
 WG_FLAG_FULL_WIDTH = 2
 WG_FLAG_COPY_BACK = 4
+WG_FLAG_HASH_JOIN = 8
 WG_PENDING, WG_RUNNING, WG_DONE, WG_FAILED = 0, 1, 2, 3
 ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPACITY",
           -5: "WG_E_NOT_READY", -6: "WG_E_ITER_CAP", -7: "WG_E_DEVICE_TIMEOUT", -8: "WG_E_CUDA"}
@@ -119,9 +120,10 @@ def _check(rc, where):
 
 
 def _opts(max_iters=0, loop=WG_LOOP_DEVICE, profile=False, reserve_full=0, reserve_cand=0,
-          separate_stages=False, full_width=False, copy_back=False):
+          separate_stages=False, full_width=False, copy_back=False, hash_join=False):
     flags = ((WG_FLAG_SEPARATE_STAGES if separate_stages else 0) |
-             (WG_FLAG_FULL_WIDTH if full_width else 0) | (WG_FLAG_COPY_BACK if copy_back else 0))
+             (WG_FLAG_FULL_WIDTH if full_width else 0) | (WG_FLAG_COPY_BACK if copy_back else 0) |
+             (WG_FLAG_HASH_JOIN if hash_join else 0))
     return wg_opts(max_iters, loop, 1 if profile else 0, flags, reserve_full, reserve_cand)
 
 

@@ -201,7 +201,8 @@ def test_result_into_pinned_buffer(ctx):
 
 @pytest.mark.parametrize("flags", [dict(full_width=True), dict(copy_back=True),
                                    dict(full_width=True, copy_back=True),
-                                   dict(copy_back=True, separate_stages=True)])
+                                   dict(copy_back=True, separate_stages=True),
+                                   dict(hash_join=True), dict(hash_join=True, full_width=True)])
 def test_ablation_variants_same_result(ctx, flags):
     # the engineering ablations change the layout or the number of passes,
     # never the result, the iteration count or the per-iteration delta sizes
@@ -211,3 +212,14 @@ def test_ablation_variants_same_result(ctx, flags):
     check(ctx, "sg", f.src, f.dst, **flags)
     ids = I.er_graph(400, 1500, 2)
     check(ctx, "tc", ids.src.astype(np.uint64) * 9_999_991 % (1 << 32), ids.dst, **flags)
+
+
+def test_hash_join_hubs_and_regrowth(ctx):
+    # a hub of out-degree 3,000 (one long probe cluster) and tiny initial
+    # pools (the pools regrow mid-run; the join must keep using the table)
+    hub = np.zeros(3000, dtype=np.uint32)
+    leaves = np.arange(1, 3001, dtype=np.uint32)
+    g = I.er_graph(3001, 6000, 12)
+    src = np.concatenate([hub, g.src])
+    dst = np.concatenate([leaves, g.dst])
+    check(ctx, "tc", src, dst, hash_join=True, reserve_cand=4096, reserve_full=4096)
