@@ -113,7 +113,7 @@ struct Inst {
 };
 
 // Stage slots of an engine (one Stage record per kernel of the iteration).
-enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_HSCAN, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
+enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
                      S_NUM = S_PASS0 + kMaxPasses };
 
 // Tile of the join count: 3,072 / 2,048 delta tuples (static shared memory

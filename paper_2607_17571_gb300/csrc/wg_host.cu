@@ -294,7 +294,6 @@ static int prim_sort(wg_ctx* c, K* keys, size_t n, uint32_t bits) {
   Stage h = prim_stage(c, ntiles);
   h.in = keys; h.passes = passes; h.dbits = dbits;
   TRY(prim_put(c, S_HIST, h));
-  TRY(prim_put(c, S_HSCAN, h));
   K* buf[2] = {keys, (K*)c->s_tmp};
   for (uint32_t p = 0; p < passes; ++p) {
     Stage s = h;
@@ -303,7 +302,6 @@ static int prim_sort(wg_ctx* c, K* keys, size_t n, uint32_t bits) {
     TRY(prim_put(c, S_PASS0 + p, s));
   }
   launch_sort_hist<K>(c->s_stage + S_HIST, grid_of(c, occupancy_sort<K>(0)), c->stream);
-  launch_sort_hscan(c->s_stage + S_HSCAN, 64, c->stream);
   for (uint32_t p = 0; p < passes; ++p)
     launch_sort_pass<K>(c->s_stage + S_PASS0 + p, grid_of(c, occupancy_sort<K>(1)), c->stream);
   CK(cudaGetLastError());
@@ -490,7 +488,7 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 11 + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
+  int kernels_per_iter() const { return 10 + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
@@ -697,7 +695,6 @@ struct Engine : EngineBase {
       mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
     }
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
-    launch_sort_hscan(dv->st + S_HSCAN, c->num_sms, s);
     for (uint32_t p = 0; p < passes; ++p) {
       mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
     }

@@ -537,11 +537,8 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
     if (slen[i / row]) hrow[i] = 0;
   if (b == nchunks - 1 && threadIdx.x == 0) {
     const uint32_t ntiles = (uint32_t)(pt + tt);
-    const int ids[2] = {S_HIST, S_HSCAN};
-    for (int k = 0; k < 2; ++k) {
-      dv->st[ids[k]].segs = dv->segX; dv->st[ids[k]].nseg = nv;
-      dv->st[ids[k]].ntiles = ntiles; dv->st[ids[k]].tile_seg = dv->tile_seg;
-    }
+    dv->st[S_HIST].segs = dv->segX; dv->st[S_HIST].nseg = nv;
+    dv->st[S_HIST].ntiles = ntiles; dv->st[S_HIST].tile_seg = dv->tile_seg;
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
       dv->st[S_PASS0 + p].ntiles = ntiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
@@ -625,7 +622,6 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     Stage h = base;
     h.in = dv->C[0];
     dv->st[S_HIST] = h;
-    dv->st[S_HSCAN] = base;
     for (uint32_t p = 0; p < dv->passes; ++p) {
       Stage s = base;
       s.in = dv->C[p & 1]; s.out = dv->C[(p + 1) & 1];

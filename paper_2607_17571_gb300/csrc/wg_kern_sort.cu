@@ -1,8 +1,10 @@
 // wg_kern_sort.cu -- sorted-array stages of one semi-naive iteration (sm_103a):
 //   * LSD radix sort of packed keys (Sec. Buffer Routing and Adaptive Radix Sort):
 //     one upfront histogram of every digit, then one pass per digit that ranks a
-//     tile in shared memory, finds its global offset by decoupled lookback and
-//     scatters through shared memory so that stores come out in digit runs;
+//     tile in shared memory, finds its global offset by decoupled lookback (and
+//     the digit's start in the segment by a block scan of the segment's
+//     histogram row) and scatters through shared memory so that stores come
+//     out in digit runs;
 //   * fused deduplication + set difference against the full relation
 //     (Sec. Fused Deduplication and Set Difference): classify, block scan,
 //     decoupled lookback, ordered scatter -- one pass over the candidates;
@@ -74,31 +76,6 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
     unsigned long long* gh = stp->hist + (unsigned long long)k * passes * kRadix;
     for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads)
       if (sh[i]) atomicAdd(&gh[i], (unsigned long long)sh[i]);
-  }
-}
-
-// Exclusive scan of every (segment, pass) row of the digit histogram: the
-// global start of each digit bucket.  One warp per row; rows of empty
-// segments are skipped (nothing zeroed or read them).
-__global__ void __launch_bounds__(kThreads) k_sort_hscan(Stage* stp) {
-  if (*(volatile uint32_t*)&stp->ctl->abort) return;
-  const uint32_t rows = stp->nseg * stp->passes;
-  const uint32_t lane = threadIdx.x & 31;
-  for (uint32_t r = blockIdx.x * kWarps + (threadIdx.x >> 5); r < rows; r += gridDim.x * kWarps) {
-    if (stp->segs[r / stp->passes].n == 0) continue;  // no keys: the row is never read
-    unsigned long long* h = stp->hist + (unsigned long long)r * kRadix;
-    unsigned long long v[kRadix / 32], s = 0;
-#pragma unroll
-    for (int i = 0; i < kRadix / 32; ++i) { v[i] = h[lane * (kRadix / 32) + i]; s += v[i]; }
-    unsigned long long x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= (uint32_t)o) x += y;
-    }
-    unsigned long long run = x - s;
-#pragma unroll
-    for (int i = 0; i < kRadix / 32; ++i) { h[lane * (kRadix / 32) + i] = run; run += v[i]; }
   }
 }
 
@@ -210,6 +187,9 @@ __device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
   Ctl* ctl = stp->ctl;
   unsigned long long* status = stp->status;
   const uint32_t d = threadIdx.x;
+  // the segment's count of digit d (loaded now, scanned after the lookback)
+  const unsigned long long hcount =
+      stp->hist[((unsigned long long)m.k * stp->passes + stp->pass) * kRadix + d];
   unsigned long long excl = 0;
   if (!m.first) {  // per-digit lookback over earlier tiles of this segment
     const unsigned long long tile0 = sg.tile0;
@@ -234,9 +214,11 @@ __device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
     st_put(status + (unsigned long long)m.t * kRadix + d,
            st_pack(epoch, FLAG_INC, excl + S.tcnt[sl][d]));
   }
-  const unsigned long long* hbase =
-      stp->hist + ((unsigned long long)m.k * stp->passes + stp->pass) * kRadix;
-  S.gdst[d] = sg.out_off + hbase[d] + excl - S.tstart[sl][d];
+  // digit d of the segment starts after all its smaller digits: a block
+  // scan of the segment's histogram row (one digit per thread)
+  unsigned long long htot;
+  const unsigned long long hstart = block_excl_scan(hcount, S.s_scan, &htot);
+  S.gdst[d] = sg.out_off + hstart + excl - S.tstart[sl][d];
   __syncthreads();
   if (S.s_bad) return false;
   K* out = (K*)stp->out;
@@ -733,7 +715,6 @@ __global__ void k_partition(Stage* cons, int mode, uint32_t tile) {
 // ------------------------------------------------------------------ launchers
 template <typename K>
 void launch_sort_hist(Stage* st, int grid, cudaStream_t s) { k_sort_hist<K><<<grid, kThreads, 0, s>>>(st); }
-void launch_sort_hscan(Stage* st, int grid, cudaStream_t s) { k_sort_hscan<<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_sort_pass(Stage* st, int grid, cudaStream_t s) { k_sort_pass<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>

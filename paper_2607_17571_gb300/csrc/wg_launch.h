@@ -15,7 +15,6 @@ struct Inst;
 
 // sorted-array stages (wg_kern_sort.cu); K = uint32_t or unsigned long long
 template <typename K> void launch_sort_hist(Stage* st, int grid, cudaStream_t s);
-void launch_sort_hscan(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);

@@ -83,7 +83,6 @@ __global__ void k_noalloc_setup(unsigned char* base, void* keys, unsigned long l
     h.segs = sg; h.ctl = ctl; h.status = status; h.hist = hist;
     h.nseg = 1; h.ntiles = ntiles; h.in = keys; h.passes = passes; h.dbits = dbits;
     st[S_HIST] = h;
-    st[S_HSCAN] = h;
     void* buf[2] = {keys, base + kOffKeys};
     for (uint32_t p = 0; p < passes; ++p) {
       Stage x = h;
@@ -122,7 +121,6 @@ int sort_noalloc(K* keys, size_t n, uint32_t bits, cudaStream_t s, int dev) {
   k_noalloc_setup<<<64, 256, 0, s>>>(base, keys, n, passes, dbits, ntiles);
   Stage* st = (Stage*)(base + kOffStage);
   launch_sort_hist<K>(st + S_HIST, sms * std::max(1, occupancy_sort<K>(0)), s);
-  launch_sort_hscan(st + S_HSCAN, 1, s);
   for (uint32_t p = 0; p < passes; ++p)
     launch_sort_pass<K>(st + S_PASS0 + p, sms * std::max(1, occupancy_sort<K>(1)), s);
   if (passes & 1) {
