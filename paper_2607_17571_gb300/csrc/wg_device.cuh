@@ -82,6 +82,10 @@ struct Stage {
                                 // with E(c,a) (nothing is written)
   const unsigned long long* htab;  // hash-join ablation: linear-probing table of E (or NULL)
   unsigned long long hmask;        // table slots - 1 (a power of two minus one)
+  // fused pass: tiles holding candidates ("mixed"), listed after the
+  // partition; the others hold Full elements only and are copied separately
+  const uint32_t* mixl;            // mixed tiles in order (or NULL: every tile)
+  const uint32_t* mixc;            // mixed tiles before tile t; [ntiles] = their number
 };
 
 // Hash-join ablation (the hash-based join the paper's sorted-array join
@@ -163,6 +167,9 @@ struct Dev {
   unsigned long long* xsum;           // [kXChunks][2]: candidates and tiles per chunk of x
   const unsigned long long* htab;     // hash-join ablation: the relation's table (or NULL)
   unsigned long long hmask;
+  uint32_t* mixl;                     // fused pass: mixed tile list [tiles]
+  uint32_t* mixc;                     // mixed tiles before each tile [tiles + 1]
+  uint32_t* mixs;                     // mixed tiles per chunk of kThreads tiles
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;

@@ -478,8 +478,9 @@ struct Engine : EngineBase {
   Dev h{};             // host mirror (read back after each run)
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
-  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b, xsum_b;
+  DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b, xsum_b, mix_b;
   unsigned long long capC = 0, capF = 0, capR = 0;
+  size_t mix_tiles = 0;  // tiles the per-tile arrays (st_s, spl, mix_b) hold
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -488,7 +489,7 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 10 + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
+  int kernels_per_iter() const { return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
@@ -515,8 +516,12 @@ struct Engine : EngineBase {
     if (ev_done) cudaEventDestroy(ev_done);
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
-                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b, &xsum_b};
+                   &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b, &xsum_b,
+                   &mix_b};
     for (DBuf* b : all) b->release(c);
+    capC = capF = capR = 0;
+    mix_tiles = 0;
+    nv_cap = 0;
     if (own_st && st) {
       cudaStreamSynchronize(st);
       cudaStreamDestroy(st);
@@ -581,6 +586,10 @@ struct Engine : EngineBase {
     h.segX = (Seg*)segx_b.p;
     h.tile_seg = (uint32_t*)tseg_b.p;
     h.xsum = (unsigned long long*)xsum_b.p;
+    // [mix_tiles] list | [mix_tiles + 1] prefix | [mix_tiles / kThreads + 2] chunk counts
+    h.mixl = (uint32_t*)mix_b.p;
+    h.mixc = mix_b.p ? h.mixl + mix_tiles : nullptr;
+    h.mixs = mix_b.p ? h.mixc + mix_tiles + 1 : nullptr;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, st));
     return WG_OK;
@@ -646,13 +655,19 @@ struct Engine : EngineBase {
       for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
       capF = wantF;
     }
-    {  // scalar lookback words: join-count tiles and fused / dedup tiles
+    {  // scalar lookback words: join-count tiles and fused / dedup tiles.  The
+       // per-tile arrays are sized by an exact tile count (mix_tiles), never by
+       // the rounded-up byte size of one of them: they are carved differently
       const size_t tiles = std::max<size_t>(capC / kTileD, capF / FuseTile<K>::T) + n_slots + 2;
-      if (tiles * 8 > st_s.bytes) {
+      if (tiles > mix_tiles) {
         st_s.release(c);
         spl.release(c);
+        mix_b.release(c);
         TRY(st_s.get(c, tiles * 8));
         TRY(spl.get(c, (tiles + 1) * 8));
+        // fused pass: mixed-tile list, prefix per tile, count per chunk of tiles
+        TRY(mix_b.get(c, (2 * tiles + 1 + tiles / kThreads + 2) * 4));
+        mix_tiles = tiles;
         CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
         h.ctl.epoch = 0;
         CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
@@ -700,7 +715,14 @@ struct Engine : EngineBase {
     }
     if (fuse) {
       launch_partition<K>(dv->st + S_FUSE, 0, FuseTile<K>::T, c->num_sms * 4, s);
-      mark(); launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s); mark();
+      // mixed tiles through the fused kernel, Full-only tiles by a plain copy
+      // (timed together as the fused stage)
+      mark();
+      launch_fuse_mark(dv, c->num_sms * 2, s);
+      launch_fuse_list(dv, c->num_sms * 2, s);
+      launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s);
+      launch_fuse_copy<K>(dv->st + S_FUSE, c->num_sms * 8, s);
+      mark();
       launch_plan_post(dv, s);
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
     } else {

@@ -634,6 +634,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       f.out = dv->D[dv->dphase ^ 1]; f.out2 = dv->F[dv->fphase ^ 1];
       f.segs = dv->segF; f.status = dv->status_scalar; f.epoch = ++ctl.epoch;
       f.ntiles = (uint32_t)s_ft; f.splits = dv->splits;
+      f.mixl = dv->mixl; f.mixc = dv->mixc;
       dv->st[S_FUSE] = f;
     } else {
       Stage u = base;

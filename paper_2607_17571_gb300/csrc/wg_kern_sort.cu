@@ -472,9 +472,9 @@ __device__ __forceinline__ unsigned long long mpath_tie(const K* A, unsigned lon
 // Per-tile state a CTA keeps between classifying a tile and writing it out.
 struct FuseMeta {
   unsigned long long a0;  // Full elements before the tile
-  uint32_t t, k;          // tile, segment
+  uint32_t j, j0, k;      // mixed-tile index (lookback words), first one of the segment, segment
   uint32_t totK, totN;    // kept elements (Full' part) and new tuples of the tile
-  uint32_t first, last;   // first / last tile of its segment
+  uint32_t first, last;   // first / last mixed tile of its segment
 };
 
 // Classify tile t into slot `sb`: load its Full and candidate parts, merge,
@@ -482,7 +482,7 @@ struct FuseMeta {
 // the kept elements in Full' order in sbuf plus, per thread, where its kept
 // run starts, how many new tuples precede it, and its two masks.
 template <typename K>
-__device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, uint32_t* smask,
+__device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t j, K* sbuf, uint32_t* smask,
                                               uint32_t* spre, FuseMeta* meta,
                                               unsigned long long* s_scan,
                                               unsigned long long* s_a0, unsigned long long* s_a1,
@@ -490,8 +490,11 @@ __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, u
   constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
   const K* Aall = (const K*)stp->in;     // Full
   const K* Ball = (const K*)stp->aux;    // sorted candidates
+  const uint32_t t = stp->mixl ? stp->mixl[j] : j;
   const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
   const Seg sg = stp->segs[k];
+  const uint32_t j0 = stp->mixc ? stp->mixc[sg.tile0] : sg.tile0;
+  const uint32_t jl = (stp->mixc ? stp->mixc[sg.tile0 + sg.ntiles] : sg.tile0 + sg.ntiles) - 1;
   const K* A = Aall + sg.in_off;
   const K* B = Ball + sg.aux_off;
   const unsigned long long na = sg.n, nb = sg.aux_n;
@@ -593,11 +596,11 @@ __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t t, K* sbuf, u
   const unsigned long long both = ((unsigned long long)__popc(isN) << 32) | __popc(kept);
   const unsigned long long ex = block_excl_scan(both, s_scan, &tot);  // ends with a barrier:
   const uint32_t totN = (uint32_t)(tot >> 32), totK = (uint32_t)tot;  // sbuf reads are done
-  const bool first = (t == sg.tile0);
+  const bool first = (j == j0);
   if (threadIdx.x == 0) {
-    st_put(stp->status + t, st_pack(stp->epoch, first ? FLAG_INC : FLAG_AGG, totN));
-    meta->a0 = a0; meta->t = t; meta->k = k; meta->totK = totK; meta->totN = totN;
-    meta->first = first; meta->last = last;
+    st_put(stp->status + j, st_pack(stp->epoch, first ? FLAG_INC : FLAG_AGG, totN));
+    meta->a0 = a0; meta->j = j; meta->j0 = j0; meta->k = k; meta->totK = totK; meta->totN = totN;
+    meta->first = first; meta->last = j == jl;
   }
   // kept elements in Full' order, at tile-local positions
   uint32_t wk = (uint32_t)ex;
@@ -654,7 +657,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
   __shared__ uint32_t s_hasprev, s_t, s_bad;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
-  const uint32_t ntiles = stp->ntiles;
+  // the tiles holding candidates (the others are copied by k_fuse_copy)
+  const uint32_t ntiles = stp->mixc ? stp->mixc[stp->ntiles] : stp->ntiles;
   uint32_t cur = 0;
   uint32_t t = claim_tile(stp, &s_t);
   if (t >= ntiles) return;
@@ -670,12 +674,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
     const FuseMeta m = smeta[cur];
     if (threadIdx.x == 0) s_bad = 0;
     if (!m.first && threadIdx.x < 32) {
-      const unsigned long long e =
-          lookback_scalar(stp->status, m.t, stp->segs[m.k].tile0, stp->epoch, ctl);
+      const unsigned long long e = lookback_scalar(stp->status, m.j, m.j0, stp->epoch, ctl);
       if (threadIdx.x == 0) {
         s_excl = e;
         if (*(volatile uint32_t*)&ctl->abort) s_bad = 1;
-        st_put(stp->status + m.t, st_pack(stp->epoch, FLAG_INC, e + m.totN));
+        st_put(stp->status + m.j, st_pack(stp->epoch, FLAG_INC, e + m.totN));
       }
     } else if (m.first && threadIdx.x == 0) {
       s_excl = 0;
@@ -685,6 +688,110 @@ __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
     fuse_write<K>(stp, sbuf[cur], smask[cur], spre[cur], m, s_excl);
     if (!more) return;
     cur ^= 1;
+  }
+}
+
+// ------------------------------------------------------------------ fused pass: tile kinds
+// After the merge-path partition, a tile of the fused pass either holds
+// candidates ("mixed": classified by k_diff_merge) or Full elements only --
+// all kept, in order, none new.  Most tiles are of the second kind once the
+// deltas are small; k_fuse_copy moves them with plain coalesced copies, shifted
+// by the new-tuple prefix of the last mixed tile before them, so k_diff_merge
+// claims, classifies and looks back over the mixed tiles only.
+__device__ __forceinline__ bool fuse_tile_mixed(const Stage& f, uint32_t t, uint32_t T) {
+  const uint32_t k = find_seg(f.segs, f.nseg, t, f.tile_seg);
+  const Seg& sg = f.segs[k];
+  const unsigned long long na = sg.n, nb = sg.aux_n;
+  const unsigned long long d0 = (unsigned long long)(t - sg.tile0) * T;
+  const unsigned long long d1 = min(d0 + (unsigned long long)T, na + nb);
+  const unsigned long long a0 = f.splits[t];
+  const unsigned long long a1 = t == sg.tile0 + sg.ntiles - 1 ? na : f.splits[t + 1];
+  return d1 - d0 > a1 - a0;  // fewer Full elements than positions: candidates inside
+}
+
+// Pass 1: mark mixed tiles (mixc[t] = 0/1) and count them per chunk of kThreads.
+__global__ void __launch_bounds__(kThreads) k_fuse_mark(Dev* dv) {
+  if (dv->ctl.abort) return;
+  const Stage& f = dv->st[S_FUSE];
+  const uint32_t ntiles = f.ntiles, T = dv->fuse_tile;
+  const uint32_t nch = (ntiles + kThreads - 1) / kThreads;
+  for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const uint32_t t = c * kThreads + threadIdx.x;
+    const int mixed = t < ntiles && fuse_tile_mixed(f, t, T);
+    if (t < ntiles) dv->mixc[t] = (uint32_t)mixed;
+    const int cnt = __syncthreads_count(mixed);
+    if (threadIdx.x == 0) dv->mixs[c] = (uint32_t)cnt;
+  }
+}
+
+// Pass 2: mixc[t] = mixed tiles before t (mixc[ntiles] = all of them) and the
+// list of mixed tiles in order.
+__global__ void __launch_bounds__(kThreads) k_fuse_list(Dev* dv) {
+  __shared__ unsigned long long sh[kWarps];
+  if (dv->ctl.abort) return;
+  const Stage& f = dv->st[S_FUSE];
+  const uint32_t ntiles = f.ntiles;
+  const uint32_t nch = (ntiles + kThreads - 1) / kThreads;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) dv->mixc[0] = 0;
+  for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    unsigned long long pre = 0, tp;
+    for (uint32_t q = threadIdx.x; q < c; q += kThreads) pre += dv->mixs[q];
+    block_excl_scan(pre, sh, &tp);  // mixed tiles in the chunks before this one
+    const uint32_t t = c * kThreads + threadIdx.x;
+    const uint32_t mixed = t < ntiles ? dv->mixc[t] : 0u;
+    unsigned long long tot;
+    const uint32_t j = (uint32_t)(tp + block_excl_scan(mixed, sh, &tot));
+    if (t < ntiles) {
+      dv->mixc[t] = j;
+      if (mixed) dv->mixl[j] = t;
+    }
+    if (t + 1 == ntiles) dv->mixc[ntiles] = j + mixed;
+  }
+}
+
+// Pass 4 (after k_diff_merge): copy the Full-only tiles to Full'.
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_fuse_copy(Stage* stp) {
+  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
+  Ctl* ctl = stp->ctl;
+  if (*(volatile uint32_t*)&ctl->abort) return;
+  const uint32_t ntiles = stp->ntiles;
+  const K* Aall = (const K*)stp->in;
+  K* Fall = (K*)stp->out2;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (stp->mixc[t + 1] != stp->mixc[t]) continue;  // mixed: k_diff_merge wrote it
+    const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
+    const Seg& sg = stp->segs[k];
+    const bool last = t == sg.tile0 + sg.ntiles - 1;
+    const unsigned long long a0 = stp->splits[t], a1 = last ? sg.n : stp->splits[t + 1];
+    const uint32_t la = (uint32_t)(a1 - a0);
+    if ((unsigned long long)la > (unsigned long long)T) {  // not a Full-only tile: corrupt input
+      if (threadIdx.x == 0) fail_timeout(ctl);
+      return;
+    }
+    const uint32_t j0 = stp->mixc[sg.tile0], jp = stp->mixc[t];
+    unsigned long long exN = 0;  // new tuples before the tile: last mixed tile's inclusive count
+    if (jp > j0) {
+      const unsigned long long w = st_get(stp->status + jp - 1);
+      if (!st_ready(w, stp->epoch) || ((w >> 38) & 3u) != FLAG_INC) {
+        if (threadIdx.x == 0) fail_timeout(ctl);
+        return;
+      }
+      exN = w & kValMask;
+    }
+    const K* src = Aall + sg.in_off + a0;
+    K* dst = Fall + sg.out2_off + a0 + exN;
+    K v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      v[e] = i < la ? src[i] : (K)0;
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      if (i < la) dst[i] = v[e];
+    }
   }
 }
 
@@ -723,6 +830,10 @@ template <typename K>
 void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_diff_merge(Stage* st, int grid, cudaStream_t s) { k_diff_merge<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_fuse_mark(Dev* dv, int grid, cudaStream_t s) { k_fuse_mark<<<grid, kThreads, 0, s>>>(dv); }
+void launch_fuse_list(Dev* dv, int grid, cudaStream_t s) { k_fuse_list<<<grid, kThreads, 0, s>>>(dv); }
+template <typename K>
+void launch_fuse_copy(Stage* st, int grid, cudaStream_t s) { k_fuse_copy<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s) {
   k_partition<K><<<grid, 256, 0, s>>>(consumer, mode, tile);
@@ -758,6 +869,7 @@ int occupancy_sort(int which) {
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t); \
+  template void launch_fuse_copy<K>(Stage*, int, cudaStream_t);  \
   template void launch_partition<K>(Stage*, int, uint32_t, int, cudaStream_t); \
   template int occupancy_sort<K>(int);
 WG_INST(uint32_t)

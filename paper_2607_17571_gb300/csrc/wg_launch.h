@@ -29,6 +29,9 @@ template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq,
 template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_tri_probe(Stage* st, int grid, cudaStream_t s);
+void launch_fuse_mark(Dev* dv, int grid, cudaStream_t s);
+void launch_fuse_list(Dev* dv, int grid, cudaStream_t s);
+template <typename K> void launch_fuse_copy(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_join_emit_hash(Stage* st, int grid, cudaStream_t s);
 template <typename K>
 void launch_hash_build(const K* E, unsigned long long ne, uint32_t w, unsigned long long* T,
