@@ -14,8 +14,14 @@
 // Plan kernels (one CTA) are the CUDA form of the paper's lightweight
 // dispatch-parameter kernel (Sec. Batched Indirect-Dispatch Loop): they read
 // the sizes the previous stage left in device memory and write the next
-// stage's work description.  plan_merge also makes the termination decision
-// (Sec. Background, step 5) and sets the graph's WHILE condition.
+// stage's work description.  plan_post (fused stages) / plan_merge (separate
+// stages) also make the termination decision (Sec. Background, step 5) and
+// set the graph's WHILE condition.  The x-segment kernels build the per-source
+// sort segments of single TC queries.
+//
+// Also here: the emit kernel's probe mode for triangle counting (Sec.
+// Generalization, "Triangle Counting") and the hash-join ablation (a
+// linear-probing table of E, Sec. "Data Skew in Hash-Based Join").
 #include "wg_device.cuh"
 #include "wg_launch.h"
 

@@ -6,10 +6,14 @@
 //     histogram row) and scatters through shared memory so that stores come
 //     out in digit runs;
 //   * fused deduplication + set difference against the full relation
-//     (Sec. Fused Deduplication and Set Difference): classify, block scan,
-//     decoupled lookback, ordered scatter -- one pass over the candidates;
-//   * disjoint merge of the new delta into the full relation (Sec. Disjoint
-//     Merge): merge-path partitions, |out| = |Full| + |Delta| exactly, no atomics.
+//     (Sec. Fused Deduplication and Set Difference) that also writes the
+//     merged relation (Sec. Disjoint Merge): one merge-path pass over
+//     (Full, sorted candidates); the tiles holding candidates are classified
+//     (block scan, decoupled lookback, ordered scatter), the Full-only tiles
+//     are copied by a plain kernel;
+//   * the paper's separate stages: dedup + diff against Full (k_unique_diff)
+//     and the disjoint merge (k_merge: merge-path partitions, |out| = |Full| +
+//     |Delta| exactly, no atomics).
 // All kernels are segmented (one segment per fixpoint instance) and indirect:
 // their work comes from a device-resident Stage record.
 #include "wg_device.cuh"
@@ -639,11 +643,13 @@ __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint
   if (threadIdx.x == 0 && m.last) stp->segs[m.k].res = exN + m.totN;
 }
 
-// Software-pipelined over two tiles: a CTA classifies its next tile (and
-// publishes that tile's count) before it looks back for the previous one, so
-// the predecessors the lookback waits on have had one tile time to publish.
-// Deadlock-free: publishing a tile's count never waits, so the oldest
-// unfinished tile can always complete its lookback.
+// The fused pass over the mixed tiles (k_fuse_list's order; every tile when
+// the stage has no list).  Lookback words are indexed by the mixed-tile index:
+// Full-only tiles add no new tuples.  Software-pipelined over two tiles: a CTA
+// classifies its next tile (and publishes that tile's count) before it looks
+// back for the previous one, so the predecessors the lookback waits on have
+// had one tile time to publish.  Deadlock-free: publishing a tile's count
+// never waits, so the oldest unfinished tile can always complete its lookback.
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
   constexpr int T = FuseTile<K>::T;
