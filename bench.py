@@ -704,15 +704,17 @@ def run_serve(args):
             wait = arr[i] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
-            q = single(i)
-            try:
+            q = None
+            try:  # a query whose first pools do not fit fails at the call
+                q = single(i)
                 st = q.wait()
                 ok += 1
                 tuples += st.n_tuples
             except wg.WgError:
                 rej += 1
             lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
-            q.free()
+            if q is not None:
+                q.free()
         el = time.perf_counter() - t0
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
                     p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), completed=ok, rejected=rej,

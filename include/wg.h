@@ -167,7 +167,9 @@ void wg_relation_free(wg_ctx* ctx, wg_rel rel);
  * opts may be NULL (defaults).  The result is ready when wg_poll reports
  * WG_DONE or wg_wait returns WG_OK; buffers that turn out too small are grown
  * and the loop resumed inside wg_poll / wg_wait.  Errors: WG_E_INVAL (bad
- * handle), WG_E_NOMEM / WG_E_BUDGET. */
+ * handle), WG_E_NOMEM / WG_E_BUDGET (the first pools do not fit; idle
+ * engines' pools are released first).  On an error no query is left behind
+ * and *out is 0. */
 int wg_tc(wg_ctx* ctx, wg_rel edges, const wg_opts* opts, wg_query* out);
 int wg_sg(wg_ctx* ctx, wg_rel edges, const wg_opts* opts, wg_query* out);
 

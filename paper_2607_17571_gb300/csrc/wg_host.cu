@@ -83,6 +83,7 @@ struct wg_ctx {
   std::map<int, std::unique_ptr<EngineBase>> batch;  // batch engines by key class
   std::vector<uint64_t> pending;                  // submitted, not yet admitted
   std::vector<uint64_t> completed;                // batch queries finished, not yet taken
+  uint64_t excl = 0;  // batch query that runs with the whole budget (0: none), see batch_preempt
   cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
@@ -94,10 +95,12 @@ struct wg_ctx {
   uint32_t s_epoch = 0;
 };
 
+static void drop_idle_engines(wg_ctx* c, size_t bytes);
 static int dev_alloc(wg_ctx* c, size_t bytes, void** out, cudaStream_t st) {
   *out = nullptr;
   if (bytes == 0) return WG_OK;
   bytes = round_up(bytes);
+  if (c->used + bytes > c->budget) drop_idle_engines(c, bytes);  // unused pools go first
   if (c->used + bytes > c->budget)
     return set_err(WG_E_BUDGET, "allocation of " + std::to_string(bytes) +
                                     " bytes exceeds the memory budget");
@@ -486,6 +489,8 @@ struct Engine : EngineBase {
   cudaGraphExec_t exec = nullptr;
   int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_uniq = 0, g_merge = 0, g_fuse = 0;
   bool in_flight = false;
+  bool grow_wait = false;  // batch: paused after an overflow until the memory comes back
+  size_t wait_used = 0;    // the context's allocated bytes when the pause began
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
@@ -596,7 +601,11 @@ struct Engine : EngineBase {
   }
 
   // (Re)size the pools; live data (the current delta and full relation and the
-  // retired results) is copied into the new buffers.
+  // retired results) is copied into the new buffers.  A buffer is released only
+  // once its successor is allocated, and the device block is rewritten on
+  // every exit: a growth that fails (over the budget, out of memory) leaves
+  // the engine whole, at the capacities it reached, never pointing at freed
+  // memory.
   int ensure(unsigned long long wantC, unsigned long long wantF, unsigned long long wantR,
              bool keep) {
     AllocScope scope(c, st);
@@ -611,12 +620,44 @@ struct Engine : EngineBase {
           liveF = std::max<uint64_t>(liveF, I.f_off + I.n_full);
         }
     }
+    bool clear = false;  // lookback words must start over (a status array is new)
+    auto finish = [&](int rc) -> int {
+      if (clear) {
+        if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
+        if (st_k.p) CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
+        h.ctl.epoch = 0;
+      }
+      const int pr = put_pools();
+      return rc != WG_OK ? rc : pr;
+    };
+    {  // per-tile arrays first, for the capacities about to be reached: the
+       // scalar lookback words (join-count and fused / dedup tiles), the tile
+       // partitions and the fused pass's mixed-tile list, prefix and chunk
+       // counts.  Sized by an exact tile count (mix_tiles), never by the
+       // rounded-up byte size of one of them: they are carved differently
+      const unsigned long long nC = std::max(capC, wantC), nF = std::max(capF, wantF);
+      const size_t tiles = std::max<size_t>(nC / kTileD, nF / FuseTile<K>::T) + n_slots + 2;
+      if (tiles > mix_tiles) {
+        DBuf ns, np, nm;
+        int rc = ns.get(c, tiles * 8);
+        if (rc == WG_OK) rc = np.get(c, (tiles + 1) * 8);
+        if (rc == WG_OK) rc = nm.get(c, (2 * tiles + 1 + tiles / kThreads + 2) * 4);
+        if (rc != WG_OK) {
+          ns.release(c); np.release(c); nm.release(c);
+          return finish(rc);
+        }
+        st_s.release(c); spl.release(c); mix_b.release(c);
+        st_s = ns; spl = np; mix_b = nm;
+        mix_tiles = tiles;
+        clear = true;
+      }
+    }
     if (wantC > capC) {
-      DBuf nd[2], nc[2], np, nk;
+      DBuf nd[2], nc[2], np, nk, nt;
       auto undo = [&](int rc) {
         for (int i = 0; i < 2; ++i) { nd[i].release(c); nc[i].release(c); }
-        np.release(c); nk.release(c);
-        return rc;
+        np.release(c); nk.release(c); nt.release(c);
+        return finish(rc);
       };
       int rc = WG_OK;
       for (int i = 0; i < 2 && rc == WG_OK; ++i) {
@@ -625,8 +666,8 @@ struct Engine : EngineBase {
       }
       if (rc == WG_OK) rc = np.get(c, wantC * 8);
       if (rc == WG_OK) rc = nk.get(c, (wantC / kTileC + std::max(n_slots, nv_cap) + 2) * kRadix * 8);
+      if (rc == WG_OK && xseg) rc = nt.get(c, (wantC / kTileC + nv_cap + 2) * 4);
       if (rc != WG_OK) return undo(rc);
-      CK(cudaMemsetAsync(nk.p, 0, nk.bytes, st));
       if (liveD)
         CK(cudaMemcpyAsync(nd[h.dphase].p, D[h.dphase].p, liveD * sizeof(K),
                            cudaMemcpyDeviceToDevice, st));
@@ -636,53 +677,32 @@ struct Engine : EngineBase {
       }
       pos.release(c); st_k.release(c);
       pos = np; st_k = nk;
+      if (xseg) { tseg_b.release(c); tseg_b = nt; }
       capC = wantC;
-      if (xseg) {
-        tseg_b.release(c);
-        TRY(tseg_b.get(c, (capC / kTileC + nv_cap + 2) * 4));
-      }
-      h.ctl.epoch = 0;
-      if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
+      clear = true;
     }
     if (wantF > capF) {
       DBuf nf[2];
       int rc = nf[0].get(c, wantF * sizeof(K));
       if (rc == WG_OK) rc = nf[1].get(c, wantF * sizeof(K));
-      if (rc != WG_OK) { nf[0].release(c); nf[1].release(c); return rc; }
+      if (rc != WG_OK) { nf[0].release(c); nf[1].release(c); return finish(rc); }
       if (liveF)
         CK(cudaMemcpyAsync(nf[h.fphase].p, F[h.fphase].p, liveF * sizeof(K),
                            cudaMemcpyDeviceToDevice, st));
       for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
       capF = wantF;
     }
-    {  // scalar lookback words: join-count tiles and fused / dedup tiles.  The
-       // per-tile arrays are sized by an exact tile count (mix_tiles), never by
-       // the rounded-up byte size of one of them: they are carved differently
-      const size_t tiles = std::max<size_t>(capC / kTileD, capF / FuseTile<K>::T) + n_slots + 2;
-      if (tiles > mix_tiles) {
-        st_s.release(c);
-        spl.release(c);
-        mix_b.release(c);
-        TRY(st_s.get(c, tiles * 8));
-        TRY(spl.get(c, (tiles + 1) * 8));
-        // fused pass: mixed-tile list, prefix per tile, count per chunk of tiles
-        TRY(mix_b.get(c, (2 * tiles + 1 + tiles / kThreads + 2) * 4));
-        mix_tiles = tiles;
-        CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
-        h.ctl.epoch = 0;
-        CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
-      }
-    }
     if (!single && wantR > capR) {
       DBuf nr;
-      TRY(nr.get(c, wantR * sizeof(K)));  // nothing else is held on this path
+      const int rc = nr.get(c, wantR * sizeof(K));
+      if (rc != WG_OK) return finish(rc);
       if (keep && h.r_used)
         CK(cudaMemcpyAsync(nr.p, R.p, h.r_used * sizeof(K), cudaMemcpyDeviceToDevice, st));
       R.release(c);
       R = nr;
       capR = wantR;
     }
-    return put_pools();
+    return finish(WG_OK);
   }
 
   // The kernels of one semi-naive iteration (Secs. Per-Iteration Pipeline and
@@ -783,8 +803,27 @@ struct Engine : EngineBase {
     return WG_OK;
   }
 
+  // Radix passes of the next launch.  A batch engine's passes cover its key
+  // class; its instances' keys use 2w bits (w of the widest active one), so
+  // the passes above them are skipped (their kernels find no tiles).
+  int put_passes() {
+    uint32_t need = 0;
+    if (!single) {
+      for (const Inst& I : hi)
+        if (I.state == INST_ACTIVE) need = std::max(need, 2 * I.w);
+    }
+    const uint32_t np = single || need == 0 ? passes
+                                            : std::min(passes, std::max(1u, (need + dbits - 1) / dbits));
+    if (np != h.passes) {
+      h.passes = np;
+      CK(cudaMemcpyAsync(&dv->passes, &h.passes, sizeof(h.passes), cudaMemcpyHostToDevice, st));
+    }
+    return WG_OK;
+  }
+
   // Launch the loop (graph, or one host round trip per iteration).
   int launch(uint32_t budget, bool host_loop) {
+    TRY(put_passes());
     if (host_loop) {
       TRY(put_ctl(budget, false));
       for (;;) {
@@ -835,18 +874,26 @@ struct Engine : EngineBase {
     return WG_OK;
   }
 
-  // Buffers of the x-grouped sort for relations of up to nv vertices.
+  // Buffers of the x-grouped sort for relations of up to nv vertices (all
+  // allocated before any is replaced, as in ensure()).
   int ensure_nv(uint32_t nv) {
     if (!xseg || nv <= nv_cap) return WG_OK;
     AllocScope scope(c, st);
+    DBuf nx, ns, nh, nk, nt, nz;
+    int rc = nx.get(c, (size_t)nv * 8);
+    if (rc == WG_OK) rc = ns.get(c, (size_t)nv * sizeof(Seg));
+    if (rc == WG_OK) rc = nh.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8);
+    if (rc == WG_OK) rc = nk.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8);
+    if (rc == WG_OK) rc = nt.get(c, (capC / kTileC + nv + 2) * 4);
+    if (rc == WG_OK && !xsum_b.p) rc = nz.get(c, (size_t)kXChunks * 2 * 8);
+    if (rc != WG_OK) {
+      DBuf* tmp[] = {&nx, &ns, &nh, &nk, &nt, &nz};
+      for (DBuf* b : tmp) b->release(c);
+      return rc;  // nothing was replaced: the device block is still current
+    }
     xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c); tseg_b.release(c);
-    TRY(xlen_b.get(c, (size_t)nv * 8));
-    if (!xsum_b.p) TRY(xsum_b.get(c, (size_t)kXChunks * 2 * 8));
-    TRY(segx_b.get(c, (size_t)nv * sizeof(Seg)));
-    TRY(hist.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8));
-    TRY(st_k.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8));
-    tseg_b.release(c);
-    TRY(tseg_b.get(c, (capC / kTileC + nv + 2) * 4));
+    xlen_b = nx; segx_b = ns; hist = nh; st_k = nk; tseg_b = nt;
+    if (nz.p) xsum_b = nz;
     CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
     h.ctl.epoch = 0;
     if (st_s.p) CK(cudaMemsetAsync(st_s.p, 0, st_s.bytes, st));
@@ -905,6 +952,13 @@ struct Engine : EngineBase {
     return pool == 2 ? R.p : F[pool & 1].p;
   }
 };
+
+// Free the pools of idle single-query engines, least recently used first,
+// until `bytes` more fit in the budget (a cached engine only saves the next
+// query of its kind a pool allocation and a graph capture).
+static void drop_idle_engines(wg_ctx* c, size_t bytes) {
+  while (!c->idle.empty() && c->used + bytes > c->budget) c->idle.erase(c->idle.begin());
+}
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
                               uint32_t logcap, bool fuse, bool xseg, int* rc,
@@ -1079,6 +1133,68 @@ struct BatchInfo {
 };
 static std::map<wg_ctx*, std::map<int, BatchInfo>> g_binfo;
 
+// Whether batch engine `cls` holds work: a launch in flight, an admitted
+// instance or a result not yet retired (queued requests do not count: the
+// engine is built again for them when it was dropped).
+template <typename K>
+static bool batch_holds_work(wg_ctx* c, int cls) {
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  if (E->in_flight) return true;
+  for (const Inst& I : E->hi)
+    if (I.state == INST_ACTIVE) return true;
+  for (uint64_t q : g_binfo[c][cls].slot_q)
+    if (q) return true;
+  return false;
+}
+static bool batch_holds_work_any(wg_ctx* c, int cls) {
+  if (!c->batch[cls]) return false;
+  return c->batch[cls]->kb() == 4 ? batch_holds_work<uint32_t>(c, cls)
+                                  : batch_holds_work<unsigned long long>(c, cls);
+}
+
+// Release the pools of the other batch engines that hold no work; true when
+// any was released.
+static bool drop_idle_batch(wg_ctx* c, int keep) {
+  bool dropped = false;
+  for (auto& kv : c->batch) {
+    if (kv.first == keep || !kv.second || batch_holds_work_any(c, kv.first)) continue;
+    kv.second.reset();
+    g_binfo[c].erase(kv.first);
+    dropped = true;
+  }
+  return dropped;
+}
+
+// The exclusive query (see batch_preempt), or NULL; a stale id is cleared.
+static Query* excl_query(wg_ctx* c) {
+  if (!c->excl) return nullptr;
+  auto it = c->queries.find(c->excl);
+  if (it == c->queries.end() || it->second->state == WG_DONE || it->second->state == WG_FAILED) {
+    c->excl = 0;
+    return nullptr;
+  }
+  return it->second.get();
+}
+
+// Query q of class cls does not fit in its engine although it runs there
+// alone: while other engines hold pools it becomes the exclusive query (if
+// there is none yet) and stays queued; with the whole budget it fails.
+// True when it failed.
+static bool alone_too_large(wg_ctx* c, int cls, Query* q, int why) {
+  bool others = false;  // other engines hold pools
+  for (auto& kv : c->batch) others |= kv.first != cls && kv.second != nullptr;
+  if (c->excl == q->id || !others) {
+    if (c->excl == q->id) c->excl = 0;
+    q->state = WG_FAILED;
+    q->error = why;
+    q->t_done_us = now_us();
+    c->completed.push_back(q->id);
+    return true;
+  }
+  if (!excl_query(c)) c->excl = q->id;
+  return false;
+}
+
 // Admission estimate of a query's final relation: at most nv^2 tuples, capped
 // so that a single large query is still admitted into an idle engine.
 static double admit_estimate(const Relation* R, unsigned long long capF) {
@@ -1098,7 +1214,15 @@ static int batch_admit(wg_ctx* c, int cls) {
       load += B.est[s];
       ++active;
     }
-  if (B.hold && active > 0) return WG_OK;
+  Query* x = excl_query(c);
+  if (x) {  // the exclusive query only, once nothing else runs anywhere
+    if (x->state != WG_PENDING || x->bclass != cls || active > 0) return WG_OK;
+    for (auto& kv : c->batch)
+      if (kv.first != cls && batch_holds_work_any(c, kv.first)) return WG_OK;
+    drop_idle_batch(c, cls);
+  } else {
+    if (B.hold && active > 0) return WG_OK;
+  }
   B.hold = false;
   uint32_t first = 0xFFFFFFFFu, last = 0, next_free = 0;
   std::vector<uint64_t> still;
@@ -1106,10 +1230,25 @@ static int batch_admit(wg_ctx* c, int cls) {
     auto it = c->queries.find(qid);
     if (it == c->queries.end()) continue;
     Query* q = it->second.get();
-    if (q->bclass != cls) { still.push_back(qid); continue; }
+    if (q->bclass != cls || (x && q != x)) { still.push_back(qid); continue; }
     while (next_free < E->n_slots &&
            (B.slot_q[next_free] != 0 || E->hi[next_free].state == INST_ACTIVE))
       ++next_free;
+    if (active == 0 && q->rel->nv > E->capC) {
+      // an idle engine too small for the base rule of q: grow it first
+      const unsigned long long want = 2ull * q->rel->nv + 4096;
+      int rc = E->ensure(want, E->capF, E->capR, true);
+      if ((rc == WG_E_BUDGET || rc == WG_E_NOMEM) && drop_idle_batch(c, cls)) {
+        cudaGetLastError();
+        rc = E->ensure(want, E->capF, E->capR, true);
+      }
+      if (rc == WG_E_BUDGET || rc == WG_E_NOMEM) {
+        cudaGetLastError();
+        if (!alone_too_large(c, cls, q, rc)) still.push_back(qid);
+        continue;
+      }
+      TRY(rc);
+    }
     const double est = admit_estimate(q->rel, E->capF);
     const bool fits = dend + q->rel->nv <= E->capC && (active == 0 || load + est <= (double)E->capF);
     if (next_free >= E->n_slots || !fits) { still.push_back(qid); continue; }
@@ -1134,8 +1273,11 @@ static int batch_admit(wg_ctx* c, int cls) {
 // The pools cannot grow within the budget: requeue the most recently
 // admitted running instance (it restarts later from its base rule), and admit
 // nothing new until some instance retires.  Evicting the youngest keeps the
-// oldest instance progressing, so every query eventually runs with the whole
-// pool; a query that does not fit even alone fails with WG_E_BUDGET.
+// oldest instance progressing.  A query that runs alone in its engine and
+// still does not fit while other engines hold pools becomes the exclusive
+// query: requeued, it is admitted once every other engine has drained (no
+// admissions anywhere meanwhile) and been dropped, so it runs with the whole
+// budget; only then does a query that does not fit fail with WG_E_BUDGET.
 template <typename K>
 static int batch_preempt(wg_ctx* c, int cls, int why) {
   auto& B = g_binfo[c][cls];
@@ -1156,13 +1298,7 @@ static int batch_preempt(wg_ctx* c, int cls, int why) {
   auto it = c->queries.find(qid);
   if (it == c->queries.end()) return WG_OK;
   Query* q = it->second.get();
-  if (active == 1) {  // alone and still too large
-    q->state = WG_FAILED;
-    q->error = why;
-    q->t_done_us = now_us();
-    c->completed.push_back(q->id);
-    return WG_OK;
-  }
+  if (active == 1 && alone_too_large(c, cls, q, why)) return WG_OK;
   q->state = WG_PENDING;
   q->regrows += 1;
   c->pending.insert(c->pending.begin(), qid);
@@ -1235,6 +1371,46 @@ static void batch_fail_all(wg_ctx* c, int cls, int rc) {
     }
 }
 
+// Grow the pools after an overflow (or retry a paused growth).  Over the
+// budget, idle engines' pools are released and the growth tried once more.
+// An engine that still cannot grow with one instance left, while other
+// engines hold work, pauses with that instance's state as the exclusive
+// query: nothing is admitted anywhere, the others drain and are dropped, and
+// the loop resumes from the iteration that overflowed.  Otherwise preempt.
+template <typename K>
+static int batch_grow(wg_ctx* c, int cls) {
+  auto* E = static_cast<Engine<K>*>(c->batch[cls].get());
+  int rc = E->grow();
+  if ((rc == WG_E_BUDGET || rc == WG_E_NOMEM) && drop_idle_batch(c, cls)) {
+    cudaGetLastError();
+    rc = E->grow();
+  }
+  if (rc == WG_OK) {
+    E->grow_wait = false;
+    return WG_OK;
+  }
+  E->grow_wait = false;
+  if (rc != WG_E_BUDGET && rc != WG_E_NOMEM) {
+    batch_fail_all<K>(c, cls, rc);
+    return rc;
+  }
+  cudaGetLastError();
+  uint32_t active = 0, slot = 0;
+  for (uint32_t s = 0; s < E->n_slots; ++s)
+    if (E->hi[s].state == INST_ACTIVE) { ++active; slot = s; }
+  bool others = false;  // other engines hold pools (and work: idle ones were dropped)
+  for (auto& kv : c->batch) others |= kv.first != cls && kv.second != nullptr;
+  const uint64_t qid = active == 1 ? g_binfo[c][cls].slot_q[slot] : 0;
+  Query* x = excl_query(c);
+  if (qid && others && c->queries.count(qid) && (!x || x->id == qid)) {
+    c->excl = qid;
+    E->grow_wait = true;
+    E->wait_used = c->used;
+    return WG_OK;
+  }
+  return batch_preempt<K>(c, cls, rc);
+}
+
 // One scheduling round: finish the launch in flight (grow or preempt after an
 // overflow, retire finished queries), admit queued queries, launch again.
 template <typename K>
@@ -1258,17 +1434,16 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch, boo
     }
     if (E->h.ctl.abort) {
       ++E->regrows;
-      const int rc = E->grow();
-      if (rc == WG_E_BUDGET || rc == WG_E_NOMEM) {
-        cudaGetLastError();
-        TRY(batch_preempt<K>(c, cls, rc));
-      } else if (rc != WG_OK) {
-        batch_fail_all<K>(c, cls, rc);
-        return rc;
-      }
+      TRY(batch_grow<K>(c, cls));
     }
     TRY(batch_retire<K>(c, cls));
+  } else if (E->grow_wait) {  // paused: retry once memory has come back
+    if (drop_idle_batch(c, cls) || c->used < E->wait_used) {
+      TRY(batch_grow<K>(c, cls));
+      if (!E->grow_wait) *progressed = true;
+    }
   }
+  if (E->grow_wait) return WG_OK;
   TRY(batch_admit<K>(c, cls));
   bool any = false;
   for (const Inst& I : E->hi) any |= I.state == INST_ACTIVE;
@@ -1279,8 +1454,44 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch, boo
   return WG_OK;
 }
 
+static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R);
+
+// A dropped engine is built again for the requests of its class still queued
+// (not while another class's exclusive query waits for the memory).  If its
+// first pools do not fit although no other batch engine holds any, those
+// requests fail with the allocation's error.
+static int rebuild_batch(wg_ctx* c, int cls) {
+  Query* x = excl_query(c);
+  if (x && x->bclass != cls) return WG_OK;
+  Query* p = nullptr;
+  for (uint64_t qid : c->pending) {
+    auto it = c->queries.find(qid);
+    if (it != c->queries.end() && it->second->bclass == cls) { p = it->second.get(); break; }
+  }
+  if (!p) return WG_OK;
+  const int rc = ensure_batch_engine(c, cls, p->rel);
+  if (rc != WG_E_BUDGET && rc != WG_E_NOMEM) return rc;
+  cudaGetLastError();
+  for (auto& kv : c->batch)
+    if (kv.second) return WG_OK;  // memory may come back: retry next round
+  std::vector<uint64_t> still;
+  for (uint64_t qid : c->pending) {
+    auto it = c->queries.find(qid);
+    if (it == c->queries.end()) continue;
+    Query* q = it->second.get();
+    if (q->bclass != cls) { still.push_back(qid); continue; }
+    q->state = WG_FAILED;
+    q->error = rc;
+    q->t_done_us = now_us();
+    c->completed.push_back(qid);
+  }
+  c->pending.swap(still);
+  return WG_OK;
+}
+
 static int batch_round_any(wg_ctx* c, int cls, uint32_t iters, bool wait_launch,
                            bool* progressed) {
+  if (!c->batch[cls]) TRY(rebuild_batch(c, cls));
   if (!c->batch[cls]) return WG_OK;
   return c->batch[cls]->kb() == 4
              ? batch_round<uint32_t>(c, cls, iters, wait_launch, progressed)
@@ -1328,9 +1539,14 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   const bool small = (cls & 1) == 0;  // small-query engines need far smaller pools
   const double avail = (double)(c->budget - c->used) / (small ? 8.0 : 3.0);
   const unsigned long long capC = std::max<unsigned long long>(1ull << 16, (unsigned long long)(avail / per_key));
-  if (R->kb == 4)
-    return static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 4, false);
-  return static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 4, false);
+  const int prc = R->kb == 4
+                      ? static_cast<Engine<uint32_t>*>(e)->ensure(capC, capC, capC / 4, false)
+                      : static_cast<Engine<unsigned long long>*>(e)->ensure(capC, capC, capC / 4, false);
+  if (prc != WG_OK) {  // no pools: drop the engine, a later request builds it again
+    c->batch[cls].reset();
+    g_binfo[c].erase(cls);
+  }
+  return prc;
 }
 
 template <typename K>
@@ -1563,12 +1779,14 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
     E->regrows = 0; E->launches_issued = 0;
     rc = single_start<unsigned long long>(c, q);
   }
-  if (rc != WG_OK) {
+  if (rc != WG_OK) {  // nothing left running: drop the query, its engine goes back idle
     q->state = WG_FAILED;
     q->error = rc;
+    wg_query_free(c, q->id);
+    return rc;
   }
   *out = q->id;
-  return rc;
+  return WG_OK;
 }
 
 int wg_tc(wg_ctx* c, wg_rel edges, const wg_opts* opts, wg_query* out) {
@@ -1587,7 +1805,8 @@ int wg_submit(wg_ctx* c, const wg_request* reqs, size_t n, wg_query* ids) {
     TRY(make_query(c, reqs[i].kind, reqs[i].edges, &reqs[i].opts, &q));
     q->batch = true;
     q->bclass = batch_class(q->rel);
-    TRY(ensure_batch_engine(c, q->bclass, q->rel));
+    if (!excl_query(c)) TRY(ensure_batch_engine(c, q->bclass, q->rel));
+    else c->batch[q->bclass];  // the class is listed; its engine is built on demand
     c->pending.push_back(q->id);
     ids[i] = q->id;
   }

@@ -634,6 +634,12 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       s.status = dv->status_sort; s.shift = p * dv->dbits; s.pass = p; s.epoch = ++ctl.epoch;
       dv->st[S_PASS0 + p] = s;
     }
+    for (uint32_t p = dv->passes; p < kMaxPasses; ++p) {
+      // digits above every active instance's keys: launched, but no tiles
+      Stage s = base;
+      s.ntiles = 0;
+      dv->st[S_PASS0 + p] = s;
+    }
     if (dv->fuse) {
       Stage f = base;
       f.in = dv->F[dv->fphase]; f.aux = dv->C[dv->passes & 1];

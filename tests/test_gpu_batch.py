@@ -7,6 +7,8 @@ when the pools cannot grow inside the memory budget the largest running
 query is requeued and still finishes with the same result; a query that does
 not fit even alone fails with WG_E_BUDGET.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -138,6 +140,91 @@ def test_query_larger_than_budget_fails_cleanly():
         assert e.value.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
         hs.wait()
         assert np.array_equal(hs.result(), oracle_tc(small.src, small.dst).keys)
+
+
+@functools.lru_cache(maxsize=1)
+def _growth_cases():
+    gs = [I.er_graph(n, 3 * n, 90 + n) for n in (800, 1400, 2000, 2600)]  # 0.6 .. 6.0 M tuples
+    small = I.er_graph(300, 700, 17)
+    return gs, [oracle_tc(g.src, g.dst) for g in gs], small, oracle_tc(small.src, small.dst)
+
+
+@pytest.mark.parametrize("budget_mb", [72, 96, 128, 160, 200, 256, 320])
+def test_failed_growth_leaves_engines_whole(budget_mb):
+    """Pools that cannot grow within the budget, at whatever step of a growth
+    the budget runs out (the candidate pools, the full-relation pools, the
+    per-tile arrays, the retire pool): every query completes with the
+    oracle's result or fails with a budget error, and later queries on the
+    same context -- batched and alone, reusing the engines whose growth
+    failed -- complete."""
+    from paper_2607_17571_gb300 import wg
+    gs, want, small, want_small = _growth_cases()
+    with wg.Context(0, mem_budget=budget_mb << 20) as c:
+        rels = [c.load(g.src, g.dst) for g in gs]
+        srel = c.load(small.src, small.dst)
+        for h, w in zip(c.submit([(wg.WG_TC, r) for r in rels]), want):
+            try:
+                h.wait()
+                assert np.array_equal(h.result(), w.keys)
+            except wg.WgError as e:
+                assert e.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
+            h.free()
+        for r, w in [(srel, want_small)] + list(zip(rels[::-1], want[::-1])) + [(srel, want_small)]:
+            q = None
+            try:  # alone: the engine may not even get its first pools
+                q = c.tc(r)
+                q.wait()
+                assert np.array_equal(q.result(), w.keys)
+            except wg.WgError as e:
+                assert e.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
+            finally:
+                if q is not None:
+                    q.free()
+        (h,) = c.submit([(wg.WG_TC, srel)])  # the batch engine's pools hold it
+        h.wait()
+        assert np.array_equal(h.result(), want_small.keys)
+        h.free()
+
+
+@functools.lru_cache(maxsize=1)
+def _exclusive_cases():
+    big = I.er_graph(5000, 7000, 77)  # > 4,096 vertices: its own engine; 6.3 M tuples
+    smalls = [I.er_graph(n, 3 * n, 300 + n) for n in (800, 1100, 1400, 1700, 2000, 900, 1300, 1900)]
+    return (big, smalls, oracle_tc(big.src, big.dst),
+            [oracle_tc(g.src, g.dst) for g in smalls])
+
+
+@pytest.mark.parametrize("budget_mb", [96, 128, 192])
+def test_query_that_fits_alone_completes_in_a_mix(budget_mb):
+    """A batched query that completes when it is the only request finishes
+    in a mix too, under the same budget with the same relations resident:
+    when its engine cannot grow because another engine holds pools, it waits
+    as the exclusive query for the others to drain, then runs with the whole
+    budget."""
+    from paper_2607_17571_gb300 import wg
+    big, smalls, want_big, want_smalls = _exclusive_cases()
+
+    def run(mix):
+        with wg.Context(0, mem_budget=budget_mb << 20) as c:
+            rb = c.load(big.src, big.dst)
+            rs = [c.load(g.src, g.dst) for g in smalls]
+            reqs = [(wg.WG_TC, r) for r in rs] if mix else []
+            hs = c.submit(reqs[:4] + [(wg.WG_TC, rb)] + reqs[4:])
+            wants = (want_smalls[:4] + [want_big] + want_smalls[4:]) if mix else [want_big]
+            done = []
+            for h, w in zip(hs, wants):
+                try:
+                    h.wait()
+                    assert np.array_equal(h.result(), w.keys)
+                    done.append(True)
+                except wg.WgError as e:
+                    assert e.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
+                    done.append(False)
+                h.free()
+            return done[4] if mix else done[0]
+
+    if run(mix=False):
+        assert run(mix=True)
 
 
 def test_iteration_cap_in_batch(ctx):
