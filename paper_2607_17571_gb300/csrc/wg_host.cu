@@ -84,6 +84,7 @@ struct wg_ctx {
   std::vector<uint64_t> pending;                  // submitted, not yet admitted
   std::vector<uint64_t> completed;                // batch queries finished, not yet taken
   uint64_t excl = 0;  // batch query that runs with the whole budget (0: none), see batch_preempt
+  uint64_t solo_run = 0;  // the served request running on a single-query engine (0: none)
   cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
@@ -455,6 +456,10 @@ struct Query {
   bool batch = false;
   int bclass = -1;
   uint32_t slot = 0;
+  // served through a single-query engine (a large request, see solo_round)
+  bool solo = false;
+  bool solo_wait = false;        // paused after a growth over the budget
+  size_t wait_used = 0;          // the context's allocated bytes when it paused
   // results
   uint64_t n_tuples = 0;
   uint32_t iterations = 0, regrows = 0;
@@ -1057,7 +1062,7 @@ static int single_start(wg_ctx* c, Query* q) {
 }
 
 template <typename K>
-static int single_progress(wg_ctx* c, Query* q, bool block) {
+static int single_progress(wg_ctx* c, Query* q, bool block, bool pause_on_budget = false) {
   auto* E = static_cast<Engine<K>*>(q->eng);
   for (;;) {
     if (E->in_flight) {
@@ -1071,6 +1076,12 @@ static int single_progress(wg_ctx* c, Query* q, bool block) {
     }
     bool again = false;
     int rc = E->settle(&again);
+    if (rc != WG_OK && pause_on_budget && (rc == WG_E_BUDGET || rc == WG_E_NOMEM)) {
+      cudaGetLastError();  // the pools stay whole at their old capacities
+      q->solo_wait = true;
+      q->wait_used = c->used;
+      return WG_OK;
+    }
     if (rc != WG_OK) {
       q->state = WG_FAILED;
       q->error = rc;
@@ -1122,6 +1133,10 @@ static int batch_class(const Relation* R) {
 }
 static uint32_t class_bits(int cls) { return cls / 2 == 0 ? 32 : (cls / 2 == 1 ? 48 : 64); }
 constexpr uint32_t kBatchSlots = 1024;    // queries running at once per key class
+// Served requests over more edges than this run one at a time on a
+// single-query engine (per-source sort, exact pass plan) beside the batch
+// engines: one such fixpoint already fills the GPU.
+constexpr uint64_t kSoloEdges = 1u << 16;
 constexpr uint32_t kBatchLogCap = 1024;   // per-iteration delta sizes kept per query
 
 struct BatchInfo {
@@ -1176,13 +1191,26 @@ static Query* excl_query(wg_ctx* c) {
   return it->second.get();
 }
 
+// Whether memory that may come back is held outside batch engine `cls`:
+// another batch engine's pools, or the served request running on a
+// single-query engine.
+static bool solo_running(wg_ctx* c) {
+  if (!c->solo_run) return false;
+  auto it = c->queries.find(c->solo_run);
+  return it != c->queries.end() && it->second->state == WG_RUNNING;
+}
+static bool held_elsewhere(wg_ctx* c, int cls) {
+  for (auto& kv : c->batch)
+    if (kv.first != cls && kv.second) return true;
+  return solo_running(c);
+}
+
 // Query q of class cls does not fit in its engine although it runs there
 // alone: while other engines hold pools it becomes the exclusive query (if
 // there is none yet) and stays queued; with the whole budget it fails.
 // True when it failed.
 static bool alone_too_large(wg_ctx* c, int cls, Query* q, int why) {
-  bool others = false;  // other engines hold pools
-  for (auto& kv : c->batch) others |= kv.first != cls && kv.second != nullptr;
+  const bool others = held_elsewhere(c, cls);
   if (c->excl == q->id || !others) {
     if (c->excl == q->id) c->excl = 0;
     q->state = WG_FAILED;
@@ -1216,7 +1244,8 @@ static int batch_admit(wg_ctx* c, int cls) {
     }
   Query* x = excl_query(c);
   if (x) {  // the exclusive query only, once nothing else runs anywhere
-    if (x->state != WG_PENDING || x->bclass != cls || active > 0) return WG_OK;
+    if (x->solo || x->state != WG_PENDING || x->bclass != cls || active > 0) return WG_OK;
+    if (solo_running(c)) return WG_OK;
     for (auto& kv : c->batch)
       if (kv.first != cls && batch_holds_work_any(c, kv.first)) return WG_OK;
     drop_idle_batch(c, cls);
@@ -1230,7 +1259,7 @@ static int batch_admit(wg_ctx* c, int cls) {
     auto it = c->queries.find(qid);
     if (it == c->queries.end()) continue;
     Query* q = it->second.get();
-    if (q->bclass != cls || (x && q != x)) { still.push_back(qid); continue; }
+    if (q->solo || q->bclass != cls || (x && q != x)) { still.push_back(qid); continue; }
     while (next_free < E->n_slots &&
            (B.slot_q[next_free] != 0 || E->hi[next_free].state == INST_ACTIVE))
       ++next_free;
@@ -1398,8 +1427,7 @@ static int batch_grow(wg_ctx* c, int cls) {
   uint32_t active = 0, slot = 0;
   for (uint32_t s = 0; s < E->n_slots; ++s)
     if (E->hi[s].state == INST_ACTIVE) { ++active; slot = s; }
-  bool others = false;  // other engines hold pools (and work: idle ones were dropped)
-  for (auto& kv : c->batch) others |= kv.first != cls && kv.second != nullptr;
+  const bool others = held_elsewhere(c, cls);  // (idle engines were dropped above)
   const uint64_t qid = active == 1 ? g_binfo[c][cls].slot_q[slot] : 0;
   Query* x = excl_query(c);
   if (qid && others && c->queries.count(qid) && (!x || x->id == qid)) {
@@ -1462,11 +1490,14 @@ static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R);
 // requests fail with the allocation's error.
 static int rebuild_batch(wg_ctx* c, int cls) {
   Query* x = excl_query(c);
-  if (x && x->bclass != cls) return WG_OK;
+  if (x && (x->solo || x->bclass != cls)) return WG_OK;
   Query* p = nullptr;
   for (uint64_t qid : c->pending) {
     auto it = c->queries.find(qid);
-    if (it != c->queries.end() && it->second->bclass == cls) { p = it->second.get(); break; }
+    if (it != c->queries.end() && !it->second->solo && it->second->bclass == cls) {
+      p = it->second.get();
+      break;
+    }
   }
   if (!p) return WG_OK;
   const int rc = ensure_batch_engine(c, cls, p->rel);
@@ -1474,12 +1505,13 @@ static int rebuild_batch(wg_ctx* c, int cls) {
   cudaGetLastError();
   for (auto& kv : c->batch)
     if (kv.second) return WG_OK;  // memory may come back: retry next round
+  if (held_elsewhere(c, cls)) return WG_OK;
   std::vector<uint64_t> still;
   for (uint64_t qid : c->pending) {
     auto it = c->queries.find(qid);
     if (it == c->queries.end()) continue;
     Query* q = it->second.get();
-    if (q->bclass != cls) { still.push_back(qid); continue; }
+    if (q->solo || q->bclass != cls) { still.push_back(qid); continue; }
     q->state = WG_FAILED;
     q->error = rc;
     q->t_done_us = now_us();
@@ -1511,13 +1543,16 @@ static bool batch_busy(wg_ctx* c) {
 // One serving round over every batch engine, without waiting on one engine
 // while another could run: engines whose launch finished are retired,
 // admitted and relaunched; if none had finished, wait briefly and retry.
+static int solo_round(wg_ctx* c, bool* progressed, bool* busy);
+
 static int serve_round(wg_ctx* c, uint32_t iters) {
-  for (int spin = 0;; ++spin) {
-    bool progressed = false;
+  for (long spin = 0;; ++spin) {
+    bool progressed = false, solo_busy = false;
+    TRY(solo_round(c, &progressed, &solo_busy));
     for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, iters, false, &progressed));
-    if (progressed || !batch_busy(c)) return WG_OK;
-    if (spin > 200000) {  // ~10 s without any engine finishing a launch
-      return set_err(WG_E_DEVICE_TIMEOUT, "no batch launch finished");
+    if (progressed || !(batch_busy(c) || solo_busy)) return WG_OK;
+    if (spin > 12000000) {  // ~10 min without any launch finishing
+      return set_err(WG_E_DEVICE_TIMEOUT, "no launch finished");
     }
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
@@ -1712,12 +1747,11 @@ static int make_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, Qu
   return WG_OK;
 }
 
-static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, wg_query* out) {
-  if (!c || !out) return set_err(WG_E_INVAL, "bad argument");
-  *out = 0;
-  Query* q;
-  TRY(make_query(c, kind, edges, opts, &q));
+// Give query q a single-query engine (an idle one of the same key width, pass
+// plan and stage layout, else a new one) and start its fixpoint.
+static int single_begin(wg_ctx* c, Query* q) {
   Relation* R = q->rel;
+  const int kind = q->kind;
   const bool fuse = !(q->opts.flags & WG_FLAG_SEPARATE_STAGES);
   const bool full_width = (q->opts.flags & WG_FLAG_FULL_WIDTH) != 0;
   const bool copyback = fuse && (q->opts.flags & WG_FLAG_COPY_BACK) != 0;
@@ -1741,44 +1775,48 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
                                               grid_of(c, 8), c->stream);
       if (cudaGetLastError() != cudaSuccess) brc = set_err(WG_E_CUDA, "hash table build");
     }
-    if (brc != WG_OK) { R->htab.release(c); c->queries.erase(q->id); return brc; }
+    if (brc != WG_OK) { R->htab.release(c); return brc; }
   }
   // TC candidates leave the join grouped by source: sort each group on the
   // destination field only (per-vertex histograms bound the vertex count)
   const bool xseg = !full_width && kind == WG_TC && R->nv <= kXSegMaxVertices;
   const uint32_t bits = full_width ? 8u * R->kb : xseg ? R->w : 2 * R->w;
-  // reuse an idle engine of the same key width, pass plan and stage layout
-  for (size_t i = 0; i < c->idle.size(); ++i)
+  for (size_t i = 0; i < c->idle.size() && !q->own; ++i)
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
         c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
         c->idle[i]->hashjoin() == hashjoin) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
-      break;
     }
   int rc = WG_OK;
   if (!q->own) {
     EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc, copyback,
                                hashjoin);
-    if (!e) { c->queries.erase(q->id); return rc; }
+    if (!e) return rc;
     q->own.reset(e);
   }
   q->eng = q->own.get();
   if (hashjoin) {  // this relation's table, in the host mirror too (pool regrowth rewrites it)
-    const int hr = R->kb == 4
-        ? static_cast<Engine<uint32_t>*>(q->eng)->put_htab(R->htab.p, R->hmask)
-        : static_cast<Engine<unsigned long long>*>(q->eng)->put_htab(R->htab.p, R->hmask);
-    if (hr != WG_OK) { c->queries.erase(q->id); return hr; }
+    TRY(R->kb == 4
+            ? static_cast<Engine<uint32_t>*>(q->eng)->put_htab(R->htab.p, R->hmask)
+            : static_cast<Engine<unsigned long long>*>(q->eng)->put_htab(R->htab.p, R->hmask));
   }
   if (R->kb == 4) {
     auto* E = static_cast<Engine<uint32_t>*>(q->eng);
     E->regrows = 0; E->launches_issued = 0;
-    rc = single_start<uint32_t>(c, q);
-  } else {
-    auto* E = static_cast<Engine<unsigned long long>*>(q->eng);
-    E->regrows = 0; E->launches_issued = 0;
-    rc = single_start<unsigned long long>(c, q);
+    return single_start<uint32_t>(c, q);
   }
+  auto* E = static_cast<Engine<unsigned long long>*>(q->eng);
+  E->regrows = 0; E->launches_issued = 0;
+  return single_start<unsigned long long>(c, q);
+}
+
+static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, wg_query* out) {
+  if (!c || !out) return set_err(WG_E_INVAL, "bad argument");
+  *out = 0;
+  Query* q;
+  TRY(make_query(c, kind, edges, opts, &q));
+  const int rc = single_begin(c, q);
   if (rc != WG_OK) {  // nothing left running: drop the query, its engine goes back idle
     q->state = WG_FAILED;
     q->error = rc;
@@ -1788,6 +1826,139 @@ static int single_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, 
   *out = q->id;
   return WG_OK;
 }
+
+}  // extern "C" (templates below)
+
+// ------------------------------------------------------------------ served large requests
+// A served request over more than kSoloEdges edges runs on a single-query
+// engine, one at a time on the context stream, while the batch engines take
+// the small requests.  A growth over the budget pauses it with its state as
+// the exclusive query: the batch engines admit nothing, drain and are
+// dropped, then it grows and resumes from the iteration that overflowed; if
+// it does not fit with the whole budget it fails.  If another query is
+// already exclusive it is requeued instead (restarting later).
+template <typename K>
+static int solo_resume(wg_ctx* c, Query* q) {
+  auto* E = static_cast<Engine<K>*>(q->eng);
+  const int rc = E->grow();
+  if (rc == WG_E_BUDGET || rc == WG_E_NOMEM) {
+    cudaGetLastError();
+    q->wait_used = c->used;
+    return WG_OK;
+  }
+  TRY(rc);
+  q->solo_wait = false;
+  const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
+  return E->launch(0xFFFFFFFFu, host_loop);
+}
+
+static void solo_requeue(wg_ctx* c, Query* q) {
+  if (q->own) c->idle.push_back(std::move(q->own));  // its pools may be dropped meanwhile
+  q->eng = nullptr;
+  q->solo_wait = false;
+  q->state = WG_PENDING;
+  q->regrows += 1;
+  c->pending.insert(c->pending.begin(), q->id);
+  if (c->solo_run == q->id) c->solo_run = 0;
+}
+
+static void solo_finish(wg_ctx* c, Query* q, int rc) {
+  if (rc != WG_OK && q->state != WG_FAILED) {
+    q->state = WG_FAILED;
+    q->error = rc;
+  }
+  if (c->excl == q->id) c->excl = 0;
+  q->t_done_us = now_us();
+  c->completed.push_back(q->id);
+  if (c->solo_run == q->id) c->solo_run = 0;
+}
+
+static int solo_round(wg_ctx* c, bool* progressed, bool* busy) {
+  *busy = false;
+  if (c->solo_run && !solo_running(c)) c->solo_run = 0;  // freed while running
+  if (c->solo_run) {
+    Query* q = c->queries.find(c->solo_run)->second.get();
+    const bool k4 = q->eng->kb() == 4;
+    if (q->solo_wait) {
+      Query* x = excl_query(c);
+      if (x && x != q) {  // another query waits for the whole budget first
+        solo_requeue(c, q);
+        *progressed = true;
+        return WG_OK;
+      }
+      c->excl = q->id;
+      if (drop_idle_batch(c, -1) || c->used < q->wait_used) {
+        TRY(k4 ? solo_resume<uint32_t>(c, q) : solo_resume<unsigned long long>(c, q));
+        if (!q->solo_wait) *progressed = true;
+      }
+      if (q->solo_wait) {
+        bool held = false;  // memory that may still come back
+        for (auto& kv : c->batch) held |= kv.second != nullptr;
+        if (!held) {
+          solo_finish(c, q, WG_E_BUDGET);
+          *progressed = true;
+        }
+        return WG_OK;
+      }
+    }
+    const int rc = k4 ? single_progress<uint32_t>(c, q, false, true)
+                      : single_progress<unsigned long long>(c, q, false, true);
+    if (q->solo_wait) {  // paused: exclusive from now on, unless another query is
+      Query* x = excl_query(c);
+      if (x && x != q) solo_requeue(c, q);
+      else c->excl = q->id;
+      *progressed = true;
+      return WG_OK;
+    }
+    if (q->state == WG_RUNNING && rc == WG_OK) {
+      *busy = true;
+      return WG_OK;
+    }
+    solo_finish(c, q, rc);
+    *progressed = true;
+    if (rc == WG_E_CUDA || rc == WG_E_DEVICE_TIMEOUT) return rc;
+  }
+  // start the next queued large request
+  Query* x = excl_query(c);
+  for (size_t i = 0; i < c->pending.size(); ++i) {
+    auto it = c->queries.find(c->pending[i]);
+    if (it == c->queries.end() || !it->second->solo) continue;
+    Query* q = it->second.get();
+    if (x && x != q) return WG_OK;  // only the exclusive query may start
+    if (x == q) {  // once the batch engines hold no work, they go
+      for (auto& kv : c->batch)
+        if (batch_holds_work_any(c, kv.first)) return WG_OK;
+      drop_idle_batch(c, -1);
+    }
+    c->pending.erase(c->pending.begin() + i);
+    q->state = WG_RUNNING;
+    c->solo_run = q->id;
+    *progressed = true;
+    const int rc = single_begin(c, q);
+    if (rc == WG_OK) {
+      *busy = true;
+      return WG_OK;
+    }
+    if (rc != WG_E_BUDGET && rc != WG_E_NOMEM) {
+      solo_finish(c, q, rc);
+      return WG_OK;  // the request failed; the server carries on
+    }
+    cudaGetLastError();
+    bool held = false;
+    for (auto& kv : c->batch) held |= kv.second != nullptr;
+    if (held && (!x || x == q)) {  // wait for the whole budget
+      solo_requeue(c, q);
+      q->regrows -= 1;
+      c->excl = q->id;
+    } else {
+      solo_finish(c, q, rc);
+    }
+    return WG_OK;
+  }
+  return WG_OK;
+}
+
+extern "C" {
 
 int wg_tc(wg_ctx* c, wg_rel edges, const wg_opts* opts, wg_query* out) {
   return single_query(c, WG_TC, edges, opts, out);
@@ -1805,8 +1976,14 @@ int wg_submit(wg_ctx* c, const wg_request* reqs, size_t n, wg_query* ids) {
     TRY(make_query(c, reqs[i].kind, reqs[i].edges, &reqs[i].opts, &q));
     q->batch = true;
     q->bclass = batch_class(q->rel);
-    if (!excl_query(c)) TRY(ensure_batch_engine(c, q->bclass, q->rel));
-    else c->batch[q->bclass];  // the class is listed; its engine is built on demand
+    q->solo = q->rel->ne > kSoloEdges;
+    if (q->solo) {
+      // runs on a single-query engine (solo_round)
+    } else if (!excl_query(c)) {
+      TRY(ensure_batch_engine(c, q->bclass, q->rel));
+    } else {
+      c->batch[q->bclass];  // the class is listed; its engine is built on demand
+    }
     c->pending.push_back(q->id);
     ids[i] = q->id;
   }
@@ -1844,7 +2021,8 @@ static int progress(wg_ctx* c, Query* q, bool block) {
   if (q->batch) {
     // drive the batch engines until this query is retired
     if (!block) {
-      bool progressed = false;
+      bool progressed = false, busy = false;
+      TRY(solo_round(c, &progressed, &busy));
       for (auto& kv : c->batch) TRY(batch_round_any(c, kv.first, 0xFFFFFFFFu, false, &progressed));
       return WG_OK;
     }

@@ -186,23 +186,35 @@ def test_failed_growth_leaves_engines_whole(budget_mb):
         h.free()
 
 
-@functools.lru_cache(maxsize=1)
-def _exclusive_cases():
-    big = I.er_graph(5000, 7000, 77)  # > 4,096 vertices: its own engine; 6.3 M tuples
+def _components(k, n, m, seed):
+    """k disjoint ER graphs of n nodes and m edges each (vertex ids offset)."""
+    gs = [I.er_graph(n, m, seed + i) for i in range(k)]
+    src = np.concatenate([g.src + np.uint32(i * n) for i, g in enumerate(gs)]).astype(np.uint32)
+    dst = np.concatenate([g.dst + np.uint32(i * n) for i, g in enumerate(gs)]).astype(np.uint32)
+    return I.EdgeList(src, dst, dict(recipe=f"{k} x ER({n}, {m})"))
+
+
+@functools.lru_cache(maxsize=2)
+def _exclusive_cases(big_kind):
+    if big_kind == "batch":  # > 4,096 vertices: its own batch engine; 6.3 M tuples
+        big = I.er_graph(5000, 7000, 77)
+    else:  # > 65,536 edges: served on a single-query engine; 9.9 M tuples
+        big = _components(150, 500, 700, 900)
     smalls = [I.er_graph(n, 3 * n, 300 + n) for n in (800, 1100, 1400, 1700, 2000, 900, 1300, 1900)]
     return (big, smalls, oracle_tc(big.src, big.dst),
             [oracle_tc(g.src, g.dst) for g in smalls])
 
 
+@pytest.mark.parametrize("big_kind", ["batch", "solo"])
 @pytest.mark.parametrize("budget_mb", [96, 128, 192])
-def test_query_that_fits_alone_completes_in_a_mix(budget_mb):
-    """A batched query that completes when it is the only request finishes
+def test_query_that_fits_alone_completes_in_a_mix(budget_mb, big_kind):
+    """A served request that completes when it is the only request finishes
     in a mix too, under the same budget with the same relations resident:
-    when its engine cannot grow because another engine holds pools, it waits
-    as the exclusive query for the others to drain, then runs with the whole
-    budget."""
+    when it cannot grow because other engines hold pools, it waits as the
+    exclusive query for them to drain, then runs with the whole budget --
+    in a batch engine, or (over 65,536 edges) on a single-query engine."""
     from paper_2607_17571_gb300 import wg
-    big, smalls, want_big, want_smalls = _exclusive_cases()
+    big, smalls, want_big, want_smalls = _exclusive_cases(big_kind)
 
     def run(mix):
         with wg.Context(0, mem_budget=budget_mb << 20) as c:
@@ -225,6 +237,29 @@ def test_query_that_fits_alone_completes_in_a_mix(budget_mb):
 
     if run(mix=False):
         assert run(mix=True)
+
+
+def test_large_requests_served_on_single_engines(ctx):
+    """Served requests over 65,536 edges run one at a time on single-query
+    engines beside the batch engines taking the small ones: every result
+    equals the oracle's (and the per-iteration sizes too), whatever engine
+    ran it."""
+    from paper_2607_17571_gb300 import wg
+    bigs = [_components(500, 100, 140, 900), _components(300, 200, 240, 1900)]
+    smalls = [g for _, g in _mix(11, n_q=12)]
+    gs = smalls[:6] + bigs[:1] + smalls[6:] + bigs[1:]
+    kinds = [wg.WG_TC] * len(gs)
+    want = [oracle_tc(g.src, g.dst) for g in gs]
+    rels = [ctx.load(g.src, g.dst) for g in gs]
+    hs = ctx.submit(list(zip(kinds, rels)))
+    for h, w, g in zip(hs, want, gs):
+        st = h.wait()
+        assert np.array_equal(h.result(), w.keys) and h.delta_sizes() == w.log.tolist()
+        if len(g) > (1 << 16):
+            assert st.gpu_launches > 0  # launched by its own engine
+        h.free()
+    for r in rels:
+        r.free()
 
 
 def test_iteration_cap_in_batch(ctx):
