@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_join_emit_hash(Stage* stp) {
 
 // ------------------------------------------------------------------ join count
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 4) k_join_count(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
   __shared__ K sd[kTileD];
   __shared__ unsigned long long sp[kTileD];
   __shared__ unsigned long long s_scan[kWarps];

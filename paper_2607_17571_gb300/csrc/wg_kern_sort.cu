@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t digit(K k, uint32_t shift, uint32_t mask) {
 
 // ------------------------------------------------------------------ histogram
 template <typename K>
-__global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
   __shared__ K sk[Padded<kTileC>::n];
   __shared__ uint32_t sh[kMaxPasses * kRadix];
   __shared__ uint32_t s_t;
@@ -84,6 +84,8 @@ __global__ void __launch_bounds__(kThreads) k_sort_hist(Stage* stp) {
 }
 
 // ------------------------------------------------------------------ one radix pass
+constexpr int kLookW = 8;  // lookback words a digit thread loads at once
+
 struct PassMeta {
   uint32_t t, k, n, first;  // tile, segment, keys in the tile, first tile of its segment
 };
@@ -95,7 +97,10 @@ struct PassSmem {
   uint32_t whist[kWarps][kRadix];       // per-warp counts -> prefix over warps
   uint32_t tstart[kSlots][kRadix];      // digit start inside the tile
   uint32_t tcnt[kSlots][kRadix];        // digit count of the tile
-  unsigned long long gdst[kRadix];      // global base of each digit minus tstart
+  union {                               // global base of each digit minus tstart:
+    unsigned long long gdst[kRadix];    //   absolute, or
+    uint32_t gdst32[kRadix];            //   from the segment's start (segments < 2^32 keys)
+  };
   unsigned long long s_scan[kWarps];
   PassMeta meta[kSlots];
   uint32_t s_t, s_bad;
@@ -103,16 +108,16 @@ struct PassSmem {
 
 // Rank tile t into slot `sl`: load, rank every key within its digit, publish
 // the tile's digit counts and place the keys in digit order in shared memory.
-// Nothing here waits for another tile.
-template <typename K>
-__device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, uint32_t t, int sl) {
+// Nothing here waits for another tile.  kFull: the tile holds kTileC keys
+// (every bounds test folds away).
+template <typename K, bool kFull>
+__device__ __forceinline__ void pass_rank_tile(Stage* stp, PassSmem<K>& S, uint32_t t, int sl,
+                                               uint32_t k, const Seg& sg, uint32_t n_tile) {
   const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u, pass = stp->pass;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
-  const Seg sg = stp->segs[k];
+  const uint32_t n = kFull ? (uint32_t)kTileC : n_tile;
   const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
-  const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
   const K* p = (const K*)stp->in + sg.in_off + start;
   for (uint32_t i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&S.whist[0][0])[i] = 0;
   if (threadIdx.x == 0) S.s_bad = 0;
@@ -180,6 +185,21 @@ __device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, uint32_t t
     }
 }
 
+template <typename K>
+__device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, uint32_t t, int sl) {
+  const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
+  const Seg sg = stp->segs[k];
+  const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+  const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+  if constexpr (sizeof(K) == 4) {  // (64-bit keys: no room for a second copy in 64 registers)
+    if (n == (uint32_t)kTileC) {
+      pass_rank_tile<K, true>(stp, S, t, sl, k, sg, n);
+      return;
+    }
+  }
+  pass_rank_tile<K, false>(stp, S, t, sl, k, sg, n);
+}
+
 // Global offsets of the tile in slot `sl` by per-digit lookback, then stream
 // its digit runs out.  False when a lookback gave up (the run is void).
 template <typename K>
@@ -195,25 +215,40 @@ __device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
   const unsigned long long hcount =
       stp->hist[((unsigned long long)m.k * stp->passes + stp->pass) * kRadix + d];
   unsigned long long excl = 0;
-  if (!m.first) {  // per-digit lookback over earlier tiles of this segment
-    const unsigned long long tile0 = sg.tile0;
+  if (!m.first) {
+    // per-digit lookback over earlier tiles of this segment: the words of a
+    // window of kLookW predecessors are loaded at once, then consumed nearest
+    // first until an inclusive one (a walk of dependent loads would cost one
+    // L2 round trip per tile, and tiles behind this one wait for it)
+    const long long tile0 = sg.tile0;
     long long j = (long long)m.t - 1;
-    for (;;) {
-      unsigned long long s = st_get(status + (unsigned long long)j * kRadix + d);
-      uint32_t spins = 0;
-      while (!st_ready(s, epoch)) {
-        if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) break;
-        __nanosleep(64);
-        s = st_get(status + (unsigned long long)j * kRadix + d);
+    bool done = false;
+    while (!done) {
+      const long long w = min((long long)kLookW, j - tile0 + 1);
+      unsigned long long sw[kLookW];
+#pragma unroll
+      for (int q = 0; q < kLookW; ++q)
+        sw[q] = q < w ? st_get(status + (unsigned long long)(j - q) * kRadix + d) : 0ull;
+#pragma unroll
+      for (int q = 0; q < kLookW; ++q) {
+        if (done || q >= w) break;
+        unsigned long long s = sw[q];
+        uint32_t spins = 0;
+        while (!st_ready(s, epoch)) {
+          if (++spins > kSpinLimit || *(volatile uint32_t*)&ctl->abort) break;
+          __nanosleep(64);
+          s = st_get(status + (unsigned long long)(j - q) * kRadix + d);
+        }
+        if (!st_ready(s, epoch)) {
+          if (!*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
+          S.s_bad = 1;
+          done = true;
+          break;
+        }
+        excl += s & kValMask;
+        if (((s >> 38) & 3u) == FLAG_INC || j - q == tile0) done = true;
       }
-      if (!st_ready(s, epoch)) {
-        if (!*(volatile uint32_t*)&ctl->abort) fail_timeout(ctl);
-        S.s_bad = 1;
-        break;
-      }
-      excl += s & kValMask;
-      if (((s >> 38) & 3u) == FLAG_INC || j == (long long)tile0) break;
-      --j;
+      j -= w;
     }
     st_put(status + (unsigned long long)m.t * kRadix + d,
            st_pack(epoch, FLAG_INC, excl + S.tcnt[sl][d]));
@@ -222,13 +257,33 @@ __device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
   // scan of the segment's histogram row (one digit per thread)
   unsigned long long htot;
   const unsigned long long hstart = block_excl_scan(hcount, S.s_scan, &htot);
-  S.gdst[d] = sg.out_off + hstart + excl - S.tstart[sl][d];
+  // a segment of fewer than 2^32 keys: 32-bit offsets from its start
+  const bool rel32 = sg.n <= 0xFFFFFFFFull;
+  if (rel32) S.gdst32[d] = (uint32_t)(hstart + excl - S.tstart[sl][d]);
+  else S.gdst[d] = sg.out_off + hstart + excl - S.tstart[sl][d];
   __syncthreads();
   if (S.s_bad) return false;
   K* out = (K*)stp->out;
-  for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
-    const K v = S.sk[sl][i];
-    out[S.gdst[digit(v, shift, mask)] + i] = v;
+  if (rel32) {
+    K* outs = out + sg.out_off;
+    if (m.n == (uint32_t)kTileC) {
+#pragma unroll
+      for (int e = 0; e < kItemsC; ++e) {
+        const uint32_t i = threadIdx.x + e * kThreads;
+        const K v = S.sk[sl][i];
+        outs[S.gdst32[digit(v, shift, mask)] + i] = v;
+      }
+    } else {
+      for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
+        const K v = S.sk[sl][i];
+        outs[S.gdst32[digit(v, shift, mask)] + i] = v;
+      }
+    }
+  } else {
+    for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
+      const K v = S.sk[sl][i];
+      out[S.gdst[digit(v, shift, mask)] + i] = v;
+    }
   }
   return true;
 }
@@ -651,7 +706,7 @@ __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint
 // had one tile time to publish.  Deadlock-free: publishing a tile's count
 // never waits, so the oldest unfinished tile can always complete its lookback.
 template <typename K>
-__global__ void __launch_bounds__(kThreads, 4) k_diff_merge(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 5) k_diff_merge(Stage* stp) {
   constexpr int T = FuseTile<K>::T;
   static_assert(FuseTile<K>::E <= 16 && T <= 65535, "masks and prefixes are packed in 16 bits");
   __shared__ K sbuf[2][Padded<T>::n];  // tile input, then its kept elements in Full' order
