@@ -200,6 +200,8 @@ def run_ours(args):
     def run(r, **kw):
         return run0(r, loop=loop, **kw)
     kb = 4 if 2 * info["field_bits"] <= 32 else 8
+    tiles = None if args.no_autotune else autotune_ctx(
+        ctx, [rel], wg.WG_TC if wl["kind"] == "tc" else wg.WG_SG)
 
     # warm-up: also sizes the pools (a relation remembers the capacities it needed)
     st = None
@@ -308,7 +310,8 @@ def run_ours(args):
                            "candidates": int(st.candidates), "edges": n,
                            "vertices": info["n_vertices"], "field_bits": info["field_bits"],
                            "l2": "flushed between steps (256 MB write); working set > L2",
-                           "parallelism": f"replicas x{world}", "regrows_timed": regrows},
+                           "parallelism": f"replicas x{world}", "regrows_timed": regrows,
+                           "tiles": tiles or "compiled defaults"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": int(launches)}
         print(json.dumps(line))
@@ -317,6 +320,23 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def autotune_ctx(ctx, rels, kind=None):
+    """wg_autotune on the largest relation of each key width (outside every
+    timed region); engines the context creates afterwards use the shapes."""
+    from paper_2607_17571_gb300 import wg
+    best = {}
+    for i, r in enumerate(rels):
+        info = r.info()
+        kb = 4 if 2 * info["field_bits"] <= 32 else 8
+        if kb not in best or info["n_edges"] > best[kb][1]:
+            best[kb] = (i, info["n_edges"])
+    out = {}
+    for kb, (i, _) in sorted(best.items()):
+        t = ctx.autotune(rels[i], wg.WG_TC if kind is None else kind)
+        out[f"{kb}B_keys"] = {k: t[k] for k in ("count_tile", "fuse_tile", "count_ms", "fuse_ms")}
+    return out
 
 
 def _pct(xs, p):
@@ -350,6 +370,9 @@ def run_batch(args):
             ctx.close()
         ctx = wg.Context(0)
         rels = [ctx.load(g.src, g.dst) for g in graphs]
+        if not args.no_autotune:
+            tuned.update(autotune_ctx(ctx, rels))
+    tuned = {}
     # parity sample: the smallest queries, checked against the oracle
     order = sorted(range(len(sizes)), key=lambda i: sizes[i][0])
     sample = set(order[:: max(1, len(order) // 24)][:24])
@@ -415,7 +438,8 @@ def run_batch(args):
             "config": {"workload": "batch4096", "queries": n,
                        "desc": "ER TC queries, n log-uniform [64,16384], mean degree U[1.2,3.0], "
                                "seeds 40000+q", "closure_tuples_total": int(nb),
-                       "iterations_per_launch": args.batch_iters},
+                       "iterations_per_launch": args.batch_iters,
+                       "tiles": tuned or "compiled defaults"},
             "batched": {"seconds": round(tb, 3), "queries_per_s": n / tb, "tuples_per_s": nb / tb,
                         "p50_ms": _pct(lb, 50), "p99_ms": _pct(lb, 99), "parity_failures": bad_b},
             "plain_loop": {"seconds": round(tp, 3), "queries_per_s": n / tp,
@@ -750,6 +774,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the compiled tile shapes instead of running wg_autotune first")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tc_rmat17_400k",
                     choices=sorted(WORKLOADS) + ["batch4096", "serve", "tri_rmat16_800k",

@@ -213,6 +213,38 @@ int wg_result_profile(wg_ctx* ctx, wg_query q, wg_kernel_stat* stats, size_t cap
                       size_t* n_out);
 void wg_query_free(wg_ctx* ctx, wg_query q);
 
+/* ---- tile shapes and the autotuner --------------------------------------
+ * Two stages have a compiled choice of tile shape: the join count (delta
+ * tuples per tile: 2,048 or 1,024) and the fused deduplication / set
+ * difference / merge pass (merged keys per tile: 4,096 or 2,048 for 4-byte
+ * keys, 2,048 or 1,024 for 8-byte keys).  Sec. Fused Deduplication fixes its
+ * own workgroup tile (256 threads x 12 keys) for its hardware; here the
+ * shape is an engine setting, the same results for every choice.
+ *
+ * wg_autotune: time each candidate on a profiled fixpoint of `edges` (kind
+ * WG_TC or WG_SG; one warm-up run and one timed run per candidate, the join
+ * count and the fused stage timed with CUDA events) and keep the faster
+ * shape of each stage in the context for the relation's key width: every
+ * engine created afterwards (single, batched, served) uses it.  `out` may be
+ * NULL.  Synchronous; runs on the context stream.  Errors: WG_E_INVAL (bad
+ * handle or kind), WG_E_NOMEM / WG_E_BUDGET (a run's pools do not fit),
+ * WG_E_CUDA.  On an error the context keeps its previous shapes.
+ *
+ * wg_set_tiles: set the shapes for key width key_bytes (4 or 8) directly,
+ * e.g. from a saved wg_tune; 0 = the compiled default.  Errors: WG_E_INVAL
+ * (a shape that is not one of the compiled candidates). */
+typedef struct wg_tune {
+  uint32_t key_bytes;           /* key width the shapes apply to */
+  uint32_t count_tile;          /* chosen delta tuples per join-count tile */
+  uint32_t fuse_tile;           /* chosen merged keys per fused-pass tile */
+  uint32_t count_cand[2];       /* candidates (default first) */
+  uint32_t fuse_cand[2];
+  double count_ms[2];           /* join-count time per fixpoint, per candidate */
+  double fuse_ms[2];            /* fused-stage time per fixpoint, per candidate */
+} wg_tune;
+int wg_autotune(wg_ctx* ctx, wg_rel edges, int kind, wg_tune* out);
+int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_tile);
+
 /* ---- sorted-array primitives (the stages of one iteration) ---------------
  * Device buffers of packed keys, key_bytes = 4 (uint32) or 8 (uint64).  They
  * run on the context stream, use context scratch, and synchronise the stream

@@ -120,13 +120,11 @@ struct Inst {
 enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
                      S_NUM = S_PASS0 + kMaxPasses };
 
-// Tile of the join count: 3,072 / 2,048 delta tuples (static shared memory
-// holds the tuples and their 64-bit slab offsets, under 48 KB).
-template <typename K> struct CountTile { static constexpr int T = sizeof(K) == 4 ? 3072 : 2048; };
 // Full-relation window staged by dedup + diff (separate-stage mode).
 template <typename K> struct FWin { static constexpr int n = sizeof(K) == 4 ? 2048 : 1024; };
 
-// Tile of the fused dedup + set difference + merge: 16 KB of keys.
+// Tile of the fused dedup + set difference + merge: 16 KB of keys by default
+// (half of it is the other compiled shape the autotuner may pick).
 template <typename K> struct FuseTile {
   static constexpr int T = sizeof(K) == 4 ? 4096 : 2048;
   static constexpr int E = T / kThreads;

@@ -85,6 +85,9 @@ struct wg_ctx {
   std::vector<uint64_t> completed;                // batch queries finished, not yet taken
   uint64_t excl = 0;  // batch query that runs with the whole budget (0: none), see batch_preempt
   uint64_t solo_run = 0;  // the served request running on a single-query engine (0: none)
+  // tile shapes engines are built with, per key width (index 0: 4-byte keys,
+  // 1: 8-byte); 0 = the compiled default.  Set by wg_autotune / wg_set_tiles.
+  uint32_t tune_count[2] = {0, 0}, tune_fuse[2] = {0, 0};
   cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
@@ -241,7 +244,7 @@ static int tri_count(wg_ctx* c, Relation* R, unsigned long long* count) {
   k.in = R->keys.p; k.inst = (Inst*)inst.p; k.pos = (unsigned long long*)pos.p;
   k.epoch = prim_epoch(c);
   TRY(prim_put(c, S_COUNT, k));
-  launch_join_count<K>(c->s_stage + S_COUNT, grid_of(c, occupancy_join<K>(0)), c->stream);
+  launch_join_count<K>(c->s_stage + S_COUNT, grid_of(c, occupancy_join<K>(0)), c->stream, kTileD);
   CK(cudaGetLastError());
   Seg back{};
   Ctl ctl{};
@@ -441,8 +444,20 @@ struct EngineBase {
   virtual bool xgrouped() const = 0;
   virtual bool copyback() const = 0;
   virtual bool hashjoin() const = 0;
+  virtual uint32_t count_tile() const = 0;
+  virtual uint32_t fuse_tile() const = 0;
   virtual void release() = 0;
 };
+
+// The tile shapes a new engine of key type K takes from the context.
+template <typename K> static uint32_t count_tile_of(const wg_ctx* c) {
+  const uint32_t v = c->tune_count[sizeof(K) == 8];
+  return v ? v : (uint32_t)kTileD;
+}
+template <typename K> static uint32_t fuse_tile_of(const wg_ctx* c) {
+  const uint32_t v = c->tune_fuse[sizeof(K) == 8];
+  return v ? v : (uint32_t)FuseTile<K>::T;
+}
 
 struct Query {
   uint64_t id = 0;
@@ -503,10 +518,12 @@ struct Engine : EngineBase {
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
+  uint32_t count_tile_, fuse_tile_;  // delta tuples per join-count tile, keys per fused tile
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
          bool xseg_, bool copy_back_ = false, bool hash_join_ = false)
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
-        log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_) {
+        log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_),
+        count_tile_(count_tile_of<K>(ctx)), fuse_tile_(fuse_tile_of<K>(ctx)) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
@@ -515,6 +532,8 @@ struct Engine : EngineBase {
   bool xgrouped() const override { return xseg; }
   bool copyback() const override { return copy_back; }
   bool hashjoin() const override { return hash_join; }
+  uint32_t count_tile() const override { return count_tile_; }
+  uint32_t fuse_tile() const override { return fuse_tile_; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -563,22 +582,22 @@ struct Engine : EngineBase {
     Seg* s = (Seg*)b_seg.p;
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
     h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
-    h.fuse = fuse ? 1 : 0; h.fuse_tile = FuseTile<K>::T; h.xseg = xseg ? 1 : 0;
+    h.fuse = fuse ? 1 : 0; h.fuse_tile = fuse_tile_; h.xseg = xseg ? 1 : 0;
     h.copyback = copy_back && single && fuse ? 1 : 0;
-    h.count_tile = CountTile<K>::T;
+    h.count_tile = count_tile_;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
     h.ctl.iter_budget = 0xFFFFFFFFu;
     CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, st));
     CK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
-    g_count = grid_of(c, occupancy_join<K>(0));
+    g_count = grid_of(c, occupancy_join<K>(count_tile_ == (uint32_t)kTileD ? 0 : 3));
     g_emit = grid_of(c, occupancy_join<K>(1));
     g_hist = grid_of(c, occupancy_sort<K>(0));
     g_pass = grid_of(c, occupancy_sort<K>(1));
     g_uniq = grid_of(c, occupancy_sort<K>(2));
     g_merge = grid_of(c, occupancy_sort<K>(3));
-    g_fuse = grid_of(c, occupancy_sort<K>(4));
+    g_fuse = grid_of(c, occupancy_sort<K>(fuse_tile_ == (uint32_t)FuseTile<K>::T ? 4 : 5));
     return WG_OK;
   }
 
@@ -641,7 +660,7 @@ struct Engine : EngineBase {
        // counts.  Sized by an exact tile count (mix_tiles), never by the
        // rounded-up byte size of one of them: they are carved differently
       const unsigned long long nC = std::max(capC, wantC), nF = std::max(capF, wantF);
-      const size_t tiles = std::max<size_t>(nC / kTileD, nF / FuseTile<K>::T) + n_slots + 2;
+      const size_t tiles = std::max<size_t>(nC / count_tile_, nF / fuse_tile_) + n_slots + 2;
       if (tiles > mix_tiles) {
         DBuf ns, np, nm;
         int rc = ns.get(c, tiles * 8);
@@ -725,7 +744,7 @@ struct Engine : EngineBase {
     };
     (void)prof;
     launch_plan_delta(dv, s);
-    mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s); mark();
+    mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s, count_tile_); mark();
     launch_plan_cand(dv, s);
     if (xseg) launch_xseg_build(dv, s);
     if (hash_join) {
@@ -739,14 +758,14 @@ struct Engine : EngineBase {
       mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
     }
     if (fuse) {
-      launch_partition<K>(dv->st + S_FUSE, 0, FuseTile<K>::T, c->num_sms * 4, s);
+      launch_partition<K>(dv->st + S_FUSE, 0, fuse_tile_, c->num_sms * 4, s);
       // mixed tiles through the fused kernel, Full-only tiles by a plain copy
       // (timed together as the fused stage)
       mark();
       launch_fuse_mark(dv, c->num_sms * 2, s);
       launch_fuse_list(dv, c->num_sms * 2, s);
-      launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s);
-      launch_fuse_copy<K>(dv->st + S_FUSE, c->num_sms * 8, s);
+      launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s, fuse_tile_);
+      launch_fuse_copy<K>(dv->st + S_FUSE, c->num_sms * 8, s, fuse_tile_);
       mark();
       launch_plan_post(dv, s);
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
@@ -1781,10 +1800,13 @@ static int single_begin(wg_ctx* c, Query* q) {
   // destination field only (per-vertex histograms bound the vertex count)
   const bool xseg = !full_width && kind == WG_TC && R->nv <= kXSegMaxVertices;
   const uint32_t bits = full_width ? 8u * R->kb : xseg ? R->w : 2 * R->w;
+  const uint32_t ct = R->kb == 4 ? count_tile_of<uint32_t>(c) : count_tile_of<unsigned long long>(c);
+  const uint32_t ft = R->kb == 4 ? fuse_tile_of<uint32_t>(c) : fuse_tile_of<unsigned long long>(c);
   for (size_t i = 0; i < c->idle.size() && !q->own; ++i)
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
         c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
-        c->idle[i]->hashjoin() == hashjoin) {
+        c->idle[i]->hashjoin() == hashjoin && c->idle[i]->count_tile() == ct &&
+        c->idle[i]->fuse_tile() == ft) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
     }
@@ -2107,6 +2129,69 @@ int wg_result_profile(wg_ctx* c, wg_query id, wg_kernel_stat* stats, size_t cap,
     stats[i].total_ms = q->prof[i].ms;
     stats[i].bytes = q->prof[i].bytes;
   }
+  return WG_OK;
+}
+
+int wg_set_tiles(wg_ctx* c, int key_bytes, uint32_t count_tile, uint32_t fuse_tile) {
+  if (!c || (key_bytes != 4 && key_bytes != 8)) return set_err(WG_E_INVAL, "bad argument");
+  const uint32_t T = key_bytes == 4 ? FuseTile<uint32_t>::T : FuseTile<unsigned long long>::T;
+  if (count_tile && count_tile != (uint32_t)kTileD && count_tile != (uint32_t)kTileD / 2)
+    return set_err(WG_E_INVAL, "count tile is not a compiled shape");
+  if (fuse_tile && fuse_tile != T && fuse_tile != T / 2)
+    return set_err(WG_E_INVAL, "fused tile is not a compiled shape");
+  c->tune_count[key_bytes == 8] = count_tile;
+  c->tune_fuse[key_bytes == 8] = fuse_tile;
+  return WG_OK;
+}
+
+// One profiled fixpoint: the join-count and fused-stage times (ms).
+static int tune_run(wg_ctx* c, wg_rel edges, int kind, double* count_ms, double* fuse_ms) {
+  wg_opts o{};
+  o.profile = 1;
+  wg_query id = 0;
+  TRY(single_query(c, kind, edges, &o, &id));
+  const int rc = wg_wait(c, id, 0);
+  *count_ms = *fuse_ms = 0;
+  if (rc == WG_OK) {
+    Query* q = find_q(c, id);
+    for (const KStat& k : q->prof) {
+      if (!std::strcmp(k.name, "join_count")) *count_ms = k.ms;
+      if (!std::strcmp(k.name, "dedup_diff_merge") || !std::strcmp(k.name, "dedup_diff")) *fuse_ms += k.ms;
+    }
+  }
+  wg_query_free(c, id);
+  return rc;
+}
+
+int wg_autotune(wg_ctx* c, wg_rel edges, int kind, wg_tune* out) {
+  if (!c || (kind != WG_TC && kind != WG_SG)) return set_err(WG_E_INVAL, "bad argument");
+  auto it = c->rels.find(edges);
+  if (it == c->rels.end()) return set_err(WG_E_INVAL, "no such relation");
+  const int kb = it->second->kb, i = kb == 8;
+  const uint32_t T = kb == 4 ? FuseTile<uint32_t>::T : FuseTile<unsigned long long>::T;
+  wg_tune t{};
+  t.key_bytes = (uint32_t)kb;
+  t.count_cand[0] = kTileD; t.count_cand[1] = kTileD / 2;
+  t.fuse_cand[0] = T; t.fuse_cand[1] = T / 2;
+  const uint32_t keep_count = c->tune_count[i], keep_fuse = c->tune_fuse[i];
+  for (int v = 0; v < 2; ++v) {
+    // the two stages are separate kernels: one run per candidate pair times both
+    c->tune_count[i] = t.count_cand[v];
+    c->tune_fuse[i] = t.fuse_cand[v];
+    for (int rep = 0; rep < 2; ++rep) {  // the first run grows the engine's pools
+      const int rc = tune_run(c, edges, kind, &t.count_ms[v], &t.fuse_ms[v]);
+      if (rc != WG_OK) {
+        c->tune_count[i] = keep_count;
+        c->tune_fuse[i] = keep_fuse;
+        return rc;
+      }
+    }
+  }
+  t.count_tile = t.count_ms[1] < t.count_ms[0] ? t.count_cand[1] : t.count_cand[0];
+  t.fuse_tile = t.fuse_ms[1] < t.fuse_ms[0] ? t.fuse_cand[1] : t.fuse_cand[0];
+  c->tune_count[i] = t.count_tile;
+  c->tune_fuse[i] = t.fuse_tile;
+  if (out) *out = t;
   return WG_OK;
 }
 

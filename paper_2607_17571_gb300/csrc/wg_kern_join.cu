@@ -122,10 +122,13 @@ __global__ void __launch_bounds__(kThreads) k_join_emit_hash(Stage* stp) {
 }
 
 // ------------------------------------------------------------------ join count
-template <typename K>
+// ITEMS delta tuples per thread: a tile of kThreads * ITEMS (the tile shape
+// is an engine setting the autotuner picks; kItemsD by default).
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
-  __shared__ K sd[kTileD];
-  __shared__ unsigned long long sp[kTileD];
+  constexpr int kTile = kThreads * ITEMS;
+  __shared__ K sd[kTile];
+  __shared__ unsigned long long sp[kTile];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_excl;
   __shared__ uint32_t s_xprev, s_xnext;  // sources of the delta tuples around the tile
@@ -150,20 +153,20 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     const uint32_t* off = I->off;
     const uint32_t w = I->w, kind = I->kind, iter = I->iter;
     const K mask = (K)(((K)1 << w) - 1);
-    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileD;
-    const uint32_t n = (uint32_t)min((unsigned long long)kTileD, sg.n - start);
+    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTile;
+    const uint32_t n = (uint32_t)min((unsigned long long)kTile, sg.n - start);
     const K* p = D + sg.in_off + start;
-    tile_to_smem<kItemsD>(sd, p, n, Ident());
+    tile_to_smem<ITEMS>(sd, p, n, Ident());
     if (threadIdx.x == 0) {
       s_bad = 0;
       s_xprev = start > 0 ? (uint32_t)(p[-1] >> w) : 0xFFFFFFFFu;
       s_xnext = start + n < sg.n ? (uint32_t)(p[n] >> w) : 0xFFFFFFFFu;
     }
     __syncthreads();
-    const uint32_t b = threadIdx.x * kItemsD;
-    unsigned long long c[kItemsD], sum = 0;
+    const uint32_t b = threadIdx.x * ITEMS;
+    unsigned long long c[ITEMS], sum = 0;
 #pragma unroll
-    for (int i = 0; i < kItemsD; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
       c[i] = 0;
       if (b + i < n) {
         const K key = sd[b + i];
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     if (s_bad) return;
     unsigned long long run = s_excl + texcl;
 #pragma unroll
-    for (int i = 0; i < kItemsD; ++i)
+    for (int i = 0; i < ITEMS; ++i)
       if (b + i < n) { sp[b + i] = run; run += c[i]; }
     if (stp->xlen) {
       // candidates per source x.  Delta is sorted by x, so x's tuples are one
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
       // start): one atomic where the run starts, one where it ends.
       unsigned long long r = s_excl + texcl;
 #pragma unroll
-      for (int i = 0; i < kItemsD; ++i) {
+      for (int i = 0; i < ITEMS; ++i) {
         if (b + i < n) {
           const uint32_t x = (uint32_t)(sd[b + i] >> w);
           const uint32_t xp = b + i > 0 ? (uint32_t)(sd[b + i - 1] >> w) : s_xprev;
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
     const Inst* I = valid ? dv->inst + q : nullptr;
     const bool act = valid && I->state == INST_ACTIVE;
     const unsigned long long nd = act ? I->n_delta : 0ull;
-    const unsigned long long nt = (nd + kTileD - 1) / kTileD;
+    const unsigned long long nt = (nd + dv->count_tile - 1) / dv->count_tile;
     unsigned long long tot;
     const unsigned long long ex = scan1024(nt, sh, &tot);
     if (valid) {
@@ -953,7 +956,10 @@ __global__ void k_result_map(const K* F, unsigned long long n, uint32_t w, const
 
 // ------------------------------------------------------------------ launchers
 template <typename K>
-void launch_join_count(Stage* st, int grid, cudaStream_t s) { k_join_count<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_join_count(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
+  if (tile == (uint32_t)kTileD / 2) k_join_count<K, kItemsD / 2><<<grid, kThreads, 0, s>>>(st);
+  else k_join_count<K, kItemsD><<<grid, kThreads, 0, s>>>(st);
+}
 template <typename K>
 void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, false><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
@@ -975,8 +981,12 @@ int occupancy_join(int which) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0);
     return b;
   };
-  return which == 0 ? one(k_join_count<K>) : which == 1 ? one(k_join_emit<K, false>)
-                                                         : one(k_join_emit<K, true>);
+  switch (which) {
+    case 0: return one(k_join_count<K, kItemsD>);
+    case 1: return one(k_join_emit<K, false>);
+    case 2: return one(k_join_emit<K, true>);
+    default: return one(k_join_count<K, kItemsD / 2>);
+  }
 }
 void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
@@ -1008,7 +1018,7 @@ void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint3
 }
 
 #define WG_INST(K)                                                                          \
-  template void launch_join_count<K>(Stage*, int, cudaStream_t);                            \
+  template void launch_join_count<K>(Stage*, int, cudaStream_t, uint32_t);                  \
   template void launch_join_emit<K>(Stage*, int, cudaStream_t);                             \
   template void launch_tri_probe<K>(Stage*, int, cudaStream_t);                             \
   template void launch_join_emit_hash<K>(Stage*, int, cudaStream_t);                        \

@@ -540,13 +540,13 @@ struct FuseMeta {
 // mark kept and new elements, publish the tile's new-tuple count, and leave
 // the kept elements in Full' order in sbuf plus, per thread, where its kept
 // run starts, how many new tuples precede it, and its two masks.
-template <typename K>
+template <typename K, int T>
 __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t j, K* sbuf, uint32_t* smask,
                                               uint32_t* spre, FuseMeta* meta,
                                               unsigned long long* s_scan,
                                               unsigned long long* s_a0, unsigned long long* s_a1,
                                               K* s_prev, uint32_t* s_hasprev) {
-  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
+  constexpr int E = T / kThreads;
   const K* Aall = (const K*)stp->in;     // Full
   const K* Ball = (const K*)stp->aux;    // sorted candidates
   const uint32_t t = stp->mixl ? stp->mixl[j] : j;
@@ -671,11 +671,11 @@ __device__ __forceinline__ void fuse_classify(Stage* stp, uint32_t j, K* sbuf, u
 }
 
 // Write out a classified tile once its new-tuple prefix exN is known.
-template <typename K>
+template <typename K, int T>
 __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint32_t* smask,
                                            const uint32_t* spre, const FuseMeta& m,
                                            unsigned long long exN) {
-  constexpr int E = FuseTile<K>::E;
+  constexpr int E = T / kThreads;
   const Seg& sg = stp->segs[m.k];
   K* Nall = (K*)stp->out;                // new delta
   K* Fall = (K*)stp->out2;               // Full'
@@ -705,10 +705,9 @@ __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint
 // back for the previous one, so the predecessors the lookback waits on have
 // had one tile time to publish.  Deadlock-free: publishing a tile's count
 // never waits, so the oldest unfinished tile can always complete its lookback.
-template <typename K>
+template <typename K, int T>
 __global__ void __launch_bounds__(kThreads, 5) k_diff_merge(Stage* stp) {
-  constexpr int T = FuseTile<K>::T;
-  static_assert(FuseTile<K>::E <= 16 && T <= 65535, "masks and prefixes are packed in 16 bits");
+  static_assert(T / kThreads <= 16 && T <= 65535, "masks and prefixes are packed in 16 bits");
   __shared__ K sbuf[2][Padded<T>::n];  // tile input, then its kept elements in Full' order
   __shared__ uint32_t smask[2][kThreads], spre[2][kThreads];
   __shared__ FuseMeta smeta[2];
@@ -723,15 +722,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_diff_merge(Stage* stp) {
   uint32_t cur = 0;
   uint32_t t = claim_tile(stp, &s_t);
   if (t >= ntiles) return;
-  fuse_classify<K>(stp, t, sbuf[0], smask[0], spre[0], &smeta[0], s_scan, &s_a0, &s_a1, &s_prev,
-                   &s_hasprev);
+  fuse_classify<K, T>(stp, t, sbuf[0], smask[0], spre[0], &smeta[0], s_scan, &s_a0, &s_a1, &s_prev,
+                      &s_hasprev);
   for (;;) {
     // next tile first (claim_tile's barriers also publish smeta[cur])
     const uint32_t tn = claim_tile(stp, &s_t);
     const bool more = tn < ntiles;
     if (more)
-      fuse_classify<K>(stp, tn, sbuf[cur ^ 1], smask[cur ^ 1], spre[cur ^ 1], &smeta[cur ^ 1],
-                       s_scan, &s_a0, &s_a1, &s_prev, &s_hasprev);
+      fuse_classify<K, T>(stp, tn, sbuf[cur ^ 1], smask[cur ^ 1], spre[cur ^ 1], &smeta[cur ^ 1],
+                          s_scan, &s_a0, &s_a1, &s_prev, &s_hasprev);
     const FuseMeta m = smeta[cur];
     if (threadIdx.x == 0) s_bad = 0;
     if (!m.first && threadIdx.x < 32) {
@@ -746,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_diff_merge(Stage* stp) {
     }
     __syncthreads();  // the kept elements, masks and s_excl of the previous tile are visible
     if (s_bad) return;
-    fuse_write<K>(stp, sbuf[cur], smask[cur], spre[cur], m, s_excl);
+    fuse_write<K, T>(stp, sbuf[cur], smask[cur], spre[cur], m, s_excl);
     if (!more) return;
     cur ^= 1;
   }
@@ -811,9 +810,9 @@ __global__ void __launch_bounds__(kThreads) k_fuse_list(Dev* dv) {
 }
 
 // Pass 4 (after k_diff_merge): copy the Full-only tiles to Full'.
-template <typename K>
+template <typename K, int T>
 __global__ void __launch_bounds__(kThreads) k_fuse_copy(Stage* stp) {
-  constexpr int T = FuseTile<K>::T, E = FuseTile<K>::E;
+  constexpr int E = T / kThreads;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   const uint32_t ntiles = stp->ntiles;
@@ -890,11 +889,19 @@ void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><
 template <typename K>
 void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
-void launch_diff_merge(Stage* st, int grid, cudaStream_t s) { k_diff_merge<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_diff_merge(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
+  constexpr int T = FuseTile<K>::T;
+  if (tile == (uint32_t)T / 2) k_diff_merge<K, T / 2><<<grid, kThreads, 0, s>>>(st);
+  else k_diff_merge<K, T><<<grid, kThreads, 0, s>>>(st);
+}
 void launch_fuse_mark(Dev* dv, int grid, cudaStream_t s) { k_fuse_mark<<<grid, kThreads, 0, s>>>(dv); }
 void launch_fuse_list(Dev* dv, int grid, cudaStream_t s) { k_fuse_list<<<grid, kThreads, 0, s>>>(dv); }
 template <typename K>
-void launch_fuse_copy(Stage* st, int grid, cudaStream_t s) { k_fuse_copy<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_fuse_copy(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
+  constexpr int T = FuseTile<K>::T;
+  if (tile == (uint32_t)T / 2) k_fuse_copy<K, T / 2><<<grid, kThreads, 0, s>>>(st);
+  else k_fuse_copy<K, T><<<grid, kThreads, 0, s>>>(st);
+}
 template <typename K>
 void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s) {
   k_partition<K><<<grid, 256, 0, s>>>(consumer, mode, tile);
@@ -919,7 +926,8 @@ int occupancy_sort(int which) {
     case 1: return occupancy_of(k_sort_pass<K>);
     case 2: return occupancy_of(k_unique_diff<K>);
     case 3: return occupancy_of(k_merge<K>);
-    case 4: return occupancy_of(k_diff_merge<K>);
+    case 4: return occupancy_of(k_diff_merge<K, FuseTile<K>::T>);
+    case 5: return occupancy_of(k_diff_merge<K, FuseTile<K>::T / 2>);
     default: return 0;
   }
 }
@@ -929,8 +937,8 @@ int occupancy_sort(int which) {
   template void launch_sort_pass<K>(Stage*, int, cudaStream_t);  \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
-  template void launch_diff_merge<K>(Stage*, int, cudaStream_t); \
-  template void launch_fuse_copy<K>(Stage*, int, cudaStream_t);  \
+  template void launch_diff_merge<K>(Stage*, int, cudaStream_t, uint32_t); \
+  template void launch_fuse_copy<K>(Stage*, int, cudaStream_t, uint32_t);  \
   template void launch_partition<K>(Stage*, int, uint32_t, int, cudaStream_t); \
   template int occupancy_sort<K>(int);
 WG_INST(uint32_t)

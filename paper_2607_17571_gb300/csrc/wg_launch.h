@@ -18,25 +18,29 @@ template <typename K> void launch_sort_hist(Stage* st, int grid, cudaStream_t s)
 template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
-template <typename K> void launch_diff_merge(Stage* st, int grid, cudaStream_t s);
+// tile: merged keys per fused-pass tile, FuseTile<K>::T or half of it
+template <typename K> void launch_diff_merge(Stage* st, int grid, cudaStream_t s, uint32_t tile);
 // mode 0: merge-path splits of a (Full, candidates) / (Full, delta) stage;
 // mode 1: join-slab owner of each emit tile.  `tile` = outputs per tile.
 template <typename K>
 void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s);
-template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge, 4 fused
+template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge, 4 fused,
+                                                      // 5 fused with half tiles
 
 // join and engine control (wg_kern_join.cu)
-template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s);
+// tile: delta tuples per count tile, kTileD or kTileD / 2
+template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s, uint32_t tile);
 template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_tri_probe(Stage* st, int grid, cudaStream_t s);
 void launch_fuse_mark(Dev* dv, int grid, cudaStream_t s);
 void launch_fuse_list(Dev* dv, int grid, cudaStream_t s);
-template <typename K> void launch_fuse_copy(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_fuse_copy(Stage* st, int grid, cudaStream_t s, uint32_t tile);
 template <typename K> void launch_join_emit_hash(Stage* st, int grid, cudaStream_t s);
 template <typename K>
 void launch_hash_build(const K* E, unsigned long long ne, uint32_t w, unsigned long long* T,
                        unsigned long long mask, int grid, cudaStream_t s);
-template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 triangle probe
+template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 triangle probe,
+                                                      // 3 count with half tiles
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);

@@ -46,6 +46,12 @@ class wg_request(Structure):
     _fields_ = [("kind", c_int32), ("reserved0", c_uint32), ("edges", c_uint64), ("opts", wg_opts)]
 
 
+class wg_tune(Structure):
+    _fields_ = [("key_bytes", c_uint32), ("count_tile", c_uint32), ("fuse_tile", c_uint32),
+                ("count_cand", c_uint32 * 2), ("fuse_cand", c_uint32 * 2),
+                ("count_ms", c_double * 2), ("fuse_ms", c_double * 2)]
+
+
 class wg_kernel_stat(Structure):
     _fields_ = [("name", c_char * 32), ("launches", c_uint64), ("total_ms", c_double),
                 ("bytes", c_double)]
@@ -75,6 +81,8 @@ SIGNATURES = {
     "wg_result_copy": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_copy_device": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_iters": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "wg_autotune": (c_int, [c_void_p, c_uint64, c_int, POINTER(wg_tune)]),
+    "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32]),
     "wg_result_profile": (c_int, [c_void_p, c_uint64, POINTER(wg_kernel_stat), c_size_t,
                                   POINTER(c_size_t)]),
     "wg_query_free": (None, [c_void_p, c_uint64]),
@@ -296,6 +304,21 @@ class Context:
         o = _opts(**opts)
         _check(self.lib.wg_tc(self.h, rel.id, byref(o), byref(q)), "wg_tc")
         return Query(self, q.value)
+
+    def autotune(self, rel: Relation, kind: int = WG_TC) -> dict:
+        """wg_autotune: time the compiled tile shapes of the join count and the
+        fused pass on profiled fixpoints of `rel` and keep the faster ones for
+        engines of its key width."""
+        t = wg_tune()
+        _check(self.lib.wg_autotune(self.h, rel.id, kind, byref(t)), "wg_autotune")
+        return dict(key_bytes=t.key_bytes, count_tile=t.count_tile, fuse_tile=t.fuse_tile,
+                    count_cand=list(t.count_cand), fuse_cand=list(t.fuse_cand),
+                    count_ms=[round(x, 3) for x in t.count_ms],
+                    fuse_ms=[round(x, 3) for x in t.fuse_ms])
+
+    def set_tiles(self, key_bytes: int, count_tile: int = 0, fuse_tile: int = 0):
+        """wg_set_tiles: tile shapes for engines of this key width (0 = default)."""
+        _check(self.lib.wg_set_tiles(self.h, key_bytes, count_tile, fuse_tile), "wg_set_tiles")
 
     def triangles(self, rel: Relation) -> int:
         """wg_triangles: number of tuples of triangle(a,b,c) <- edge(a,b),
