@@ -20,6 +20,11 @@ constexpr int kTileC = kThreads * kItemsC;    // 4096 keys per candidate tile
 constexpr int kItemsD = 8;                    // delta tuples per thread, join count
 constexpr int kTileD = kThreads * kItemsD;    // 2048 delta tuples per tile
 constexpr int kTileM = 4096;                  // merge output tile
+// Join-emit tiles count one item per kEmitGroup delta tuples besides the
+// candidates, so a tile holds at most kEmitGroup * kTileC delta tuples
+// however many of their slabs are empty.
+constexpr uint32_t kEmitGroupShift = 3;
+constexpr uint32_t kEmitGroup = 1u << kEmitGroupShift;
 constexpr int kRadix = 256;                   // digit buckets (digits of <= 8 bits)
 constexpr int kMaxPasses = 8;
 constexpr int kFWin = 2048;                   // full-relation keys staged by dedup/diff
@@ -71,6 +76,8 @@ struct Stage {
   unsigned long long* hist;     // radix digit counts [nseg][passes][kRadix]
   unsigned long long* pos;      // join prefix sums (one per delta tuple)
   unsigned long long* splits;   // per-tile start found by a partition kernel (or NULL)
+  unsigned long long* splits2;  // join emit over merged tiles: each tile's first candidate
+                                // (or NULL: a tile is kTileC consecutive candidates)
   unsigned long long* xlen;     // join count: candidates per source x (or NULL)
   uint32_t* tile_seg;           // tile -> segment map (or NULL: binary search)
   unsigned long long hist_n;    // join count: histogram counters to clear
@@ -159,6 +166,7 @@ struct Dev {
   unsigned long long* status_sort;    // lookback words of radix passes
   unsigned long long* hist;           // [n_inst][passes][kRadix]
   unsigned long long* splits;         // tile partitions, as many entries as status_scalar
+  unsigned long long* csplits;        // join emit: first candidate of each merged tile
   unsigned long long* xlen;           // candidates per source vertex (x-grouped sort)
   Seg* segX;                          // one sort segment per source vertex
   uint32_t* tile_seg;                 // tile -> x-segment map of the x-grouped sort

@@ -610,6 +610,7 @@ struct Engine : EngineBase {
     h.status_scalar = (unsigned long long*)st_s.p;
     h.status_sort = (unsigned long long*)st_k.p;
     h.splits = (unsigned long long*)spl.p;
+    h.csplits = spl.p ? h.splits + mix_tiles + 1 : nullptr;
     h.hist = (unsigned long long*)hist.p;
     h.xlen = (unsigned long long*)xlen_b.p;
     h.segX = (Seg*)segx_b.p;
@@ -664,7 +665,7 @@ struct Engine : EngineBase {
       if (tiles > mix_tiles) {
         DBuf ns, np, nm;
         int rc = ns.get(c, tiles * 8);
-        if (rc == WG_OK) rc = np.get(c, (tiles + 1) * 8);
+        if (rc == WG_OK) rc = np.get(c, 2 * (tiles + 1) * 8);  // splits | emit tile starts
         if (rc == WG_OK) rc = nm.get(c, (2 * tiles + 1 + tiles / kThreads + 2) * 4);
         if (rc != WG_OK) {
           ns.release(c); np.release(c); nm.release(c);
@@ -750,7 +751,7 @@ struct Engine : EngineBase {
     if (hash_join) {
       mark(); launch_join_emit_hash<K>(dv->st + S_EMIT, g_emit, s); mark();
     } else {
-      launch_partition<K>(dv->st + S_EMIT, 1, kTileC, c->num_sms * 4, s);
+      launch_partition<K>(dv->st + S_EMIT, 2, kTileC, c->num_sms * 4, s);
       mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
     }
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();

@@ -278,8 +278,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     const K mask = (K)(((K)1 << w) - 1);
     const unsigned long long* P = pos_all + sg.in_off;
     const K* Dq = D + sg.in_off;
-    const unsigned long long o0 = (unsigned long long)(t - sg.tile0) * kTileC;
-    const unsigned long long o1 = min(o0 + kTileC, sg.aux_n);
+    const bool last_tile = t == sg.tile0 + sg.ntiles - 1;
+    unsigned long long o0, o1;  // the tile's candidates: [o0, o1) of the instance
+    if (stp->splits2) {         // merged tiles (at most kTileC candidates each)
+      o0 = stp->splits2[t];
+      o1 = last_tile ? sg.aux_n : stp->splits2[t + 1];
+    } else {
+      o0 = (unsigned long long)(t - sg.tile0) * kTileC;
+      o1 = min(o0 + kTileC, sg.aux_n);
+    }
     const uint32_t nout = (uint32_t)(o1 - o0);
     // delta tuples i0..i1: every slab before i0 ends at or before o0 and
     // every slab after i1 starts after o1
@@ -557,11 +564,11 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
   __shared__ unsigned long long sh[32];
-  __shared__ unsigned long long s_cc, s_ct, s_fc, s_ft;
+  __shared__ unsigned long long s_cc, s_ct, s_fc, s_ft, s_et;
   Ctl& ctl = dv->ctl;
   if (ctl.abort) return;
   const uint32_t N = dv->n_inst;
-  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; s_fc = 0; s_ft = 0; }
+  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; s_fc = 0; s_ft = 0; s_et = 0; }
   __syncthreads();
   for (uint32_t base = 0; base < N; base += kPlanThreads) {
     const uint32_t q = base + threadIdx.x;
@@ -569,22 +576,30 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     Inst* I = valid ? dv->inst + q : nullptr;
     const bool act = valid && I->state == INST_ACTIVE;
     const unsigned long long nc = act ? dv->segD[q].res : 0ull;
+    const unsigned long long nd = act ? I->n_delta : 0ull;
     const unsigned long long nt = (nc + kTileC - 1) / kTileC;
-    unsigned long long totc, tott;
+    // join emit: tiles over merged items (one per group of kEmitGroup delta
+    // tuples, then their slabs' candidates), so long runs of empty slabs are
+    // spread over tiles too
+    const unsigned long long ng = (nd + kEmitGroup - 1) >> kEmitGroupShift;
+    const unsigned long long net = nc ? (nc + ng + kTileC - 1) / kTileC : 0ull;
+    unsigned long long totc, tott, tote;
     const unsigned long long exc = scan1024(nc, sh, &totc);
     const unsigned long long ext = scan1024(nt, sh, &tott);
+    const unsigned long long exe = scan1024(net, sh, &tote);
     if (valid) {
       const unsigned long long c_off = s_cc + exc;
       const uint32_t tile0 = (uint32_t)(s_ct + ext);
       I->n_cand = nc;
       I->c_off = c_off;
       Seg e{};
-      e.in_off = I->d_off; e.n = act ? I->n_delta : 0ull; e.out_off = c_off;
-      e.aux_off = 0; e.aux_n = nc; e.res = 0; e.tile0 = tile0; e.ntiles = (uint32_t)nt;
+      e.in_off = I->d_off; e.n = nd; e.out_off = c_off;
+      e.aux_off = 0; e.aux_n = nc; e.res = 0;
+      e.tile0 = (uint32_t)(s_et + exe); e.ntiles = (uint32_t)net;
       e.inst = q; e.flags = 0;
       dv->segE[q] = e;
       Seg s = e;
-      s.in_off = c_off; s.n = nc; s.aux_n = 0;
+      s.in_off = c_off; s.n = nc; s.aux_n = 0; s.tile0 = tile0; s.ntiles = (uint32_t)nt;
       dv->segS[q] = s;
       Seg u = s;
       u.aux_off = I->f_off; u.aux_n = act ? I->n_full : 0ull;
@@ -608,7 +623,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       if (threadIdx.x == 0) { s_fc += totf; s_ft += totft; }
     }
     __syncthreads();
-    if (threadIdx.x == 0) { s_cc += totc; s_ct += tott; }
+    if (threadIdx.x == 0) { s_cc += totc; s_ct += tott; s_et += tote; }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -626,6 +641,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     base.passes = dv->passes; base.dbits = dv->dbits;
     Stage e = base;
     e.in = dv->D[dv->dphase]; e.out = dv->C[0]; e.segs = dv->segE; e.splits = dv->splits;
+    e.splits2 = dv->csplits; e.ntiles = (uint32_t)s_et;
     e.htab = dv->htab; e.hmask = dv->hmask;
     dv->st[S_EMIT] = e;
     Stage h = base;

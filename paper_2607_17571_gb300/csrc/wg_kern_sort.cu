@@ -857,9 +857,14 @@ __global__ void __launch_bounds__(kThreads) k_fuse_copy(Stage* stp) {
 
 // ------------------------------------------------------------------ tile partitions
 // One thread per tile of the consumer stage: the merge-path split at the
-// tile's first output (mode 0: merge of in/aux, Full first on ties) or the
-// delta tuple whose join slab holds the tile's first candidate (mode 1).  All
-// the binary searches are in flight at once instead of heading every tile.
+// tile's first output (mode 0: merge of in/aux, Full first on ties), the
+// delta tuple whose join slab holds the tile's first candidate (mode 1: tiles
+// of `tile` candidates), or both the first candidate and its slab for join
+// tiles over merged items (mode 2: each group of kEmitGroup delta tuples
+// counts as one item ahead of its slabs' candidates, so a tile of `tile`
+// items holds at most kEmitGroup * `tile` delta tuples however many slabs
+// are empty).  All the binary searches are in flight at once instead of
+// heading every tile.
 template <typename K>
 __global__ void k_partition(Stage* cons, int mode, uint32_t tile) {
   if (*(volatile uint32_t*)&cons->ctl->abort) return;
@@ -873,8 +878,21 @@ __global__ void k_partition(Stage* cons, int mode, uint32_t tile) {
       const K* A = (const K*)cons->in + sg.in_off;
       const K* B = (const K*)cons->aux + sg.aux_off;
       splits[t] = mpath_tie(A, sg.n, B, sg.aux_n, d);
-    } else {
+    } else if (mode == 1) {
       splits[t] = upper_bound_k(cons->pos + sg.in_off, sg.n, d) - 1;
+    } else {
+      // merged item d: the item of group j sits at pos[j * kEmitGroup] + j
+      // (increasing in j); h groups have theirs before d, so d - h
+      // candidates precede it
+      const unsigned long long* P = cons->pos + sg.in_off;
+      unsigned long long lo = 0, hi = (sg.n + kEmitGroup - 1) >> kEmitGroupShift;
+      while (lo < hi) {
+        const unsigned long long m = (lo + hi) >> 1;
+        if (P[m << kEmitGroupShift] + m < d) lo = m + 1; else hi = m;
+      }
+      const unsigned long long c0 = d - lo;
+      cons->splits2[t] = c0;
+      splits[t] = upper_bound_k(P, sg.n, c0) - 1;
     }
   }
 }
