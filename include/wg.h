@@ -179,9 +179,21 @@ int wg_sg(wg_ctx* ctx, wg_rel edges, const wg_opts* opts, wg_query* out);
  * all running queries, and the iteration loop is one CUDA graph.  Queries
  * submitted while earlier ones run join the running set at the next
  * iteration boundary that wg_poll / wg_wait / wg_serve_step reaches
- * (continuous batching).  ids[i] receives the handle of reqs[i].  Admission
- * is by device-memory budget: a request that cannot be admitted now stays
- * queued (state WG_PENDING).  Errors: WG_E_INVAL. */
+ * (continuous batching).  ids[i] receives the handle of reqs[i].  Queries
+ * are grouped into batch engines by key width and size class; a request
+ * over 65,536 edges instead runs on a single-query engine (one at a time, on
+ * the context stream) beside the batch engines -- one such fixpoint already
+ * fills the GPU.  Admission is by device-memory budget: a request that
+ * cannot be admitted now stays queued (state WG_PENDING).  When pools cannot
+ * grow within the budget, idle engines' pools are released first, then the
+ * most recently admitted query of the engine is requeued (it restarts
+ * later); a query left alone in its engine that still cannot grow pauses
+ * with its state until the other engines drain (nothing else is admitted
+ * meanwhile) and resumes with the whole budget.  Only a query that does not
+ * fit with the whole budget fails, with WG_E_BUDGET.  The results do not
+ * depend on any of this (each query's result equals its result alone).
+ * Errors: WG_E_INVAL; WG_E_BUDGET / WG_E_NOMEM when a new engine's first
+ * pools do not fit. */
 int wg_submit(wg_ctx* ctx, const wg_request* reqs, size_t n, wg_query* ids);
 /* Advance the batch engine by at most `iters` iterations (admitting queued
  * requests and retiring finished ones) and return without waiting for the
