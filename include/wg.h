@@ -257,6 +257,15 @@ typedef struct wg_tune {
 int wg_autotune(wg_ctx* ctx, wg_rel edges, int kind, wg_tune* out);
 int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_tile);
 
+/* ---- self-test of the bounded device wait --------------------------------
+ * wg_selftest_wait_timeout: run the wait of the decoupled lookback (the one
+ * every scan stage uses) against a predecessor that never publishes its
+ * count.  The wait gives up after its poll limit (a second or a few),
+ * records the timeout and the kernel returns, so the context stays usable.
+ * Returns WG_E_DEVICE_TIMEOUT when that happened (the expected outcome),
+ * WG_OK if the wait completed, WG_E_NOMEM / WG_E_BUDGET / WG_E_CUDA. */
+int wg_selftest_wait_timeout(wg_ctx* ctx);
+
 /* ---- sorted-array primitives (the stages of one iteration) ---------------
  * Device buffers of packed keys, key_bytes = 4 (uint32) or 8 (uint64).  They
  * run on the context stream, use context scratch, and synchronise the stream

@@ -2133,6 +2133,31 @@ int wg_result_profile(wg_ctx* c, wg_query id, wg_kernel_stat* stats, size_t cap,
   return WG_OK;
 }
 
+int wg_selftest_wait_timeout(wg_ctx* c) {
+  if (!c) return set_err(WG_E_INVAL, "ctx is NULL");
+  DBuf b;  // Ctl | status words | result
+  const size_t ctl_bytes = (sizeof(Ctl) + 63) / 64 * 64;
+  TRY(b.get(c, ctl_bytes + 64));
+  char* base = (char*)b.p;
+  Ctl* ctl = (Ctl*)base;
+  unsigned long long* status = (unsigned long long*)(base + ctl_bytes);
+  int rc = WG_OK;
+  if (cudaMemsetAsync(base, 0, ctl_bytes + 64, c->stream) != cudaSuccess) {
+    rc = set_err(WG_E_CUDA, "self-test clear");
+  } else {
+    launch_selftest_wait(status, ctl, status + 4, c->stream);
+    Ctl h{};
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = set_err(WG_E_CUDA, "self-test launch");
+    else if (h.error == DEV_TIMEOUT)
+      rc = set_err(WG_E_DEVICE_TIMEOUT, "the bounded device wait gave up (self-test)");
+  }
+  b.release(c);
+  return rc;
+}
+
 int wg_set_tiles(wg_ctx* c, int key_bytes, uint32_t count_tile, uint32_t fuse_tile) {
   if (!c || (key_bytes != 4 && key_bytes != 8)) return set_err(WG_E_INVAL, "bad argument");
   const uint32_t T = key_bytes == 4 ? FuseTile<uint32_t>::T : FuseTile<unsigned long long>::T;

@@ -971,6 +971,19 @@ __global__ void k_result_map(const K* F, unsigned long long n, uint32_t w, const
 }
 
 // ------------------------------------------------------------------ launchers
+// Self-test of the bounded device wait: one warp looks back, as every scan
+// stage does, for a predecessor tile whose status word is never published
+// (epoch 1 is never written).  The wait gives up after kSpinLimit polls,
+// records DEV_TIMEOUT in the control block and the kernel returns.
+__global__ void k_selftest_wait(const unsigned long long* status, Ctl* ctl, unsigned long long* out) {
+  const unsigned long long e = lookback_scalar(status, 1u, 0u, 1u, ctl);
+  if (threadIdx.x == 0) *out = e;
+}
+void launch_selftest_wait(const unsigned long long* status, Ctl* ctl, unsigned long long* out,
+                          cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(status, ctl, out);
+}
+
 template <typename K>
 void launch_join_count(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
   if (tile == (uint32_t)kTileD / 2) k_join_count<K, kItemsD / 2><<<grid, kThreads, 0, s>>>(st);

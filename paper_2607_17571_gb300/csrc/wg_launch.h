@@ -41,6 +41,10 @@ void launch_hash_build(const K* E, unsigned long long ne, uint32_t w, unsigned l
                        unsigned long long mask, int grid, cudaStream_t s);
 template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 triangle probe,
                                                       // 3 count with half tiles
+// one warp waiting on a status word that is never published (bounded wait self-test)
+struct Ctl;
+void launch_selftest_wait(const unsigned long long* status, Ctl* ctl, unsigned long long* out,
+                          cudaStream_t s);
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);

@@ -82,6 +82,7 @@ SIGNATURES = {
     "wg_result_copy_device": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_iters": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_autotune": (c_int, [c_void_p, c_uint64, c_int, POINTER(wg_tune)]),
+    "wg_selftest_wait_timeout": (c_int, [c_void_p]),
     "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32]),
     "wg_result_profile": (c_int, [c_void_p, c_uint64, POINTER(wg_kernel_stat), c_size_t,
                                   POINTER(c_size_t)]),
@@ -315,6 +316,11 @@ class Context:
                     count_cand=list(t.count_cand), fuse_cand=list(t.fuse_cand),
                     count_ms=[round(x, 3) for x in t.count_ms],
                     fuse_ms=[round(x, 3) for x in t.fuse_ms])
+
+    def selftest_wait_timeout(self) -> int:
+        """wg_selftest_wait_timeout: the return code (WG_E_DEVICE_TIMEOUT is
+        the expected outcome: the bounded device wait gave up)."""
+        return int(self.lib.wg_selftest_wait_timeout(self.h))
 
     def set_tiles(self, key_bytes: int, count_tile: int = 0, fuse_tile: int = 0):
         """wg_set_tiles: tile shapes for engines of this key width (0 = default)."""
