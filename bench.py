@@ -558,15 +558,17 @@ def run_triangles(args):
 
 
 def run_ablations(args):
-    """The paper's engineering ablations (Sec. Evaluation)
-    on one TC workload: each variant is the same fixpoint with one design
+    """The paper's engineering ablations (Sec. Evaluation: fused deduplication,
+    the asynchronous loop, adaptive radix width, ping-pong buffers) on one TC
+    workload: each variant is the same fixpoint with one design
     choice reverted, timed like the main bench (CUDA events, L2 flushed), and
     every variant's result is checked against the default's.  Variants:
     default (device loop, fused dedup/diff/merge, adaptive width, ping-pong),
     separate stages, host-driven loop (one launch per kernel, one host sync per
     iteration), full-width radix sort, copy-back instead of ping-pong, and a
-    linear-probing hash join in place of the sorted-array join (SURVEY NEXT
-    row 2; its table is built once per relation, outside the timed steps)."""
+    linear-probing hash join in place of the sorted-array join (Sec. "Data
+    Skew in Hash-Based Join"; its table is built once per relation, outside
+    the timed steps)."""
     import torch
 
     from paper_2607_17571_gb300 import inputs as I
