@@ -260,6 +260,7 @@ def run_ours(args):
                 traffic = float(parts[2])
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom["name"],
+            "frac_of_nominal_7900": round(achieved / 7900.0, 4),  # nominal HBM3e, context
             "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
             else "fallback 6.8 TB/s",
             "per_kernel": [{"name": p["name"], "launches": p["launches"],
