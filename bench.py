@@ -310,7 +310,8 @@ def run_ours(args):
                            "closure_tuples": int(st.n_tuples), "iterations": int(iters),
                            "candidates": int(st.candidates), "edges": n,
                            "vertices": info["n_vertices"], "field_bits": info["field_bits"],
-                           "l2": "flushed between steps (256 MB write); working set > L2",
+                           "l2": "flushed between steps (256 MB write); working set "
+                                 + ("> L2" if 2 * kb * int(st.n_tuples) > (129 << 20) else "fits in L2"),
                            "parallelism": f"replicas x{world}", "regrows_timed": regrows,
                            "tiles": tiles or "compiled defaults"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
