@@ -195,7 +195,8 @@ def run_ours(args):
     rel = ctx.load_device(src_t.data_ptr(), dst_t.data_ptr(), n)
     info = rel.info()
     run0 = ctx.tc if wl["kind"] == "tc" else ctx.sg
-    loop = wg.WG_LOOP_HOST if args.loop == "host" else wg.WG_LOOP_DEVICE
+    loop = {"host": wg.WG_LOOP_HOST, "staged": wg.WG_LOOP_HOST_STAGED}.get(args.loop,
+                                                                          wg.WG_LOOP_DEVICE)
 
     def run(r, **kw):
         return run0(r, loop=loop, **kw)
@@ -567,7 +568,9 @@ def run_ablations(args):
     every variant's result is checked against the default's.  Variants:
     default (device loop, fused dedup/diff/merge, adaptive width, ping-pong),
     separate stages, host-driven loop (one launch per kernel, one host sync per
-    iteration), full-width radix sort, copy-back instead of ping-pong, and a
+    iteration), host-driven loop with a readback and sync after every stage
+    (the paper's stage-wise synchronisation), full-width radix sort, copy-back
+    instead of ping-pong, and a
     linear-probing hash join in place of the sorted-array join (Sec. "Data
     Skew in Hash-Based Join"; its table is built once per relation, outside
     the timed steps)."""
@@ -581,7 +584,9 @@ def run_ablations(args):
     g = I.workload(name)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
     variants = [("default", {}), ("separate_stages", dict(separate_stages=True)),
-                ("host_loop", dict(loop=wg.WG_LOOP_HOST)), ("full_width", dict(full_width=True)),
+                ("host_loop", dict(loop=wg.WG_LOOP_HOST)),
+                ("host_staged", dict(loop=wg.WG_LOOP_HOST_STAGED)),
+                ("full_width", dict(full_width=True)),
                 ("copy_back", dict(copy_back=True)), ("hash_join", dict(hash_join=True))]
     ref, out = None, []
     clocks = Clocks(0)
@@ -797,7 +802,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-step-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--loop", default="device", choices=["device", "host"],
+    ap.add_argument("--loop", default="device", choices=["device", "host", "staged"],
                     help="host: one launch per kernel and a host sync per iteration (profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

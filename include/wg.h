@@ -63,9 +63,14 @@ enum wg_kind { WG_TC = 0, WG_SG = 1 };
 enum wg_loop {
   WG_LOOP_DEVICE = 0, /* one CUDA graph per run: a conditional WHILE node holds the
                          iteration; no host synchronisation between iterations */
-  WG_LOOP_HOST = 1    /* the host launches each iteration and reads the delta size
-                         back once per iteration (the host-driven loop of Sec.
-                         Motivation, "Stage-Wise Synchronization"), for comparison */
+  WG_LOOP_HOST = 1,   /* the host launches each iteration and reads the delta size
+                         back once per iteration (one sync per iteration), for
+                         comparison */
+  WG_LOOP_HOST_STAGED = 2 /* the host launches every stage and reads the control block
+                         back after each one, waiting for it (about 10-14 syncs per
+                         iteration: the per-stage readback of the host-driven
+                         pipelines of Sec. Motivation, "Stage-Wise Synchronization"),
+                         for comparison.  Single queries (wg_tc / wg_sg) only */
 };
 
 /* wg_opts.flags */
@@ -262,8 +267,11 @@ int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_
  * every scan stage uses) against a predecessor that never publishes its
  * count.  The wait gives up after its poll limit (a second or a few),
  * records the timeout and the kernel returns, so the context stays usable.
- * Returns WG_E_DEVICE_TIMEOUT when that happened (the expected outcome),
- * WG_OK if the wait completed, WG_E_NOMEM / WG_E_BUDGET / WG_E_CUDA. */
+ * The same wait then runs once in the control block of the allocation-free
+ * sort (wg_sort_keys_noalloc), whose next check (a call with n = 0) reports
+ * it; run it while no allocation-free sort is in flight.
+ * Returns WG_E_DEVICE_TIMEOUT when the context's wait gave up (the expected
+ * outcome), WG_OK if the wait completed, WG_E_NOMEM / WG_E_BUDGET / WG_E_CUDA. */
 int wg_selftest_wait_timeout(wg_ctx* ctx);
 
 /* ---- sorted-array primitives (the stages of one iteration) ---------------
@@ -310,11 +318,17 @@ int wg_triangles(wg_ctx* ctx, wg_rel edges, uint64_t* count);
  * the same sort as wg_sort_keys (LSD radix sort of n keys on their low `bits`
  * bits, in place; key_bytes = 4 or 8; higher bits must be zero) but takes
  * no context and allocates nothing: its scratch (stage records, digit
- * histograms, lookback words and the ping-pong key buffer, about 8.6 MB) is one
- * fixed static device array that every GPU loading the library holds until the
- * process exits.
+ * histograms, lookback words and the ping-pong key buffer) is one fixed static
+ * device array of WG_NOALLOC_SCRATCH_BYTES (8,934,912 bytes, 8.5 MiB) that every
+ * GPU loading the library holds until the process exits.
  *  - n <= WG_NOALLOC_MAX_KEYS (1,048,576); a larger n returns WG_E_CAPACITY and
  *    touches nothing.
+ *  - n = 0 (d_keys may be NULL) sorts nothing: it is the failure check.  It
+ *    synchronises `cuda_stream` and returns WG_E_DEVICE_TIMEOUT if a call on this
+ *    device gave up a bounded device wait since the last check (that call's keys
+ *    are unspecified), else WG_OK, and clears the record.  Every sort call
+ *    returns before its kernels run, so only this check can report such a
+ *    failure.
  *  - Asynchronous on `cuda_stream` (a cudaStream_t; NULL = the legacy default
  *    stream) of the current device; the caller synchronises.
  *  - All calls share the scratch array, which keeps the previous call's
@@ -323,8 +337,9 @@ int wg_triangles(wg_ctx* ctx, wg_rel edges, uint64_t* count);
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress): make that first call before any stream capture.
  * Errors: WG_E_INVAL (NULL keys with n > 0, bad key_bytes or bits),
- * WG_E_CAPACITY, WG_E_CUDA. */
+ * WG_E_CAPACITY, WG_E_CUDA, WG_E_DEVICE_TIMEOUT (the check, n = 0). */
 #define WG_NOALLOC_MAX_KEYS 1048576u
+#define WG_NOALLOC_SCRATCH_BYTES 8934912u
 int wg_sort_keys_noalloc(void* d_keys, size_t n, int key_bytes, uint32_t bits, void* cuda_stream);
 
 #ifdef __cplusplus

@@ -298,6 +298,9 @@ static int prim_sort(wg_ctx* c, K* keys, size_t n, uint32_t bits) {
   sg.n = n; sg.tile0 = 0; sg.ntiles = ntiles;
   TRY(prim_seg(c, sg));
   CK(cudaMemsetAsync(c->s_hist, 0, sizeof(unsigned long long) * passes * kRadix, c->stream));
+  // a wait that gave up in an earlier primitive must not make these passes
+  // skip their work: the control block starts clear (the caller reads it after)
+  CK(cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream));
   Stage h = prim_stage(c, ntiles);
   h.in = keys; h.passes = passes; h.dbits = dbits;
   TRY(prim_put(c, S_HIST, h));
@@ -310,7 +313,7 @@ static int prim_sort(wg_ctx* c, K* keys, size_t n, uint32_t bits) {
   }
   launch_sort_hist<K>(c->s_stage + S_HIST, grid_of(c, occupancy_sort<K>(0)), c->stream);
   for (uint32_t p = 0; p < passes; ++p)
-    launch_sort_pass<K>(c->s_stage + S_PASS0 + p, grid_of(c, occupancy_sort<K>(1)), c->stream);
+    launch_sort_pass<K>(c->s_stage + S_PASS0 + p, grid_of(c, occupancy_sort<K>(1)), c->stream, dbits);
   CK(cudaGetLastError());
   if (passes & 1) CK(cudaMemcpyAsync(keys, c->s_tmp, n * sizeof(K), cudaMemcpyDeviceToDevice, c->stream));
   return WG_OK;
@@ -733,8 +736,12 @@ struct Engine : EngineBase {
   // The kernels of one semi-naive iteration (Secs. Per-Iteration Pipeline and
   // Fused Deduplication): join count -> plan -> join emit -> radix histogram ->
   // radix passes -> fused dedup + set difference -> plan (termination) -> merge.
-  void launch_iteration(cudaStream_t s, std::vector<KStat>* prof = nullptr,
-                        std::vector<cudaEvent_t>* evs = nullptr) {
+  // staged: after every stage the host reads the control block back and
+  // waits for it (the per-stage readback of the host-driven pipelines of Sec.
+  // Motivation, "Stage-Wise Synchronization"); an overflow seen there stops
+  // the iteration's remaining launches.  Returns the host syncs issued.
+  uint32_t launch_iteration(cudaStream_t s, std::vector<KStat>* prof = nullptr,
+                            std::vector<cudaEvent_t>* evs = nullptr, bool staged = false) {
     auto mark = [&]() {
       if (evs) {
         cudaEvent_t e;
@@ -744,22 +751,44 @@ struct Engine : EngineBase {
       }
     };
     (void)prof;
+    uint32_t syncs = 0;
+    bool stop = false;
+    auto stage = [&]() {  // one stage's readback; true = the iteration goes on
+      if (!staged || stop) return !stop;
+      Ctl back{};
+      cudaMemcpyAsync(&back, &dv->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      ++syncs;
+      stop = back.abort != 0;
+      return !stop;
+    };
     launch_plan_delta(dv, s);
+    if (!stage()) return syncs;
     mark(); launch_join_count<K>(dv->st + S_COUNT, g_count, s, count_tile_); mark();
+    if (!stage()) return syncs;
     launch_plan_cand(dv, s);
-    if (xseg) launch_xseg_build(dv, s);
+    if (!stage()) return syncs;
+    if (xseg) {
+      launch_xseg_build(dv, s);
+      if (!stage()) return syncs;
+    }
     if (hash_join) {
       mark(); launch_join_emit_hash<K>(dv->st + S_EMIT, g_emit, s); mark();
     } else {
       launch_partition<K>(dv->st + S_EMIT, 2, kTileC, c->num_sms * 4, s);
+      if (!stage()) return syncs;
       mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
     }
+    if (!stage()) return syncs;
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
+    if (!stage()) return syncs;
     for (uint32_t p = 0; p < passes; ++p) {
-      mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s); mark();
+      mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits); mark();
+      if (!stage()) return syncs;
     }
     if (fuse) {
       launch_partition<K>(dv->st + S_FUSE, 0, fuse_tile_, c->num_sms * 4, s);
+      if (!stage()) return syncs;
       // mixed tiles through the fused kernel, Full-only tiles by a plain copy
       // (timed together as the fused stage)
       mark();
@@ -768,14 +797,20 @@ struct Engine : EngineBase {
       launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s, fuse_tile_);
       launch_fuse_copy<K>(dv->st + S_FUSE, c->num_sms * 8, s, fuse_tile_);
       mark();
+      if (!stage()) return syncs;
       launch_plan_post(dv, s);
+      if (!stage()) return syncs;
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
     } else {
       mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
+      if (!stage()) return syncs;
       launch_plan_merge(dv, s);
+      if (!stage()) return syncs;
       launch_partition<K>(dv->st + S_MERGE, 0, kTileM, c->num_sms * 4, s);
+      if (!stage()) return syncs;
       mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();
     }
+    return syncs;
   }
 
   int capture() {
@@ -846,18 +881,24 @@ struct Engine : EngineBase {
     return WG_OK;
   }
 
-  // Launch the loop (graph, or one host round trip per iteration).
-  int launch(uint32_t budget, bool host_loop) {
+  // Launch the loop: the graph (WG_LOOP_DEVICE), one host round trip per
+  // iteration (WG_LOOP_HOST) or one per stage (WG_LOOP_HOST_STAGED).
+  uint64_t host_syncs = 0;
+  int launch(uint32_t budget, int mode) {
     TRY(put_passes());
-    if (host_loop) {
+    if (mode != WG_LOOP_DEVICE) {
       TRY(put_ctl(budget, false));
       for (;;) {
-        launch_iteration(st);
+        host_syncs += launch_iteration(st, nullptr, nullptr, mode == WG_LOOP_HOST_STAGED);
         launches_issued += kernels_per_iter();
-        uint32_t cont = 0;
-        CK(cudaMemcpyAsync(&cont, &dv->ctl.cont, 4, cudaMemcpyDeviceToHost, st));
+        uint32_t flags[2] = {0, 0};  // cont, abort
+        CK(cudaMemcpyAsync(&flags[0], &dv->ctl.cont, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&flags[1], &dv->ctl.abort, 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));  // the per-iteration host sync
-        if (!cont) break;
+        ++host_syncs;
+        // an overflow stops the loop (a staged iteration stops before the
+        // plan kernel that would clear the continue flag)
+        if (!flags[0] || flags[1]) break;
       }
       CK(cudaGetLastError());
     } else {
@@ -1004,6 +1045,12 @@ static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, ui
 }
 
 // ------------------------------------------------------------------ single queries
+// The loop a single query runs: a profiled run is host-driven (one event
+// pair per kernel), otherwise the requested one.
+static int loop_mode(const Query* q) {
+  return q->opts.profile && q->opts.loop == WG_LOOP_DEVICE ? (int)WG_LOOP_HOST : (int)q->opts.loop;
+}
+
 template <typename K>
 static int single_start(wg_ctx* c, Query* q) {
   auto* E = static_cast<Engine<K>*>(q->eng);
@@ -1018,7 +1065,6 @@ static int single_start(wg_ctx* c, Query* q) {
   TRY(E->admit(0, Rl, q->kind, q->opts.max_iters, 0));
   TRY(E->init_deltas(0, 1));
   CK(cudaEventRecord(q->ev0, c->stream));
-  const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
   if (q->opts.profile) {
     // profiled run: host loop with CUDA events around every stage kernel
     for (;;) {
@@ -1076,7 +1122,7 @@ static int single_start(wg_ctx* c, Query* q) {
     q->state = WG_RUNNING;
     return WG_OK;
   }
-  TRY(E->launch(0xFFFFFFFFu, host_loop));
+  TRY(E->launch(0xFFFFFFFFu, loop_mode(q)));
   q->state = WG_RUNNING;
   return WG_OK;
 }
@@ -1108,8 +1154,7 @@ static int single_progress(wg_ctx* c, Query* q, bool block, bool pause_on_budget
       return rc;
     }
     if (again) {
-      const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
-      TRY(E->launch(0xFFFFFFFFu, host_loop));
+      TRY(E->launch(0xFFFFFFFFu, loop_mode(q)));
       continue;
     }
     const Inst& I = E->hi[0];
@@ -1496,7 +1541,7 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch, boo
   bool any = false;
   for (const Inst& I : E->hi) any |= I.state == INST_ACTIVE;
   if (any) {
-    TRY(E->launch(iters, false));
+    TRY(E->launch(iters, WG_LOOP_DEVICE));
     *progressed = true;
   }
   return WG_OK;
@@ -1750,6 +1795,7 @@ void wg_relation_free(wg_ctx* c, wg_rel r) {
 }
 
 static int make_query(wg_ctx* c, int kind, wg_rel edges, const wg_opts* opts, Query** out) {
+  if (opts && opts->loop > WG_LOOP_HOST_STAGED) return set_err(WG_E_INVAL, "unknown loop mode");
   auto it = c->rels.find(edges);
   if (it == c->rels.end()) return set_err(WG_E_INVAL, "no such relation");
   auto q = std::make_unique<Query>();
@@ -1871,8 +1917,7 @@ static int solo_resume(wg_ctx* c, Query* q) {
   }
   TRY(rc);
   q->solo_wait = false;
-  const bool host_loop = q->opts.loop == WG_LOOP_HOST || q->opts.profile;
-  return E->launch(0xFFFFFFFFu, host_loop);
+  return E->launch(0xFFFFFFFFu, loop_mode(q));
 }
 
 static void solo_requeue(wg_ctx* c, Query* q) {
@@ -2155,6 +2200,12 @@ int wg_selftest_wait_timeout(wg_ctx* c) {
       rc = set_err(WG_E_DEVICE_TIMEOUT, "the bounded device wait gave up (self-test)");
   }
   b.release(c);
+  if (rc == WG_E_DEVICE_TIMEOUT) {
+    // the allocation-free sort's control block records the same timeout
+    const int r2 = noalloc_selftest_wait(c->stream);
+    if (r2 != WG_OK) return r2;
+    set_err(WG_E_DEVICE_TIMEOUT, "the bounded device wait gave up (self-test)");
+  }
   return rc;
 }
 
@@ -2244,7 +2295,15 @@ int wg_sort_keys(wg_ctx* c, void* d_keys, size_t n, int kb, uint32_t bits) {
   int rc = kb == 4 ? prim_sort<uint32_t>(c, (uint32_t*)d_keys, n, bits)
                    : prim_sort<unsigned long long>(c, (unsigned long long*)d_keys, n, bits);
   if (rc != WG_OK) return rc;
+  if (n <= 1) return WG_OK;  // nothing was launched
+  Ctl ctl{};
+  CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (ctl.error) {  // a pass gave up: the keys are unspecified
+    CK(cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return set_err(WG_E_DEVICE_TIMEOUT, "a radix pass's lookback wait gave up");
+  }
   return WG_OK;
 }
 

@@ -26,201 +26,290 @@ __device__ __forceinline__ uint32_t digit(K k, uint32_t shift, uint32_t mask) {
   return (uint32_t)(k >> shift) & mask;
 }
 
+// Digit extraction of one pass.  Whole-byte digits (8-bit digits at a shift
+// that is a multiple of 8: every pass of a 16- or 32-bit sort) take one byte
+// permute of the 32-bit word that holds them.
+struct Digit {
+  uint32_t shift, mask, sel, hi;  // sel: byte selector of a whole-byte digit; hi: word
+  __device__ __forceinline__ Digit(uint32_t sh, uint32_t bits)
+      : shift(sh), mask((1u << bits) - 1u), sel(0x4440u | ((sh & 31u) >> 3)), hi(sh >= 32) {}
+  template <bool kByte, typename K>
+  __device__ __forceinline__ uint32_t operator()(K k) const {
+    if constexpr (kByte) {
+      const uint32_t w = sizeof(K) == 4 ? (uint32_t)k : (uint32_t)(hi ? (k >> 32) : k);
+      return __byte_perm(w, 0u, sel);
+    } else {
+      return (uint32_t)(k >> shift) & mask;
+    }
+  }
+};
+
 // ------------------------------------------------------------------ histogram
+// Counts of the FIRST pass's digit per segment: one read of the keys.  Each
+// radix pass counts the next pass's digits while it ranks its tile, so the
+// later digits need no read of their own.
+template <typename K, bool kByte>
+__device__ __forceinline__ void hist_tile(const K* p, uint32_t n, const Digit& dg, uint32_t* sh) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t wbase = warp * 32 * kItemsC + lane;
+  K key[kItemsC];
+#pragma unroll
+  for (int i = 0; i < kItemsC; ++i) {
+    const uint32_t idx = wbase + i * 32;
+    key[i] = idx < n ? p[idx] : (K)0;
+  }
+#pragma unroll
+  for (int i = 0; i < kItemsC; ++i)
+    if (wbase + i * 32 < n) atomicAdd(&sh[dg.operator()<kByte>(key[i])], 1u);
+}
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
-  __shared__ K sk[Padded<kTileC>::n];
-  __shared__ uint32_t sh[kMaxPasses * kRadix];
-  __shared__ uint32_t s_t;
+  __shared__ uint32_t sh[kRadix];
+  __shared__ const K* s_p;
+  __shared__ unsigned long long* s_row;
+  __shared__ uint32_t s_t, s_n;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   const K* in = (const K*)stp->in;
-  const uint32_t passes = stp->passes, dbits = stp->dbits, nseg = stp->nseg;
-  const uint32_t ntiles = stp->ntiles, mask = (1u << dbits) - 1u;
+  const uint32_t passes = stp->passes, nseg = stp->nseg, ntiles = stp->ntiles;
+  const Digit dg(0, stp->dbits);
+  const bool byte = stp->dbits == 8;
   for (;;) {
-    const uint32_t t = claim_tile(stp, &s_t);
-    if (t >= ntiles) return;
-    const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
-    const Seg sg = stp->segs[k];
-    const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
-    const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
-    const K* p = in + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
-    tile_to_smem<kItemsC>(sk, p, n, Pad32());
-    __syncthreads();
-    // the lowest digit of the candidates is close to random: one shared
-    // atomic per key, read in striped order (conflict-free)
-#pragma unroll
-    for (int e = 0; e < kItemsC; ++e) {
-      const uint32_t i = threadIdx.x + e * kThreads;
-      if (i < n) atomicAdd(&sh[digit(sk[pad32(i)], 0, mask)], 1u);
-    }
-    // higher digits come in runs (sorted adjacency lists, one source per
-    // slab): blocked order keeps equal neighbours together, one atomic per run
-    const uint32_t b = threadIdx.x * kItemsC;
-    for (uint32_t ps = 1; ps < passes; ++ps) {
-      const uint32_t shift = ps * dbits;
-      uint32_t prev = 0xFFFFFFFFu, run = 0;
-#pragma unroll
-      for (int i = 0; i < kItemsC; ++i) {
-        if (b + i < n) {
-          const uint32_t d = digit(sk[pad32(b + i)], shift, mask);
-          if (d == prev) {
-            ++run;
-          } else {
-            if (run) atomicAdd(&sh[ps * kRadix + prev], run);
-            prev = d;
-            run = 1;
-          }
-        }
+    __syncthreads();  // the previous tile's counts are flushed
+    if (threadIdx.x == 0) {
+      const uint32_t t = atomicAdd(&stp->ctr, 1u);
+      s_t = t;
+      if (t < ntiles) {
+        const uint32_t k = find_seg(stp->segs, nseg, t, stp->tile_seg);
+        const Seg& sg = stp->segs[k];
+        const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+        s_p = in + sg.in_off + start;
+        s_n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+        s_row = stp->hist + (unsigned long long)k * passes * kRadix;
       }
-      if (run) atomicAdd(&sh[ps * kRadix + prev], run);
     }
+    sh[threadIdx.x] = 0;
     __syncthreads();
-    unsigned long long* gh = stp->hist + (unsigned long long)k * passes * kRadix;
-    for (uint32_t i = threadIdx.x; i < passes * kRadix; i += kThreads)
-      if (sh[i]) atomicAdd(&gh[i], (unsigned long long)sh[i]);
+    if (s_t >= ntiles) return;
+    if (byte) hist_tile<K, true>(s_p, s_n, dg, sh);
+    else hist_tile<K, false>(s_p, s_n, dg, sh);
+    __syncthreads();
+    const uint32_t c = sh[threadIdx.x];
+    if (c) atomicAdd(&s_row[threadIdx.x], (unsigned long long)c);
   }
 }
 
 // ------------------------------------------------------------------ one radix pass
 constexpr int kLookW = 8;  // lookback words a digit thread loads at once
 
+// Tile metadata, written by thread 0 when the tile is claimed.
 struct PassMeta {
-  uint32_t t, k, n, first;  // tile, segment, keys in the tile, first tile of its segment
+  unsigned long long in;    // the tile's first key in the input pool
+  unsigned long long out;   // the segment's first key in the output pool
+  unsigned long long* nrow; // the segment's histogram row of the next pass (or NULL)
+  uint32_t t, k, n, tile0;  // tile, segment, keys in the tile, first tile of the segment
+  uint32_t first, rel32;    // first tile of its segment; segment of < 2^32 keys
 };
 
 template <typename K>
 struct PassSmem {
   static constexpr int kSlots = sizeof(K) == 4 ? 2 : 1;  // two tiles in flight fit for 32-bit keys
   K sk[kSlots][kTileC];                 // a ranked tile in digit order
-  uint32_t whist[kWarps][kRadix];       // per-warp counts -> prefix over warps
-  uint32_t tstart[kSlots][kRadix];      // digit start inside the tile
-  uint32_t tcnt[kSlots][kRadix];        // digit count of the tile
-  union {                               // global base of each digit minus tstart:
-    unsigned long long gdst[kRadix];    //   absolute, or
-    uint32_t gdst32[kRadix];            //   from the segment's start (segments < 2^32 keys)
+  // rank phase: per-warp digit counters, then the tile-local start of
+  // (warp, digit): the digit's start in the tile plus the earlier warps' keys
+  uint32_t wbase[kWarps][kRadix];
+  // write phase: global base of each digit minus its start in the tile:
+  // absolute, or from the segment's start (segments < 2^32 keys).  Not shared
+  // with wbase: the next tile's ranking starts right after the stores of the
+  // tile written, with no barrier in between.
+  union {
+    unsigned long long gdst[kRadix];
+    uint32_t gdst32[kRadix];
   };
+  uint32_t nxt[kRadix];                    // next pass's digit counts of the tile being ranked
+  uint32_t tstart[kSlots][kRadix + 1];     // digit starts inside the tile; [kRadix] = tile size
+  unsigned long long hstart[kSlots][kRadix];  // digit starts inside the segment
   unsigned long long s_scan[kWarps];
-  PassMeta meta[kSlots];
+  PassMeta meta[kSlots + 1];  // tiles in flight: written next, ranked, being loaded
   uint32_t s_t, s_bad;
 };
 
-// Rank tile t into slot `sl`: load, rank every key within its digit, publish
-// the tile's digit counts and place the keys in digit order in shared memory.
-// Nothing here waits for another tile.  kFull: the tile holds kTileC keys
-// (every bounds test folds away).
-template <typename K, bool kFull>
-__device__ __forceinline__ void pass_rank_tile(Stage* stp, PassSmem<K>& S, uint32_t t, int sl,
-                                               uint32_t k, const Seg& sg, uint32_t n_tile) {
-  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u, pass = stp->pass;
+// Claim the next tile and (thread 0) describe it in meta[mi].
+template <typename K>
+__device__ __forceinline__ uint32_t pass_claim(Stage* stp, PassSmem<K>& S, int mi) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t t = atomicAdd(&stp->ctr, 1u);
+    S.s_t = t;
+    if (t < stp->ntiles) {
+      const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
+      const Seg& sg = stp->segs[k];
+      const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
+      PassMeta m;
+      m.in = sg.in_off + start;
+      m.out = sg.out_off;
+      m.nrow = stp->pass + 1 < stp->passes
+                   ? stp->hist + ((unsigned long long)k * stp->passes + stp->pass + 1) * kRadix
+                   : nullptr;
+      m.t = t; m.k = k; m.tile0 = sg.tile0;
+      m.n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
+      m.first = t == sg.tile0;
+      m.rel32 = sg.n <= 0xFFFFFFFFull;
+      S.meta[mi] = m;
+    }
+  }
+  __syncthreads();
+  return S.s_t;
+}
+
+// Issue the loads of tile meta[mi] into registers (warp-striped: warp w owns
+// keys [w*32*kItemsC, (w+1)*32*kItemsC)).  Nothing waits for them here: the
+// caller writes out the previous tile while they are in flight.
+template <typename K>
+__device__ __forceinline__ void pass_load(const Stage* stp, const PassMeta& m, K (&key)[kItemsC]) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t wb = warp * 32 * kItemsC + lane;
+  const K* p = (const K*)stp->in + m.in;
+  if (m.n == (uint32_t)kTileC) {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) key[i] = p[wb + i * 32];
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const uint32_t idx = wb + i * 32;
+      key[i] = idx < m.n ? p[idx] : (K)0;
+    }
+  }
+}
+
+// Rank tile meta[mi] (its keys in registers) into slot sl: rank every key
+// within its digit (per warp), publish the tile's digit counts, find the
+// digit starts in the tile and in the segment (one scan), and place the keys
+// in digit order in sk[sl].  Nothing here waits for another tile.  kFull: the
+// tile holds kTileC keys (every bounds test folds away); kByte: whole-byte
+// digits.
+template <typename K, bool kFull, bool kByte>
+__device__ __forceinline__ void pass_rank_tile(Stage* stp, PassSmem<K>& S, int sl, int mi,
+                                               const K (&key)[kItemsC]) {
+  const PassMeta& m = S.meta[mi];
+  const uint32_t pass = stp->pass;
+  const Digit dg(stp->shift, stp->dbits), dn(stp->shift + stp->dbits, stp->dbits);
+  const bool ahead = m.nrow != nullptr;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t n = kFull ? (uint32_t)kTileC : n_tile;
-  const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
-  const K* p = (const K*)stp->in + sg.in_off + start;
-  for (uint32_t i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&S.whist[0][0])[i] = 0;
-  if (threadIdx.x == 0) S.s_bad = 0;
+  const uint32_t n = kFull ? (uint32_t)kTileC : m.n;
+  const uint32_t wb = warp * 32 * kItemsC + lane;
+  // this warp's counters and the block's next-digit counters start at zero
+  uint32_t* wc = S.wbase[warp];
+#pragma unroll
+  for (int j = 0; j < kRadix / 32; ++j) wc[lane + 32 * j] = 0;
+  S.nxt[threadIdx.x] = 0;
   __syncthreads();
 
-  // warp-striped load: warp w owns keys [w*32*kItemsC, (w+1)*32*kItemsC)
-  K key[kItemsC];
-  uint32_t rank[kItemsC];
-  const uint32_t wbase = warp * 32 * kItemsC + lane;
+  uint32_t rk[kItemsC / 2];  // ranks (< kTileC) packed two per word
 #pragma unroll
-  for (int i = 0; i < kItemsC; ++i) {
-    const uint32_t idx = wbase + i * 32;
-    key[i] = idx < n ? p[idx] : (K)0;
-  }
+  for (int i = 0; i < kItemsC / 2; ++i) rk[i] = 0;
   if (pass == 0) {
     // first pass: the input order carries nothing, so any order of equal
     // digits is correct -- one shared atomic per key gives its rank.  Keys
     // that tie on every sorted bit are identical (the bits above are zero),
     // so the sorted output equals that of a stable sort.
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i)
-      rank[i] = wbase + i * 32 < n ? atomicAdd(&S.whist[warp][digit(key[i], shift, mask)], 1u) : 0u;
+    for (int i = 0; i < kItemsC; ++i) {
+      if (kFull || wb + i * 32 < n)
+        rk[i >> 1] |= atomicAdd(&wc[dg.operator()<kByte>(key[i])], 1u) << (16 * (i & 1));
+    }
   } else {
     // later passes: stable rank within the warp -- peers with the same
     // digit, in (i, lane) order
 #pragma unroll
     for (int i = 0; i < kItemsC; ++i) {
-      const uint32_t d = wbase + i * 32 < n ? digit(key[i], shift, mask) : 0xFFFFFFFFu;
+      const bool ok = kFull || wb + i * 32 < n;
+      const uint32_t d = ok ? dg.operator()<kByte>(key[i]) : 0xFFFFFFFFu;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
-      if (d != 0xFFFFFFFFu) before = S.whist[warp][d];
-      rank[i] = before + __popc(peers & lt_mask);
+      if (ok) before = wc[d];
+      rk[i >> 1] |= (before + __popc(peers & lt_mask)) << (16 * (i & 1));
       __syncwarp();
-      if (d != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1))
-        S.whist[warp][d] = before + __popc(peers);
+      if (ok && lane == (uint32_t)(__ffs(peers) - 1)) wc[d] = before + __popc(peers);
       __syncwarp();
     }
   }
+  if (ahead) {  // the next pass's digits of the same keys
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (kFull || wb + i * 32 < n) atomicAdd(&S.nxt[dn.operator()<kByte>(key[i])], 1u);
+  }
   __syncthreads();
 
-  // thread d owns digit d: prefix over warps, tile count, publish it
+  // thread d owns digit d: per-warp counts, tile count, publish it; the
+  // segment's count of the digit (loaded first, its latency overlaps)
   const uint32_t d = threadIdx.x;
-  uint32_t cnt = 0;
+  const unsigned long long hcount =
+      stp->hist[((unsigned long long)m.k * stp->passes + pass) * kRadix + d];
+  uint32_t cnt = 0;  // the warps' counts become exclusive prefixes over warps
 #pragma unroll
   for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = S.whist[w][d];
-    S.whist[w][d] = cnt;
+    const uint32_t c = S.wbase[w][d];
+    S.wbase[w][d] = cnt;
     cnt += c;
   }
-  const bool first = (t == sg.tile0);
-  st_put(stp->status + (unsigned long long)t * kRadix + d,
-         st_pack(stp->epoch, first ? FLAG_INC : FLAG_AGG, cnt));
+  st_put(stp->status + (unsigned long long)m.t * kRadix + d,
+         st_pack(stp->epoch, m.first ? FLAG_INC : FLAG_AGG, cnt));
+  if (ahead) {
+    const uint32_t nx = S.nxt[d];
+    if (nx) atomicAdd(m.nrow + d, (unsigned long long)nx);
+  }
+  // one scan gives both starts: the tile count (<= kTileC < 2^13) in the low
+  // 13 bits, the segment count above them
   unsigned long long tot;
-  const unsigned long long ts = block_excl_scan(cnt, S.s_scan, &tot);
-  S.tstart[sl][d] = (uint32_t)ts;
-  S.tcnt[sl][d] = cnt;
-  if (threadIdx.x == 0) S.meta[sl] = PassMeta{t, k, n, first ? 1u : 0u};
+  const unsigned long long ex = block_excl_scan((hcount << 13) | cnt, S.s_scan, &tot);
+  const uint32_t ts = (uint32_t)(ex & 0x1FFFu);
+  S.tstart[sl][d] = ts;
+  if (d == kRadix - 1) S.tstart[sl][kRadix] = ts + cnt;
+  S.hstart[sl][d] = ex >> 13;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) S.wbase[w][d] += ts;
   __syncthreads();
   // the tile in digit order: a key's place inside the tile needs no global offset
 #pragma unroll
   for (int i = 0; i < kItemsC; ++i)
-    if (wbase + i * 32 < n) {
-      const uint32_t dg = digit(key[i], shift, mask);
-      S.sk[sl][S.tstart[sl][dg] + S.whist[warp][dg] + rank[i]] = key[i];
-    }
+    if (kFull || wb + i * 32 < n)
+      S.sk[sl][wc[dg.operator()<kByte>(key[i])] + ((rk[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = key[i];
 }
 
-template <typename K>
-__device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, uint32_t t, int sl) {
-  const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);
-  const Seg sg = stp->segs[k];
-  const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTileC;
-  const uint32_t n = (uint32_t)min((unsigned long long)kTileC, sg.n - start);
-  if constexpr (sizeof(K) == 4) {  // (64-bit keys: no room for a second copy in 64 registers)
-    if (n == (uint32_t)kTileC) {
-      pass_rank_tile<K, true>(stp, S, t, sl, k, sg, n);
+template <typename K, bool kByte>
+__device__ __forceinline__ void pass_rank(Stage* stp, PassSmem<K>& S, int sl, int mi,
+                                          const K (&key)[kItemsC]) {
+  if constexpr (sizeof(K) == 4) {
+    if (S.meta[mi].n == (uint32_t)kTileC) {
+      pass_rank_tile<K, true, kByte>(stp, S, sl, mi, key);
       return;
     }
   }
-  pass_rank_tile<K, false>(stp, S, t, sl, k, sg, n);
+  pass_rank_tile<K, false, kByte>(stp, S, sl, mi, key);
 }
 
 // Global offsets of the tile in slot `sl` by per-digit lookback, then stream
 // its digit runs out.  False when a lookback gave up (the run is void).
-template <typename K>
-__device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
-  __syncthreads();  // the slot's keys, counts and meta are visible
-  const PassMeta m = S.meta[sl];
-  const Seg& sg = stp->segs[m.k];
-  const uint32_t shift = stp->shift, mask = (1u << stp->dbits) - 1u, epoch = stp->epoch;
+template <typename K, bool kByte>
+__device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl, int mi) {
+  __syncthreads();  // the slot's keys, starts and meta are visible
+  const PassMeta& m = S.meta[mi];
+  const Digit dg(stp->shift, stp->dbits);
+  const uint32_t epoch = stp->epoch;
   Ctl* ctl = stp->ctl;
   unsigned long long* status = stp->status;
   const uint32_t d = threadIdx.x;
-  // the segment's count of digit d (loaded now, scanned after the lookback)
-  const unsigned long long hcount =
-      stp->hist[((unsigned long long)m.k * stp->passes + stp->pass) * kRadix + d];
+  const uint32_t ts = S.tstart[sl][d], cnt = S.tstart[sl][d + 1] - ts;
   unsigned long long excl = 0;
   if (!m.first) {
     // per-digit lookback over earlier tiles of this segment: the words of a
     // window of kLookW predecessors are loaded at once, then consumed nearest
     // first until an inclusive one (a walk of dependent loads would cost one
     // L2 round trip per tile, and tiles behind this one wait for it)
-    const long long tile0 = sg.tile0;
+    const long long tile0 = m.tile0;
     long long j = (long long)m.t - 1;
     bool done = false;
     while (!done) {
@@ -250,71 +339,93 @@ __device__ __forceinline__ bool pass_write(Stage* stp, PassSmem<K>& S, int sl) {
       }
       j -= w;
     }
-    st_put(status + (unsigned long long)m.t * kRadix + d,
-           st_pack(epoch, FLAG_INC, excl + S.tcnt[sl][d]));
+    st_put(status + (unsigned long long)m.t * kRadix + d, st_pack(epoch, FLAG_INC, excl + cnt));
   }
-  // digit d of the segment starts after all its smaller digits: a block
-  // scan of the segment's histogram row (one digit per thread)
-  unsigned long long htot;
-  const unsigned long long hstart = block_excl_scan(hcount, S.s_scan, &htot);
-  // a segment of fewer than 2^32 keys: 32-bit offsets from its start
-  const bool rel32 = sg.n <= 0xFFFFFFFFull;
-  if (rel32) S.gdst32[d] = (uint32_t)(hstart + excl - S.tstart[sl][d]);
-  else S.gdst[d] = sg.out_off + hstart + excl - S.tstart[sl][d];
+  const unsigned long long g = S.hstart[sl][d] + excl;
+  if (m.rel32) S.gdst32[d] = (uint32_t)g - ts;
+  else S.gdst[d] = m.out + g - ts;
   __syncthreads();
   if (S.s_bad) return false;
   K* out = (K*)stp->out;
-  if (rel32) {
-    K* outs = out + sg.out_off;
+  if (m.rel32) {
+    K* outs = out + m.out;
     if (m.n == (uint32_t)kTileC) {
 #pragma unroll
       for (int e = 0; e < kItemsC; ++e) {
         const uint32_t i = threadIdx.x + e * kThreads;
         const K v = S.sk[sl][i];
-        outs[S.gdst32[digit(v, shift, mask)] + i] = v;
+        outs[S.gdst32[dg.operator()<kByte>(v)] + i] = v;
       }
     } else {
       for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
         const K v = S.sk[sl][i];
-        outs[S.gdst32[digit(v, shift, mask)] + i] = v;
+        outs[S.gdst32[dg.operator()<kByte>(v)] + i] = v;
       }
     }
   } else {
     for (uint32_t i = threadIdx.x; i < m.n; i += kThreads) {
       const K v = S.sk[sl][i];
-      out[S.gdst[digit(v, shift, mask)] + i] = v;
+      out[S.gdst[dg.operator()<kByte>(v)] + i] = v;
     }
   }
   return true;
 }
 
-// One LSD pass (onesweep-style).  With two slots (32-bit keys) a CTA ranks and
-// publishes its next tile before it looks back for the previous one, so the
-// predecessors have had one tile time to publish.  Deadlock-free: ranking and
-// publishing never wait, so the oldest unfinished tile can always complete.
-template <typename K>
+// One LSD pass (onesweep-style), software-pipelined over the tiles a CTA
+// claims.  Each step ranks tile A (its keys already in registers) and
+// publishes its counts, claims tile B and issues B's loads, and only then
+// writes out a ranked tile -- so B's loads are in flight during that tile's
+// lookback and stores.  With two slots (32-bit keys) the tile written is the
+// one ranked a step earlier (its predecessors have had one step to publish);
+// with one slot it is A.  Deadlock-free: ranking, publishing and loading
+// never wait, and a tile that is claimed but not yet ranked sits in a CTA
+// writing an older tile, so the oldest tile being written can always finish
+// its lookback.
+template <typename K, bool kByte>
+__device__ __forceinline__ void pass_loop(Stage* stp, PassSmem<K>& S) {
+  const uint32_t ntiles = stp->ntiles;
+  if (threadIdx.x == 0) S.s_bad = 0;
+  K key[kItemsC];
+  int ma = 0, sa = 0;  // tile A: meta entry, slot
+  if (pass_claim<K>(stp, S, ma) >= ntiles) return;
+  pass_load<K>(stp, S.meta[ma], key);
+  if constexpr (PassSmem<K>::kSlots == 2) {
+    bool hasP = false;
+    int mp = 0, sp = 0;  // tile P (ranked, not yet written)
+    for (;;) {
+      pass_rank<K, kByte>(stp, S, sa, ma, key);
+      int mb = ma == 2 ? 0 : ma + 1;
+      if (hasP && mb == mp) mb = mb == 2 ? 0 : mb + 1;
+      const bool more = pass_claim<K>(stp, S, mb) < ntiles;
+      if (more) pass_load<K>(stp, S.meta[mb], key);
+      if (hasP && !pass_write<K, kByte>(stp, S, sp, mp)) return;
+      if (!more) {
+        pass_write<K, kByte>(stp, S, sa, ma);
+        return;
+      }
+      hasP = true;
+      mp = ma; sp = sa;
+      ma = mb; sa = sp ^ 1;
+    }
+  } else {
+    for (;;) {
+      pass_rank<K, kByte>(stp, S, 0, ma, key);
+      const int mb = ma ^ 1;
+      const bool more = pass_claim<K>(stp, S, mb) < ntiles;
+      if (more) pass_load<K>(stp, S.meta[mb], key);
+      if (!pass_write<K, kByte>(stp, S, 0, ma) || !more) return;
+      ma = mb;
+    }
+  }
+}
+
+// kByte: whole-byte digits (dbits == 8; the host knows the pass plan and
+// picks the instantiation).
+template <typename K, bool kByte>
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
   __shared__ PassSmem<K> S;
   if (*(volatile uint32_t*)&stp->ctl->abort) return;
-  const uint32_t ntiles = stp->ntiles;
-  uint32_t t = claim_tile(stp, &S.s_t);
-  if (t >= ntiles) return;
-  pass_rank<K>(stp, S, t, 0);
-  int cur = 0;
-  for (;;) {
-    if (PassSmem<K>::kSlots == 2) {
-      const uint32_t tn = claim_tile(stp, &S.s_t);
-      const bool more = tn < ntiles;
-      if (more) pass_rank<K>(stp, S, tn, cur ^ 1);
-      if (!pass_write<K>(stp, S, cur) || !more) return;
-      cur ^= 1;
-    } else {
-      if (!pass_write<K>(stp, S, 0)) return;
-      const uint32_t tn = claim_tile(stp, &S.s_t);
-      if (tn >= ntiles) return;
-      pass_rank<K>(stp, S, tn, 0);
-    }
-  }
+  pass_loop<K, kByte>(stp, S);
 }
 
 // ------------------------------------------------------------------ dedup + diff
@@ -901,7 +1012,10 @@ __global__ void k_partition(Stage* cons, int mode, uint32_t tile) {
 template <typename K>
 void launch_sort_hist(Stage* st, int grid, cudaStream_t s) { k_sort_hist<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
-void launch_sort_pass(Stage* st, int grid, cudaStream_t s) { k_sort_pass<K><<<grid, kThreads, 0, s>>>(st); }
+void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits) {
+  if (dbits == 8) k_sort_pass<K, true><<<grid, kThreads, 0, s>>>(st);
+  else k_sort_pass<K, false><<<grid, kThreads, 0, s>>>(st);
+}
 template <typename K>
 void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
@@ -941,7 +1055,7 @@ template <typename K>
 int occupancy_sort(int which) {
   switch (which) {
     case 0: return occupancy_of(k_sort_hist<K>);
-    case 1: return occupancy_of(k_sort_pass<K>);
+    case 1: return occupancy_of(k_sort_pass<K, true>);
     case 2: return occupancy_of(k_unique_diff<K>);
     case 3: return occupancy_of(k_merge<K>);
     case 4: return occupancy_of(k_diff_merge<K, FuseTile<K>::T>);
@@ -952,7 +1066,7 @@ int occupancy_sort(int which) {
 
 #define WG_INST(K)                                              \
   template void launch_sort_hist<K>(Stage*, int, cudaStream_t);  \
-  template void launch_sort_pass<K>(Stage*, int, cudaStream_t);  \
+  template void launch_sort_pass<K>(Stage*, int, cudaStream_t, uint32_t); \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t, uint32_t); \

@@ -15,7 +15,8 @@ struct Inst;
 
 // sorted-array stages (wg_kern_sort.cu); K = uint32_t or unsigned long long
 template <typename K> void launch_sort_hist(Stage* st, int grid, cudaStream_t s);
-template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s);
+// dbits: digit width of the pass plan (8 picks the whole-byte-digit kernel)
+template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits);
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
 // tile: merged keys per fused-pass tile, FuseTile<K>::T or half of it
@@ -45,6 +46,8 @@ template <typename K> int occupancy_join(int which);  // 0 count, 1 emit, 2 tria
 struct Ctl;
 void launch_selftest_wait(const unsigned long long* status, Ctl* ctl, unsigned long long* out,
                           cudaStream_t s);
+// the same wait in the allocation-free sort's control block (wg_noalloc.cu)
+int noalloc_selftest_wait(cudaStream_t s);
 void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);

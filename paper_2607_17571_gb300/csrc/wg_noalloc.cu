@@ -21,6 +21,14 @@
 // The first call on each device looks up the array's device address with
 // cudaGetSymbolAddress (with that device current) and caches it; make that
 // first call before any stream capture on the device.
+//
+// A radix pass whose bounded lookback wait gives up marks the control block in
+// the scratch (the later passes of that call then return at once, so the keys
+// are left unspecified).  The call has already returned by then, so the mark is
+// kept: each call's set-up kernel folds the previous control block's error
+// into a sticky word before clearing it, and a call with n = 0 synchronises the
+// stream, reads and clears that word and returns WG_E_DEVICE_TIMEOUT if any
+// call since the last such check gave up.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -37,16 +45,19 @@ constexpr size_t kNoAllocMaxKeys = WG_NOALLOC_MAX_KEYS;
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-// Scratch layout: Stage[S_NUM] | Seg | Ctl | hist u64[kMaxPasses*kRadix] |
-// status u64[(tiles+1)*kRadix] | ping-pong keys (8-byte keys, kNoAllocMaxKeys)
+// Scratch layout: Stage[S_NUM] | Seg | Ctl | sticky error word |
+// hist u64[kMaxPasses*kRadix] | status u64[(tiles+1)*kRadix] |
+// ping-pong keys (8-byte keys, kNoAllocMaxKeys)
 constexpr size_t kTiles = (kNoAllocMaxKeys + kTileC - 1) / kTileC;
 constexpr size_t kOffStage = 0;
 constexpr size_t kOffSeg = align_up(kOffStage + sizeof(Stage) * S_NUM);
 constexpr size_t kOffCtl = align_up(kOffSeg + sizeof(Seg));
-constexpr size_t kOffHist = align_up(kOffCtl + sizeof(Ctl));
+constexpr size_t kOffSticky = align_up(kOffCtl + sizeof(Ctl));
+constexpr size_t kOffHist = align_up(kOffSticky + sizeof(uint32_t));
 constexpr size_t kOffStatus = align_up(kOffHist + sizeof(unsigned long long) * kMaxPasses * kRadix);
 constexpr size_t kOffKeys = align_up(kOffStatus + sizeof(unsigned long long) * (kTiles + 1) * kRadix);
 constexpr size_t kScratchBytes = align_up(kOffKeys + sizeof(unsigned long long) * kNoAllocMaxKeys);
+static_assert(kScratchBytes == WG_NOALLOC_SCRATCH_BYTES, "the header states the scratch size");
 
 }  // namespace
 
@@ -75,6 +86,7 @@ __global__ void k_noalloc_setup(unsigned char* base, void* keys, unsigned long l
     Stage* st = (Stage*)(base + kOffStage);
     Seg* sg = (Seg*)(base + kOffSeg);
     Ctl* ctl = (Ctl*)(base + kOffCtl);
+    *(uint32_t*)(base + kOffSticky) |= ctl->error;  // kept until a call with n = 0 reads it
     *ctl = Ctl{};
     Seg s{};
     s.n = n; s.ntiles = ntiles;
@@ -108,6 +120,28 @@ int scratch_of(int dev, unsigned char** out) {
   return WG_OK;
 }
 
+// n = 0: did a call since the last check give up a device wait?  Reads the
+// sticky word and the last call's control block after the stream's earlier
+// work, then clears both.
+int noalloc_check(cudaStream_t s, int dev) {
+  unsigned char* base = nullptr;
+  int rc = scratch_of(dev, &base);
+  if (rc != WG_OK) return rc;
+  uint32_t sticky = 0, err = 0;
+  cudaError_t e = cudaMemcpyAsync(&sticky, base + kOffSticky, 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&err, base + kOffCtl + offsetof(Ctl, error), 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && (sticky || err)) {
+    e = cudaMemsetAsync(base + kOffSticky, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffCtl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) return set_error(WG_E_CUDA, cudaGetErrorString(e));
+  if (sticky || err) return set_error(WG_E_DEVICE_TIMEOUT, "an earlier allocation-free sort gave up a device wait");
+  return WG_OK;
+}
+
 template <typename K>
 int sort_noalloc(K* keys, size_t n, uint32_t bits, cudaStream_t s, int dev) {
   unsigned char* base = nullptr;
@@ -122,7 +156,7 @@ int sort_noalloc(K* keys, size_t n, uint32_t bits, cudaStream_t s, int dev) {
   Stage* st = (Stage*)(base + kOffStage);
   launch_sort_hist<K>(st + S_HIST, sms * std::max(1, occupancy_sort<K>(0)), s);
   for (uint32_t p = 0; p < passes; ++p)
-    launch_sort_pass<K>(st + S_PASS0 + p, sms * std::max(1, occupancy_sort<K>(1)), s);
+    launch_sort_pass<K>(st + S_PASS0 + p, sms * std::max(1, occupancy_sort<K>(1)), s, dbits);
   if (passes & 1) {
     const cudaError_t e = cudaMemcpyAsync(keys, base + kOffKeys, n * sizeof(K),
                                           cudaMemcpyDeviceToDevice, s);
@@ -134,6 +168,28 @@ int sort_noalloc(K* keys, size_t n, uint32_t bits, cudaStream_t s, int dev) {
 }
 
 }  // namespace
+
+// Self-test of the bounded wait in the allocation-free sort's control block:
+// the scan stages' lookback wait on a status word of the scratch that nothing
+// publishes.  The wait gives up, records DEV_TIMEOUT in the scratch's control
+// block and returns; the next check (a call with n = 0) reports it.
+int noalloc_selftest_wait(cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(WG_E_CUDA, cudaGetErrorString(e));
+  unsigned char* base = nullptr;
+  const int rc = scratch_of(dev, &base);
+  if (rc != WG_OK) return rc;
+  unsigned long long* status = (unsigned long long*)(base + kOffStatus);
+  e = cudaMemsetAsync(status, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + kOffCtl, 0, sizeof(Ctl), s);
+  if (e != cudaSuccess) return set_error(WG_E_CUDA, cudaGetErrorString(e));
+  launch_selftest_wait(status, (Ctl*)(base + kOffCtl), (unsigned long long*)(base + kOffHist), s);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? WG_OK : set_error(WG_E_CUDA, cudaGetErrorString(e));
+}
+
 }  // namespace wg
 
 extern "C" int wg_sort_keys_noalloc(void* d_keys, size_t n, int key_bytes, uint32_t bits,
@@ -142,6 +198,12 @@ extern "C" int wg_sort_keys_noalloc(void* d_keys, size_t n, int key_bytes, uint3
   if ((n && !d_keys) || (key_bytes != 4 && key_bytes != 8) || bits == 0 ||
       bits > 8u * (uint32_t)key_bytes)
     return set_error(WG_E_INVAL, "bad argument");
+  if (n == 0) {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_error(WG_E_CUDA, cudaGetErrorString(e));
+    return noalloc_check((cudaStream_t)cuda_stream, dev);
+  }
   if (n > kNoAllocMaxKeys)
     return set_error(WG_E_CAPACITY, ("wg_sort_keys_noalloc sorts at most " +
                                      std::to_string(kNoAllocMaxKeys) + " keys, got " +

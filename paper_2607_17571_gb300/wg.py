@@ -21,7 +21,7 @@ WG_OK = 0
 WG_E_INVAL, WG_E_NOMEM, WG_E_BUDGET, WG_E_CAPACITY = -1, -2, -3, -4
 WG_E_NOT_READY, WG_E_ITER_CAP, WG_E_DEVICE_TIMEOUT, WG_E_CUDA = -5, -6, -7, -8
 WG_TC, WG_SG = 0, 1
-WG_LOOP_DEVICE, WG_LOOP_HOST = 0, 1
+WG_LOOP_DEVICE, WG_LOOP_HOST, WG_LOOP_HOST_STAGED = 0, 1, 2
 WG_FLAG_SEPARATE_STAGES = 1
 WG_FLAG_FULL_WIDTH = 2
 WG_FLAG_COPY_BACK = 4
@@ -154,6 +154,14 @@ def sort_keys_noalloc(ptr: int, n: int, key_bytes: int, bits: int, stream_ptr=No
     _check(load_library().wg_sort_keys_noalloc(c_void_p(ptr), n, key_bytes, bits,
                                                c_void_p(stream_ptr) if stream_ptr else None),
            "wg_sort_keys_noalloc")
+
+
+def noalloc_check(stream_ptr=None) -> int:
+    """wg_sort_keys_noalloc with n = 0: synchronises the stream and returns
+    WG_E_DEVICE_TIMEOUT if an allocation-free sort on this device gave up a
+    device wait since the last check (else WG_OK); clears the record."""
+    return load_library().wg_sort_keys_noalloc(None, 0, 4, 32,
+                                               c_void_p(stream_ptr) if stream_ptr else None)
 
 
 class Query:

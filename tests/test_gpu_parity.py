@@ -199,7 +199,9 @@ def test_result_into_pinned_buffer(ctx):
     rel.free()
 
 
-@pytest.mark.parametrize("flags", [dict(full_width=True), dict(copy_back=True),
+@pytest.mark.parametrize("flags", [dict(loop=1), dict(loop=2),  # WG_LOOP_HOST, WG_LOOP_HOST_STAGED
+                                   dict(loop=2, separate_stages=True),
+                                   dict(full_width=True), dict(copy_back=True),
                                    dict(full_width=True, copy_back=True),
                                    dict(copy_back=True, separate_stages=True),
                                    dict(hash_join=True), dict(hash_join=True, full_width=True)])

@@ -23,3 +23,10 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
         want = oracle_tc(g.src, g.dst)
         assert np.array_equal(q.result(), want.keys) and q.delta_sizes() == want.log.tolist()
         q.free()
+        # the context's sort primitive still sorts (its control block starts clear)
+        import torch
+        keys = np.random.default_rng(3).integers(0, 2 ** 32, 200_000, dtype=np.uint64).astype(np.uint32)
+        t = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+        torch.cuda.synchronize()
+        c.sort_keys(t.data_ptr(), keys.shape[0], 4, 32)
+        assert np.array_equal(t.cpu().numpy().view(np.uint32), np.sort(keys))

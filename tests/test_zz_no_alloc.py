@@ -5,9 +5,11 @@ and a stream; its scratch is a static device array inside the library.
 
 Checked through the C-ABI against the context-based wg_sort_keys, bit for bit
 (integer keys: exact equality), on two calls in a row so that the second call
-runs on the scratch the first one left behind; and a size above the stated
-maximum must be refused without touching the keys.  This file is collected
-last so that a failure here never hides the other tests.
+runs on the scratch the first one left behind; on a non-default stream; a size
+above the stated maximum must be refused without touching the keys; and a
+bounded device wait that gives up must be reported by the next check (a call
+with n = 0).  This file is collected last so that a failure here never hides
+the other tests.
 """
 import numpy as np
 import pytest
@@ -43,6 +45,25 @@ def test_noalloc_sort_matches_wg_sort_keys_on_two_calls():
             assert np.array_equal(got.cpu().numpy().view(keys.dtype), np.sort(keys))
 
 
+def test_noalloc_sort_on_a_non_default_stream():
+    """Keys produced on a torch stream and sorted on it (odd pass count: 40-bit
+    keys take five 8-bit passes and a copy back); only that stream is
+    synchronised before the result is read."""
+    from paper_2607_17571_gb300 import wg
+    rng = np.random.default_rng(77)
+    s = torch.cuda.Stream()
+    for kb, bits, n in [(8, 40, 333_333), (4, 24, 65_537)]:
+        keys = _random_keys(rng, n, kb, bits)
+        host = torch.from_numpy(keys.view(np.int32 if kb == 4 else np.int64).copy()).pin_memory()
+        with torch.cuda.stream(s):
+            t = torch.empty_like(host, device="cuda")
+            t.copy_(host, non_blocking=True)      # produced on s
+            wg.sort_keys_noalloc(t.data_ptr(), n, kb, bits, s.cuda_stream)
+            out = t.to("cpu", non_blocking=False)
+        s.synchronize()
+        assert np.array_equal(out.numpy().view(keys.dtype), np.sort(keys))
+
+
 def test_noalloc_sort_refuses_sizes_above_the_maximum():
     from paper_2607_17571_gb300 import wg
     n = wg.WG_NOALLOC_MAX_KEYS + 1
@@ -54,3 +75,24 @@ def test_noalloc_sort_refuses_sizes_above_the_maximum():
     assert e.value.code == wg.WG_E_CAPACITY
     torch.cuda.synchronize()
     assert np.array_equal(t.cpu().numpy().view(np.uint32), keys)
+
+
+def test_noalloc_wait_timeout_is_reported_by_the_next_check():
+    """Failure detection without a GPU fault: the self-test runs the lookback
+    wait in the scratch's control block on a status word nothing publishes;
+    the wait gives up and records it.  The next check reports
+    WG_E_DEVICE_TIMEOUT and clears the record, the one after reports WG_OK,
+    and a sort afterwards is correct."""
+    from paper_2607_17571_gb300 import wg
+    wg.noalloc_check()  # start from a clear record (earlier tests may have left one)
+    with wg.Context(0) as ctx:
+        assert ctx.selftest_wait_timeout() == wg.WG_E_DEVICE_TIMEOUT
+    assert wg.noalloc_check() == wg.WG_E_DEVICE_TIMEOUT
+    assert wg.noalloc_check() == wg.WG_OK
+    rng = np.random.default_rng(5)
+    keys = _random_keys(rng, 100_000, 4, 32)
+    t = _to_dev(keys)
+    torch.cuda.synchronize()
+    wg.sort_keys_noalloc(t.data_ptr(), keys.shape[0], 4, 32)
+    assert wg.noalloc_check() == wg.WG_OK
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), np.sort(keys))
