@@ -93,6 +93,10 @@ struct Stage {
   // partition; the others hold Full elements only and are copied separately
   const uint32_t* mixl;            // mixed tiles in order (or NULL: every tile)
   const uint32_t* mixc;            // mixed tiles before tile t; [ntiles] = their number
+  // radix sort: the largest segment's tile count (or NULL).  At most
+  // kSegSortMaxTiles: one CTA per segment sorts the launch (k_sort_seg) and
+  // the lookback passes have nothing to do; otherwise the reverse.
+  const uint32_t* maxt;
 };
 
 // Hash-join ablation (the hash-based join the paper's sorted-array join
@@ -136,6 +140,9 @@ template <typename K> struct FuseTile {
   static constexpr int T = sizeof(K) == 4 ? 4096 : 2048;
   static constexpr int E = T / kThreads;
 };
+
+// Per-segment radix sort (k_sort_seg): used when no segment has more tiles.
+constexpr uint32_t kSegSortMaxTiles = 128;
 
 // x-grouped sort: relations of up to kXSegMaxVertices vertices, segment
 // records built by chunks of kXChunk source vertices.
@@ -185,6 +192,7 @@ struct Dev {
   uint32_t count_tile;                // delta tuples per join-count tile
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
+  uint32_t xseg_maxt;                 // x-grouped sort: tiles of the largest source segment
 };
 
 // Shared-memory index with one pad word per 32: threads that walk their own

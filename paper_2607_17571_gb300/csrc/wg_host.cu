@@ -510,14 +510,14 @@ struct Engine : EngineBase {
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_uniq = 0, g_merge = 0, g_fuse = 0;
+  int g_count = 0, g_emit = 0, g_hist = 0, g_pass = 0, g_seg = 0, g_uniq = 0, g_merge = 0, g_fuse = 0;
   bool in_flight = false;
   bool grow_wait = false;  // batch: paused after an overflow until the memory comes back
   size_t wait_used = 0;    // the context's allocated bytes when the pause began
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 2 : 0) - (hash_join ? 1 : 0); }
+  int kernels_per_iter() const { return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 3 : 0) - (hash_join ? 1 : 0); }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
@@ -598,6 +598,7 @@ struct Engine : EngineBase {
     g_emit = grid_of(c, occupancy_join<K>(1));
     g_hist = grid_of(c, occupancy_sort<K>(0));
     g_pass = grid_of(c, occupancy_sort<K>(1));
+    g_seg = grid_of(c, occupancy_sort<K>(6));
     g_uniq = grid_of(c, occupancy_sort<K>(2));
     g_merge = grid_of(c, occupancy_sort<K>(3));
     g_fuse = grid_of(c, occupancy_sort<K>(fuse_tile_ == (uint32_t)FuseTile<K>::T ? 4 : 5));
@@ -782,9 +783,20 @@ struct Engine : EngineBase {
     if (!stage()) return syncs;
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
     if (!stage()) return syncs;
-    for (uint32_t p = 0; p < passes; ++p) {
-      mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits); mark();
+    if (xseg) {
+      // per-source segments: one CTA per segment through every pass when no
+      // segment is longer than kSegSortMaxTiles tiles, else the lookback
+      // passes (each kernel finds out on the device and the other returns)
+      mark();
+      launch_sort_seg<K>(dv->st + S_PASS0, g_seg, s, dbits);
+      for (uint32_t p = 0; p < passes; ++p) launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits);
+      mark();
       if (!stage()) return syncs;
+    } else {
+      for (uint32_t p = 0; p < passes; ++p) {
+        mark(); launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits); mark();
+        if (!stage()) return syncs;
+      }
     }
     if (fuse) {
       launch_partition<K>(dv->st + S_FUSE, 0, fuse_tile_, c->num_sms * 4, s);
@@ -1090,7 +1102,10 @@ static int single_start(wg_ctx* c, Query* q) {
               {"join_count", nd * (kb + 8 + 8)},
               {"join_emit", nd * (kb + 8) + nc * (kb + 4)},
               {"sort_hist", nc * kb}};
-          for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
+          if (E->xgrouped())  // every pass in one timed region (k_sort_seg or the passes)
+            names.push_back({"sort_pass", E->passes * 2 * nc * kb});
+          else
+            for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
           if (E->fuse) {
             names.push_back({"dedup_diff_merge", (nc + 2 * nf + 2 * nn) * kb});
             names.push_back({"retire_copy", E->copyback() ? 2 * (nf + nn) * kb : 0.0});

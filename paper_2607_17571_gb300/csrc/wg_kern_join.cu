@@ -471,6 +471,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
   }
   const uint32_t nvx = dv->xseg ? dv->inst[0].nv : 0u;
   for (uint32_t x = threadIdx.x; x < nvx; x += kPlanThreads) dv->xlen[x] = 0;
+  if (threadIdx.x == 0) dv->xseg_maxt = 0;
   if (threadIdx.x == 0) {
     Stage& s = dv->st[S_COUNT];
     s.in = dv->D[dv->dphase]; s.out = nullptr; s.aux = nullptr; s.out2 = nullptr;
@@ -535,6 +536,10 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
   const unsigned long long el = block_excl_scan(len, sh, &tl);
   const unsigned long long et = block_excl_scan(nt, sh, &tt);
   slen[threadIdx.x] = len;
+  {  // the largest segment's tile count picks the sort kernel (k_sort_seg or the passes)
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, (uint32_t)min(nt, 0xFFFFFFFFull));
+    if ((threadIdx.x & 31) == 0 && wm) atomicMax(&dv->xseg_maxt, wm);
+  }
   if (x < nv) {
     const unsigned long long off = I.c_off + pl + el;
     const uint32_t tile0 = (uint32_t)(pt + et);
@@ -558,6 +563,7 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
       dv->st[S_PASS0 + p].ntiles = ntiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
+      dv->st[S_PASS0 + p].maxt = &dv->xseg_maxt;
     }
   }
 }

@@ -425,7 +425,192 @@ template <typename K, bool kByte>
 __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
   __shared__ PassSmem<K> S;
   if (*(volatile uint32_t*)&stp->ctl->abort) return;
+  if (stp->maxt && *stp->maxt <= kSegSortMaxTiles) return;  // k_sort_seg sorts this launch
   pass_loop<K, kByte>(stp, S);
+}
+
+// ------------------------------------------------------------------ per-segment sort
+// Many segments of at most kSegSortMaxTiles tiles (the per-source segments of
+// the x-grouped sort): one CTA takes a whole segment through every pass, its
+// tiles in order, so each digit's next output offset in the segment is a
+// running count in shared memory -- no lookback and no status words -- and
+// the next pass's digit counts of the segment are accumulated in shared
+// memory while the current pass ranks.  Every pass after the first ranks
+// stably within a tile and takes the tiles in order, so it is stable.  A CTA
+// claims the segments of at least kSegBig tiles first, then the others, so
+// the longest ones do not start last.
+constexpr uint32_t kSegBig = 16;
+
+template <typename K>
+struct SegSmem {
+  K sk[kTileC];                   // a ranked tile in digit order
+  uint32_t wbase[kWarps][kRadix]; // per-warp counters -> tile-local start of (warp, digit)
+  uint32_t gdst[kRadix];          // output offset in the segment minus the digit's tile start
+  uint32_t run[kRadix];           // next output offset of each digit in the segment
+  uint32_t nxt[kRadix];           // next pass's digit counts of the segment
+  unsigned long long s_scan[kWarps];
+  uint32_t s_k;
+};
+
+__device__ __forceinline__ uint32_t seg_claim(Stage* st0, uint32_t* s_k) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t nseg = st0->nseg;
+    uint32_t k = 0xFFFFFFFFu;
+    for (;;) {
+      const uint32_t v = atomicAdd(&st0->ctr, 1u);
+      if (v >= 2 * nseg) break;
+      const uint32_t kk = v < nseg ? v : v - nseg;
+      const uint32_t nt = st0->segs[kk].ntiles;
+      if (nt != 0 && (v < nseg) == (nt >= kSegBig)) {
+        k = kk;
+        break;
+      }
+    }
+    *s_k = k;
+  }
+  __syncthreads();
+  return *s_k;
+}
+
+// Load tile j of a segment (n keys from p) into registers, warp-striped.
+template <typename K>
+__device__ __forceinline__ void seg_load(const K* p, uint32_t n, K (&key)[kItemsC]) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t wb = warp * 32 * kItemsC + lane;
+  if (n == (uint32_t)kTileC) {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) key[i] = p[wb + i * 32];
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) key[i] = wb + i * 32 < n ? p[wb + i * 32] : (K)0;
+  }
+}
+
+// One tile of one pass: rank (unstable for the first pass, stable after),
+// count the next pass's digits, place the keys in digit order, compute their
+// output offsets from the running counts.  The caller writes the tile out.
+template <typename K, bool kByte>
+__device__ __forceinline__ void seg_rank_tile(SegSmem<K>& S, const K (&key)[kItemsC], uint32_t n,
+                                              const Digit& dg, const Digit& dn, bool first_pass,
+                                              bool ahead) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t wb = warp * 32 * kItemsC + lane;
+  uint32_t* wc = S.wbase[warp];
+#pragma unroll
+  for (int j = 0; j < kRadix / 32; ++j) wc[lane + 32 * j] = 0;
+  __syncthreads();  // (also: the previous tile's stores have read sk and gdst)
+  uint32_t rk[kItemsC / 2];
+#pragma unroll
+  for (int i = 0; i < kItemsC / 2; ++i) rk[i] = 0;
+  if (first_pass) {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (wb + i * 32 < n)
+        rk[i >> 1] |= atomicAdd(&wc[dg.operator()<kByte>(key[i])], 1u) << (16 * (i & 1));
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i) {
+      const bool ok = wb + i * 32 < n;
+      const uint32_t d = ok ? dg.operator()<kByte>(key[i]) : 0xFFFFFFFFu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t before = 0;
+      if (ok) before = wc[d];
+      rk[i >> 1] |= (before + __popc(peers & lt_mask)) << (16 * (i & 1));
+      __syncwarp();
+      if (ok && lane == (uint32_t)(__ffs(peers) - 1)) wc[d] = before + __popc(peers);
+      __syncwarp();
+    }
+  }
+  if (ahead) {
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (wb + i * 32 < n) atomicAdd(&S.nxt[dn.operator()<kByte>(key[i])], 1u);
+  }
+  __syncthreads();
+  // thread d: per-warp prefixes, the tile's count, its start in the tile and
+  // its output offset; the running count moves on
+  const uint32_t d = threadIdx.x;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    const uint32_t c = S.wbase[w][d];
+    S.wbase[w][d] = cnt;
+    cnt += c;
+  }
+  unsigned long long tot;
+  const uint32_t ts = (uint32_t)block_excl_scan((unsigned long long)cnt, S.s_scan, &tot);
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) S.wbase[w][d] += ts;
+  const uint32_t r = S.run[d];
+  S.gdst[d] = r - ts;
+  S.run[d] = r + cnt;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kItemsC; ++i)
+    if (wb + i * 32 < n)
+      S.sk[wc[dg.operator()<kByte>(key[i])] + ((rk[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = key[i];
+  __syncthreads();
+}
+
+template <typename K, bool kByte>
+__device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K>& S, uint32_t k) {
+  const Seg& sg = st0->segs[k];
+  const unsigned long long in_off = sg.in_off, out_off = sg.out_off;
+  const uint32_t n = (uint32_t)sg.n, nt = sg.ntiles, passes = st0->passes, dbits = st0->dbits;
+  const uint32_t d = threadIdx.x;
+  for (uint32_t p = 0; p < passes; ++p) {
+    const Stage* sp = st0 + p;
+    const K* in = (const K*)sp->in + in_off;
+    K* out = (K*)sp->out + out_off;
+    const Digit dg(sp->shift, dbits), dn(sp->shift + dbits, dbits);
+    const bool ahead = p + 1 < passes;
+    K key[kItemsC];
+    seg_load<K>(in, min(n, (uint32_t)kTileC), key);
+    // the segment's count of digit d in this pass: the histogram kernel's
+    // (first pass) or the previous pass's
+    const uint32_t c = p == 0 ? (uint32_t)st0->hist[(unsigned long long)k * passes * kRadix + d]
+                              : S.nxt[d];
+    unsigned long long tot;
+    S.run[d] = (uint32_t)block_excl_scan((unsigned long long)c, S.s_scan, &tot);
+    S.nxt[d] = 0;
+    for (uint32_t j = 0; j < nt; ++j) {
+      const uint32_t tn = min(n - j * (uint32_t)kTileC, (uint32_t)kTileC);
+      seg_rank_tile<K, kByte>(S, key, tn, dg, dn, p == 0, ahead);
+      if (j + 1 < nt) {  // the next tile's loads fly during this tile's stores
+        const uint32_t nn = min(n - (j + 1) * (uint32_t)kTileC, (uint32_t)kTileC);
+        seg_load<K>(in + (unsigned long long)(j + 1) * kTileC, nn, key);
+      }
+      K* o = out;  // offsets are from the segment's start
+      if (tn == (uint32_t)kTileC) {
+#pragma unroll
+        for (int e = 0; e < kItemsC; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          const K v = S.sk[i];
+          o[S.gdst[dg.operator()<kByte>(v)] + i] = v;
+        }
+      } else {
+        for (uint32_t i = threadIdx.x; i < tn; i += kThreads) {
+          const K v = S.sk[i];
+          o[S.gdst[dg.operator()<kByte>(v)] + i] = v;
+        }
+      }
+    }
+    __syncthreads();  // this pass's output (global) is complete before the next pass reads it
+  }
+}
+
+template <typename K, bool kByte>
+__global__ void __launch_bounds__(kThreads, 4) k_sort_seg(Stage* st0) {
+  __shared__ SegSmem<K> S;
+  if (*(volatile uint32_t*)&st0->ctl->abort) return;
+  if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;  // the lookback passes sort it
+  for (;;) {
+    const uint32_t k = seg_claim(st0, &S.s_k);
+    if (k == 0xFFFFFFFFu) return;
+    seg_sort<K, kByte>(st0, S, k);
+  }
 }
 
 // ------------------------------------------------------------------ dedup + diff
@@ -1017,6 +1202,11 @@ void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits) {
   else k_sort_pass<K, false><<<grid, kThreads, 0, s>>>(st);
 }
 template <typename K>
+void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits) {
+  if (dbits == 8) k_sort_seg<K, true><<<grid, kThreads, 0, s>>>(st0);
+  else k_sort_seg<K, false><<<grid, kThreads, 0, s>>>(st0);
+}
+template <typename K>
 void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
 void launch_merge(Stage* st, int grid, cudaStream_t s) { k_merge<K><<<grid, kThreads, 0, s>>>(st); }
@@ -1060,6 +1250,7 @@ int occupancy_sort(int which) {
     case 3: return occupancy_of(k_merge<K>);
     case 4: return occupancy_of(k_diff_merge<K, FuseTile<K>::T>);
     case 5: return occupancy_of(k_diff_merge<K, FuseTile<K>::T / 2>);
+    case 6: return occupancy_of(k_sort_seg<K, true>);
     default: return 0;
   }
 }
@@ -1067,6 +1258,7 @@ int occupancy_sort(int which) {
 #define WG_INST(K)                                              \
   template void launch_sort_hist<K>(Stage*, int, cudaStream_t);  \
   template void launch_sort_pass<K>(Stage*, int, cudaStream_t, uint32_t); \
+  template void launch_sort_seg<K>(Stage*, int, cudaStream_t, uint32_t); \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t, uint32_t); \
