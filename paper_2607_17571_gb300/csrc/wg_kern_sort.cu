@@ -45,11 +45,15 @@ struct Digit {
 };
 
 // ------------------------------------------------------------------ histogram
-// Counts of the FIRST pass's digit per segment: one read of the keys.  Each
-// radix pass counts the next pass's digits while it ranks its tile, so the
-// later digits need no read of their own.
-template <typename K, bool kByte>
-__device__ __forceinline__ void hist_tile(const K* p, uint32_t n, const Digit& dg, uint32_t* sh) {
+// Digit counts per segment from one read of the keys.  For the lookback
+// passes it counts the FIRST pass's digit only: each pass counts the next
+// pass's digits while it ranks its tile.  For the per-source segments (the
+// stage has `maxt`, so k_sort_seg may sort the launch) it counts the digits of
+// every pass, and no pass counts any.
+// NP > 0: that many digits per key (unrolled); NP == 0: np digits.
+template <typename K, bool kByte, int NP>
+__device__ __forceinline__ void hist_tile(const K* p, uint32_t n, uint32_t dbits, uint32_t np,
+                                          uint32_t* sh) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t wbase = warp * 32 * kItemsC + lane;
   K key[kItemsC];
@@ -58,14 +62,21 @@ __device__ __forceinline__ void hist_tile(const K* p, uint32_t n, const Digit& d
     const uint32_t idx = wbase + i * 32;
     key[i] = idx < n ? p[idx] : (K)0;
   }
+  const uint32_t npass = NP ? (uint32_t)NP : np;
 #pragma unroll
-  for (int i = 0; i < kItemsC; ++i)
-    if (wbase + i * 32 < n) atomicAdd(&sh[dg.operator()<kByte>(key[i])], 1u);
+  for (uint32_t ps = 0; ps < (NP ? (uint32_t)NP : (uint32_t)kMaxPasses); ++ps) {
+    if (ps >= npass) break;
+    const Digit dg(ps * dbits, dbits);
+    uint32_t* h = sh + ps * kRadix;
+#pragma unroll
+    for (int i = 0; i < kItemsC; ++i)
+      if (wbase + i * 32 < n) atomicAdd(&h[dg.operator()<kByte>(key[i])], 1u);
+  }
 }
 
 template <typename K>
 __global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
-  __shared__ uint32_t sh[kRadix];
+  __shared__ uint32_t sh[kMaxPasses * kRadix];
   __shared__ const K* s_p;
   __shared__ unsigned long long* s_row;
   __shared__ uint32_t s_t, s_n;
@@ -73,7 +84,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
   if (*(volatile uint32_t*)&ctl->abort) return;
   const K* in = (const K*)stp->in;
   const uint32_t passes = stp->passes, nseg = stp->nseg, ntiles = stp->ntiles;
-  const Digit dg(0, stp->dbits);
+  const uint32_t np = stp->maxt ? passes : 1u;  // digits counted per key
   const bool byte = stp->dbits == 8;
   for (;;) {
     __syncthreads();  // the previous tile's counts are flushed
@@ -89,14 +100,18 @@ __global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
         s_row = stp->hist + (unsigned long long)k * passes * kRadix;
       }
     }
-    sh[threadIdx.x] = 0;
+    for (uint32_t i = threadIdx.x; i < np * kRadix; i += kThreads) sh[i] = 0;
     __syncthreads();
     if (s_t >= ntiles) return;
-    if (byte) hist_tile<K, true>(s_p, s_n, dg, sh);
-    else hist_tile<K, false>(s_p, s_n, dg, sh);
+    if (byte && np == 1) hist_tile<K, true, 1>(s_p, s_n, 8, 1, sh);
+    else if (byte && np == 2) hist_tile<K, true, 2>(s_p, s_n, 8, 2, sh);
+    else if (byte) hist_tile<K, true, 0>(s_p, s_n, 8, np, sh);
+    else hist_tile<K, false, 0>(s_p, s_n, stp->dbits, np, sh);
     __syncthreads();
-    const uint32_t c = sh[threadIdx.x];
-    if (c) atomicAdd(&s_row[threadIdx.x], (unsigned long long)c);
+    for (uint32_t i = threadIdx.x; i < np * kRadix; i += kThreads) {
+      const uint32_t c = sh[i];
+      if (c) atomicAdd(&s_row[i], (unsigned long long)c);
+    }
   }
 }
 
@@ -149,7 +164,9 @@ __device__ __forceinline__ uint32_t pass_claim(Stage* stp, PassSmem<K>& S, int m
       PassMeta m;
       m.in = sg.in_off + start;
       m.out = sg.out_off;
-      m.nrow = stp->pass + 1 < stp->passes
+      // the next pass's digits are counted here unless the histogram
+      // kernel counted every pass's (stages with maxt)
+      m.nrow = stp->pass + 1 < stp->passes && !stp->maxt
                    ? stp->hist + ((unsigned long long)k * stp->passes + stp->pass + 1) * kRadix
                    : nullptr;
       m.t = t; m.k = k; m.tile0 = sg.tile0;
@@ -433,23 +450,60 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 // Many segments of at most kSegSortMaxTiles tiles (the per-source segments of
 // the x-grouped sort): one CTA takes a whole segment through every pass, its
 // tiles in order, so each digit's next output offset in the segment is a
-// running count in shared memory -- no lookback and no status words -- and
-// the next pass's digit counts of the segment are accumulated in shared
-// memory while the current pass ranks.  Every pass after the first ranks
+// running count in shared memory -- no lookback and no status words; the
+// histogram kernel counted every pass's digits.  Every pass after the first ranks
 // stably within a tile and takes the tiles in order, so it is stable.  A CTA
 // claims the segments of at least kSegBig tiles first, then the others, so
-// the longest ones do not start last.
+// the longest ones do not start last.  NT threads of IT keys each make a tile.
 constexpr uint32_t kSegBig = 16;
+constexpr int kSegNT = 256, kSegIT = 16, kSegMinBlocks = 4;  // 64 registers, 4 CTAs per SM
 
-template <typename K>
+template <typename K, int NT, int IT>
 struct SegSmem {
-  K sk[kTileC];                   // a ranked tile in digit order
-  uint32_t wbase[kWarps][kRadix]; // per-warp counters -> tile-local start of (warp, digit)
+  static constexpr int NW = NT / 32, TILE = NT * IT;
+  K sk[TILE];                     // a ranked tile in digit order
+  uint32_t wbase[NW][kRadix];     // per-warp counters -> tile-local start of (warp, digit)
   uint32_t gdst[kRadix];          // output offset in the segment minus the digit's tile start
   uint32_t run[kRadix];           // next output offset of each digit in the segment
-  uint32_t nxt[kRadix];           // next pass's digit counts of the segment
-  unsigned long long s_scan[kWarps];
+  uint32_t s_scan[NW];
   uint32_t s_k;
+};
+
+// Exclusive scan of one 32-bit value per thread over a CTA of NT threads.
+template <int NT>
+__device__ __forceinline__ uint32_t cta_excl_scan32(uint32_t v, uint32_t* sh) {
+  constexpr int NW = NT / 32;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  if (NW == 1) return x - v;
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < (uint32_t)NW ? sh[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < NW; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= (uint32_t)o) w += y;
+    }
+    if (lane < (uint32_t)NW) sh[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t r = (warp ? sh[warp - 1] : 0u) + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Digits owned by a thread in the per-digit steps: DPT consecutive digits
+// (CTAs of fewer than kRadix threads), else digit threadIdx.x (if < kRadix).
+template <int NT> struct SegDig {
+  static constexpr int DPT = NT >= kRadix ? 1 : kRadix / NT;
+  __device__ static bool owns() { return NT <= kRadix || threadIdx.x < (uint32_t)kRadix; }
+  __device__ static uint32_t first() { return threadIdx.x * DPT; }
 };
 
 __device__ __forceinline__ uint32_t seg_claim(Stage* st0, uint32_t* s_k) {
@@ -473,45 +527,49 @@ __device__ __forceinline__ uint32_t seg_claim(Stage* st0, uint32_t* s_k) {
   return *s_k;
 }
 
-// Load tile j of a segment (n keys from p) into registers, warp-striped.
-template <typename K>
-__device__ __forceinline__ void seg_load(const K* p, uint32_t n, K (&key)[kItemsC]) {
+// Load n <= NT*IT keys from p into registers, warp-striped.
+template <typename K, int NT, int IT>
+__device__ __forceinline__ void seg_load(const K* p, uint32_t n, K (&key)[IT]) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t wb = warp * 32 * kItemsC + lane;
-  if (n == (uint32_t)kTileC) {
+  const uint32_t wb = warp * 32 * IT + lane;
+  if (n == (uint32_t)(NT * IT)) {
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i) key[i] = p[wb + i * 32];
+    for (int i = 0; i < IT; ++i) key[i] = p[wb + i * 32];
   } else {
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i) key[i] = wb + i * 32 < n ? p[wb + i * 32] : (K)0;
+    for (int i = 0; i < IT; ++i) key[i] = wb + i * 32 < n ? p[wb + i * 32] : (K)0;
   }
 }
 
 // One tile of one pass: rank (unstable for the first pass, stable after),
 // count the next pass's digits, place the keys in digit order, compute their
 // output offsets from the running counts.  The caller writes the tile out.
-template <typename K, bool kByte>
-__device__ __forceinline__ void seg_rank_tile(SegSmem<K>& S, const K (&key)[kItemsC], uint32_t n,
-                                              const Digit& dg, const Digit& dn, bool first_pass,
-                                              bool ahead) {
+template <typename K, bool kByte, int NT, int IT>
+__device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&key)[IT],
+                                              uint32_t n, const Digit& dg, bool first_pass) {
+  using D = SegDig<NT>;
+  constexpr int NW = NT / 32;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  const uint32_t wb = warp * 32 * kItemsC + lane;
+  const uint32_t wb = warp * 32 * IT + lane;
   uint32_t* wc = S.wbase[warp];
+  // this warp's counters: the previous tile's per-digit step and scatter
+  // are behind a barrier already, and only this warp touches its row until
+  // the next barrier
 #pragma unroll
   for (int j = 0; j < kRadix / 32; ++j) wc[lane + 32 * j] = 0;
-  __syncthreads();  // (also: the previous tile's stores have read sk and gdst)
-  uint32_t rk[kItemsC / 2];
+  __syncwarp();
+  uint32_t rk[(IT + 1) / 2];
 #pragma unroll
-  for (int i = 0; i < kItemsC / 2; ++i) rk[i] = 0;
+  for (int i = 0; i < (IT + 1) / 2; ++i) rk[i] = 0;
   if (first_pass) {
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i)
+    for (int i = 0; i < IT; ++i)
       if (wb + i * 32 < n)
         rk[i >> 1] |= atomicAdd(&wc[dg.operator()<kByte>(key[i])], 1u) << (16 * (i & 1));
   } else {
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i) {
+    for (int i = 0; i < IT; ++i) {
       const bool ok = wb + i * 32 < n;
       const uint32_t d = ok ? dg.operator()<kByte>(key[i]) : 0xFFFFFFFFu;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -523,77 +581,98 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K>& S, const K (&key)[kIte
       __syncwarp();
     }
   }
-  if (ahead) {
+  __syncthreads();
+  // per digit: per-warp prefixes and the tile's count; the digit's start in
+  // the tile (a scan over the digits) and its output offset; the running
+  // count moves on
+  uint32_t cnt[D::DPT];
+  uint32_t tsum = 0;
+  if (D::owns()) {
 #pragma unroll
-    for (int i = 0; i < kItemsC; ++i)
-      if (wb + i * 32 < n) atomicAdd(&S.nxt[dn.operator()<kByte>(key[i])], 1u);
+    for (int j = 0; j < D::DPT; ++j) {
+      const uint32_t d = D::first() + j;
+      uint32_t c = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const uint32_t x = S.wbase[w][d];
+        S.wbase[w][d] = c;
+        c += x;
+      }
+      cnt[j] = c;
+      tsum += c;
+    }
+  }
+  uint32_t ts = cta_excl_scan32<NT>(tsum, S.s_scan);
+  if (D::owns()) {
+#pragma unroll
+    for (int j = 0; j < D::DPT; ++j) {
+      const uint32_t d = D::first() + j;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) S.wbase[w][d] += ts;
+      const uint32_t r = S.run[d];
+      S.gdst[d] = r - ts;
+      S.run[d] = r + cnt[j];
+      ts += cnt[j];
+    }
   }
   __syncthreads();
-  // thread d: per-warp prefixes, the tile's count, its start in the tile and
-  // its output offset; the running count moves on
-  const uint32_t d = threadIdx.x;
-  uint32_t cnt = 0;
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) {
-    const uint32_t c = S.wbase[w][d];
-    S.wbase[w][d] = cnt;
-    cnt += c;
-  }
-  unsigned long long tot;
-  const uint32_t ts = (uint32_t)block_excl_scan((unsigned long long)cnt, S.s_scan, &tot);
-#pragma unroll
-  for (int w = 0; w < kWarps; ++w) S.wbase[w][d] += ts;
-  const uint32_t r = S.run[d];
-  S.gdst[d] = r - ts;
-  S.run[d] = r + cnt;
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < kItemsC; ++i)
+  for (int i = 0; i < IT; ++i)
     if (wb + i * 32 < n)
       S.sk[wc[dg.operator()<kByte>(key[i])] + ((rk[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = key[i];
   __syncthreads();
 }
 
-template <typename K, bool kByte>
-__device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K>& S, uint32_t k) {
+template <typename K, bool kByte, int NT, int IT>
+__device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint32_t k) {
+  using D = SegDig<NT>;
+  constexpr uint32_t TILE = NT * IT;
   const Seg& sg = st0->segs[k];
   const unsigned long long in_off = sg.in_off, out_off = sg.out_off;
-  const uint32_t n = (uint32_t)sg.n, nt = sg.ntiles, passes = st0->passes, dbits = st0->dbits;
-  const uint32_t d = threadIdx.x;
+  const uint32_t n = (uint32_t)sg.n, passes = st0->passes, dbits = st0->dbits;
+  const uint32_t nt = (n + TILE - 1) / TILE;
   for (uint32_t p = 0; p < passes; ++p) {
     const Stage* sp = st0 + p;
     const K* in = (const K*)sp->in + in_off;
     K* out = (K*)sp->out + out_off;
-    const Digit dg(sp->shift, dbits), dn(sp->shift + dbits, dbits);
-    const bool ahead = p + 1 < passes;
-    K key[kItemsC];
-    seg_load<K>(in, min(n, (uint32_t)kTileC), key);
-    // the segment's count of digit d in this pass: the histogram kernel's
-    // (first pass) or the previous pass's
-    const uint32_t c = p == 0 ? (uint32_t)st0->hist[(unsigned long long)k * passes * kRadix + d]
-                              : S.nxt[d];
-    unsigned long long tot;
-    S.run[d] = (uint32_t)block_excl_scan((unsigned long long)c, S.s_scan, &tot);
-    S.nxt[d] = 0;
-    for (uint32_t j = 0; j < nt; ++j) {
-      const uint32_t tn = min(n - j * (uint32_t)kTileC, (uint32_t)kTileC);
-      seg_rank_tile<K, kByte>(S, key, tn, dg, dn, p == 0, ahead);
-      if (j + 1 < nt) {  // the next tile's loads fly during this tile's stores
-        const uint32_t nn = min(n - (j + 1) * (uint32_t)kTileC, (uint32_t)kTileC);
-        seg_load<K>(in + (unsigned long long)(j + 1) * kTileC, nn, key);
-      }
-      K* o = out;  // offsets are from the segment's start
-      if (tn == (uint32_t)kTileC) {
+    const Digit dg(sp->shift, dbits);
+    K key[IT];
+    seg_load<K, NT, IT>(in, min(n, TILE), key);
+    // the segment's count of each digit in this pass (the histogram kernel
+    // counted every pass); their scan starts the running counts
+    uint32_t c[D::DPT], csum = 0;
+    if (D::owns()) {
 #pragma unroll
-        for (int e = 0; e < kItemsC; ++e) {
-          const uint32_t i = threadIdx.x + e * kThreads;
+      for (int j = 0; j < D::DPT; ++j) {
+        c[j] = (uint32_t)st0->hist[((unsigned long long)k * passes + p) * kRadix + D::first() + j];
+        csum += c[j];
+      }
+    }
+    uint32_t hs = cta_excl_scan32<NT>(csum, S.s_scan);
+    if (D::owns()) {
+#pragma unroll
+      for (int j = 0; j < D::DPT; ++j) {
+        S.run[D::first() + j] = hs;
+        hs += c[j];
+      }
+    }
+    __syncthreads();
+    for (uint32_t j = 0; j < nt; ++j) {
+      const uint32_t tn = min(n - j * TILE, TILE);
+      seg_rank_tile<K, kByte, NT, IT>(S, key, tn, dg, p == 0);
+      if (j + 1 < nt)  // the next tile's loads fly during this tile's stores
+        seg_load<K, NT, IT>(in + (unsigned long long)(j + 1) * TILE, min(n - (j + 1) * TILE, TILE), key);
+      if (tn == TILE) {
+#pragma unroll
+        for (int e = 0; e < IT; ++e) {
+          const uint32_t i = threadIdx.x + e * NT;
           const K v = S.sk[i];
-          o[S.gdst[dg.operator()<kByte>(v)] + i] = v;
+          out[S.gdst[dg.operator()<kByte>(v)] + i] = v;  // offsets are from the segment's start
         }
       } else {
-        for (uint32_t i = threadIdx.x; i < tn; i += kThreads) {
+        for (uint32_t i = threadIdx.x; i < tn; i += NT) {
           const K v = S.sk[i];
-          o[S.gdst[dg.operator()<kByte>(v)] + i] = v;
+          out[S.gdst[dg.operator()<kByte>(v)] + i] = v;
         }
       }
     }
@@ -602,14 +681,14 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K>& S, uint32_t k) 
 }
 
 template <typename K, bool kByte>
-__global__ void __launch_bounds__(kThreads, 4) k_sort_seg(Stage* st0) {
-  __shared__ SegSmem<K> S;
+__global__ void __launch_bounds__(kSegNT, kSegMinBlocks) k_sort_seg(Stage* st0) {
+  __shared__ SegSmem<K, kSegNT, kSegIT> S;
   if (*(volatile uint32_t*)&st0->ctl->abort) return;
   if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;  // the lookback passes sort it
   for (;;) {
     const uint32_t k = seg_claim(st0, &S.s_k);
     if (k == 0xFFFFFFFFu) return;
-    seg_sort<K, kByte>(st0, S, k);
+    seg_sort<K, kByte, kSegNT, kSegIT>(st0, S, k);
   }
 }
 
@@ -1203,8 +1282,8 @@ void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits) {
 }
 template <typename K>
 void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits) {
-  if (dbits == 8) k_sort_seg<K, true><<<grid, kThreads, 0, s>>>(st0);
-  else k_sort_seg<K, false><<<grid, kThreads, 0, s>>>(st0);
+  if (dbits == 8) k_sort_seg<K, true><<<grid, kSegNT, 0, s>>>(st0);
+  else k_sort_seg<K, false><<<grid, kSegNT, 0, s>>>(st0);
 }
 template <typename K>
 void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
@@ -1233,11 +1312,11 @@ void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaSt
 // largest shared-memory carveout: with the default split the SM would host
 // fewer CTAs than its registers allow.
 template <typename F>
-int occupancy_of(F kern) {
+int occupancy_of(F kern, int threads = kThreads) {
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, 0);
   return b;
 }
 
@@ -1250,7 +1329,7 @@ int occupancy_sort(int which) {
     case 3: return occupancy_of(k_merge<K>);
     case 4: return occupancy_of(k_diff_merge<K, FuseTile<K>::T>);
     case 5: return occupancy_of(k_diff_merge<K, FuseTile<K>::T / 2>);
-    case 6: return occupancy_of(k_sort_seg<K, true>);
+    case 6: return occupancy_of(k_sort_seg<K, true>, kSegNT);
     default: return 0;
   }
 }
