@@ -46,6 +46,10 @@ def _load():
                                        ctypes.c_int, u64pp, szp,
                                        ctypes.POINTER(ctypes.c_uint64),
                                        ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, u32p]
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.oracle_tc_reach.restype = ctypes.c_int
+        lib.oracle_tc_reach.argtypes = [u32p, u32p, ctypes.c_size_t, ctypes.c_int, u64p, u32p,
+                                        u64p, ctypes.c_size_t, szp, u64p]
         lib.oracle_triangles.restype = ctypes.c_uint64
         lib.oracle_triangles.argtypes = [u32p, u32p, ctypes.c_size_t, ctypes.c_int]
         lib.oracle_free.restype = None
@@ -135,3 +139,40 @@ def oracle_triangles(src, dst, n_threads: int = 1) -> int:
     src, dst = _u32(src), _u32(dst)
     assert src.shape == dst.shape
     return int(lib.oracle_triangles(_ptr32(src), _ptr32(dst), src.shape[0], int(n_threads)))
+
+
+def oracle_tc_reach(src, dst, n_threads: int = 1, log_cap: int = 4096):
+    """TC by reachability (breadth-first search from every source): closure
+    size, iterations, the Delta-size log and the digest of the sorted closure
+    (see digest_keys), without materialising the closure."""
+    lib = _load()
+    s, d = _u32(src), _u32(dst)
+    n = ctypes.c_uint64(0)
+    it = ctypes.c_uint32(0)
+    log = np.zeros(log_cap, dtype=np.uint64)
+    nl = ctypes.c_size_t(0)
+    dg = ctypes.c_uint64(0)
+    rc = lib.oracle_tc_reach(_ptr32(s), _ptr32(d), s.shape[0], n_threads, ctypes.byref(n),
+                             ctypes.byref(it), log.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                             log_cap, ctypes.byref(nl), ctypes.byref(dg))
+    if rc != 0:
+        raise RuntimeError(f"oracle_tc_reach failed: {rc}")
+    return int(n.value), int(it.value), log[: min(nl.value, log_cap)].copy(), int(dg.value)
+
+
+_PHI = np.uint64(0x9E3779B97F4A7C15)
+
+
+def digest_keys(keys) -> int:
+    """Digest of a sorted packed-key array: sum over i of mix64(key_i + i * phi)
+    mod 2^64, mix64 = the SplitMix64 output function (Steele, Lea, Flood 2014)."""
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    tot = 0
+    with np.errstate(over="ignore"):
+        for a in range(0, k.shape[0], 1 << 24):
+            z = k[a:a + (1 << 24)] + np.arange(a, a + min(1 << 24, k.shape[0] - a), dtype=np.uint64) * _PHI
+            z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            z = z ^ (z >> np.uint64(31))
+            tot = (tot + int(z.sum(dtype=np.uint64))) & 0xFFFFFFFFFFFFFFFF
+    return tot

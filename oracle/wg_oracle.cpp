@@ -32,6 +32,19 @@
 // oracle_triangles counts the tuples of the non-recursive triangle rule
 // (Sec. Generalization, "Triangle Counting") with the same range lookup.
 //
+// oracle_tc_reach is TC by its plain definition instead of the loop: (x, z) is
+// in T exactly when a walk of length >= 1 leads from x to z (the least
+// relation closed under the two rules of Sec. Background), found by a
+// breadth-first search from every source.  The semi-naive loop adds the pairs
+// at shortest walk length k+1 in its iteration k, so the per-length counts are
+// the Delta sizes and the longest shortest walk is the iteration count.  It
+// reports the closure size, those counts and a digest of the sorted closure
+// without storing it (the batched and served benchmarks check every result
+// this way): digest = sum over i of mix64(key_i + i * 0x9E3779B97F4A7C15)
+// mod 2^64, where key_i is the i-th packed tuple in sorted order and mix64 is
+// the output function of SplitMix64 (Steele, Lea, Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014).
+//
 // oracle_tc_rows runs the same five steps on the rows T(x, .) of chosen
 // sources x, one row at a time: the TC recursive rule never changes the first
 // component, so row x of T, and row x of every Delta^i, depend only on row x of
@@ -167,6 +180,87 @@ uint64_t triangles(const std::vector<Key>& E, int n_threads) {
   return n;
 }
 
+inline uint64_t mix64(uint64_t z) {  // SplitMix64 output function
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// TC by reachability.  Vertices are the distinct ids in increasing order; a
+// breadth-first search from each source x lists the z reachable by a walk of
+// length >= 1 with their shortest walk length.  Pass 1 counts each source's
+// row; pass 2 repeats the searches and digests each row at its offset in the
+// sorted closure.  Sources are spread over n_threads std::threads.
+struct Reach {
+  uint64_t n = 0, digest = 0;
+  std::vector<uint64_t> by_len;  // by_len[d - 1] = pairs at shortest walk length d
+};
+
+Reach tc_reach(const std::vector<Key>& E, int n_threads) {
+  std::vector<uint32_t> ids;
+  for (Key k : E) { ids.push_back(src_of(k)); ids.push_back(dst_of(k)); }
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  const size_t nv = ids.size();
+  auto rank = [&](uint32_t v) { return uint32_t(std::lower_bound(ids.begin(), ids.end(), v) - ids.begin()); };
+  std::vector<uint32_t> off(nv + 1, 0), adj(E.size());
+  for (Key k : E) off[rank(src_of(k)) + 1]++;
+  for (size_t v = 0; v < nv; ++v) off[v + 1] += off[v];
+  for (size_t i = 0; i < E.size(); ++i) adj[i] = rank(dst_of(E[i]));  // E sorted: rows in order
+  if (n_threads < 1) n_threads = 1;
+  std::vector<uint64_t> row(nv, 0), rowoff(nv + 1, 0);
+  std::vector<std::vector<uint64_t>> lens(n_threads);
+  std::vector<uint64_t> part(n_threads, 0);
+  auto search = [&](uint32_t x, std::vector<int32_t>& dist, std::vector<uint32_t>& q) {
+    size_t h = 0;
+    q.clear();
+    for (uint32_t j = off[x]; j < off[x + 1]; ++j)
+      if (dist[adj[j]] < 0) { dist[adj[j]] = 1; q.push_back(adj[j]); }
+    while (h < q.size()) {
+      const uint32_t y = q[h++];
+      for (uint32_t j = off[y]; j < off[y + 1]; ++j)
+        if (dist[adj[j]] < 0) { dist[adj[j]] = dist[y] + 1; q.push_back(adj[j]); }
+    }
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1)
+      for (size_t v = 0; v < nv; ++v) rowoff[v + 1] = rowoff[v] + row[v];
+    std::vector<std::thread> pool;
+    for (int t = 0; t < n_threads; ++t) {
+      pool.emplace_back([&, t] {
+        std::vector<int32_t> dist(nv, -1);
+        std::vector<uint32_t> q;
+        for (size_t x = size_t(t); x < nv; x += size_t(n_threads)) {
+          search(uint32_t(x), dist, q);
+          if (pass == 0) {
+            row[x] = q.size();
+            for (uint32_t z : q) {
+              const size_t d = size_t(dist[z]);
+              if (lens[t].size() < d) lens[t].resize(d, 0);
+              lens[t][d - 1]++;
+            }
+          } else {
+            std::sort(q.begin(), q.end());  // ranks follow ids: the row's order
+            uint64_t i = rowoff[x], h = 0;
+            for (uint32_t z : q) h += mix64(pack(ids[x], ids[z]) + (i++) * 0x9E3779B97F4A7C15ull);
+            part[t] += h;
+          }
+          for (uint32_t z : q) dist[z] = -1;
+        }
+      });
+    }
+    for (auto& th : pool) th.join();
+  }
+  Reach r;
+  r.n = rowoff[nv];
+  for (uint64_t h : part) r.digest += h;
+  for (auto& l : lens) {
+    if (r.by_len.size() < l.size()) r.by_len.resize(l.size(), 0);
+    for (size_t d = 0; d < l.size(); ++d) r.by_len[d] += l[d];
+  }
+  return r;
+}
+
 int export_result(const Result& r, uint64_t** keys, size_t* n_keys, uint64_t** log,
                   size_t* n_log, uint32_t* iters) {
   *n_keys = r.full.size();
@@ -240,6 +334,25 @@ int oracle_tc_rows(const uint32_t* src, const uint32_t* dst, size_t n, const uin
     mx = std::max(mx, r.iters);
   }
   *max_iters_out = mx;
+  return 0;
+}
+
+// TC by reachability (see tc_reach): *n_tuples, *iters (the index of the
+// first empty Delta, as oracle_tc reports it), log[0..*n_log) = |Delta^0| ..
+// |Delta^iters| (at most log_cap entries are written) and the digest of the
+// sorted closure.
+int oracle_tc_reach(const uint32_t* src, const uint32_t* dst, size_t n, int n_threads,
+                    uint64_t* n_tuples, uint32_t* iters, uint64_t* log, size_t log_cap,
+                    size_t* n_log, uint64_t* digest) {
+  const Reach r = tc_reach(edge_set(src, dst, n), n_threads);
+  *n_tuples = r.n;
+  *digest = r.digest;
+  // Delta^k = pairs at shortest walk length k + 1; the loop stops at the
+  // first empty one (at least iteration 1)
+  const size_t it = std::max<size_t>(1, r.by_len.size());
+  *iters = uint32_t(it);
+  *n_log = it + 1;
+  for (size_t k = 0; k <= it && k < log_cap; ++k) log[k] = k < r.by_len.size() ? r.by_len[k] : 0;
   return 0;
 }
 
