@@ -41,6 +41,9 @@ WORKLOADS = {
     "tc_er_1k": dict(kind="tc", desc="TC, directed Erdos-Renyi 1,000 nodes, 3,000 edges, seed 1"),
     "tc_rmat15_100k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^15 nodes, 100k distinct "
                                            "DAG edges, seed 2 (profiling-size case)"),
+    "tc_rmat19_400k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^19 nodes, 400k distinct "
+                                           "DAG edges, seed 2 (124,568 vertices: 17-bit ranks, "
+                                           "64-bit keys)"),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -342,6 +345,15 @@ def autotune_ctx(ctx, rels, kind=None):
     return out
 
 
+def load_mix_golden(name, count):
+    """{query index: oracle figures} from tests/golden/<name> (empty if absent)."""
+    p = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(p):
+        return {}
+    qs = json.load(open(p))["queries"]
+    return {i: q for i, q in enumerate(qs[:count])}
+
+
 def _pct(xs, p):
     xs = sorted(xs)
     if not xs:
@@ -356,7 +368,6 @@ def run_batch(args):
     One step = the whole set of queries in each arm."""
     import torch
 
-    import oracle
     from paper_2607_17571_gb300 import inputs as I
     from paper_2607_17571_gb300 import wg
 
@@ -376,16 +387,25 @@ def run_batch(args):
         if not args.no_autotune:
             tuned.update(autotune_ctx(ctx, rels))
     tuned = {}
-    # parity sample: the smallest queries, checked against the oracle
-    order = sorted(range(len(sizes)), key=lambda i: sizes[i][0])
-    sample = set(order[:: max(1, len(order) // 24)][:24])
-    want = {i: oracle.oracle_tc(graphs[i].src, graphs[i].dst) for i in sample}
+    # every query is checked against the oracle's closure size, iteration
+    # count and digest of the sorted result (tests/golden/batch4096.json,
+    # written by tests/golden/make_mix_golden.py, which calls only oracle/);
+    # the device digests the result (wg_result_digest) so nothing is copied
+    want = load_mix_golden("batch4096.json", len(graphs))
+
+    def check(i, h, st):
+        g = want.get(i)
+        if g is None:
+            return 0
+        return int(st.n_tuples != g["n_tuples"] or st.iterations != g["iterations"]
+                   or h.digest() != int(g["digest"]))
 
     def batched():
         t0 = time.perf_counter()
         hs = ctx.submit([(wg.WG_TC, r) for r in rels])
         idx = {h.id: i for i, h in enumerate(hs)}
         lat, tuples, launches, bad = [0.0] * len(hs), 0, 0, 0
+        pending = []
         left = len(hs)
         while left:
             ctx.serve_step(args.batch_iters)
@@ -397,25 +417,28 @@ def run_batch(args):
                 if st.state != wg.WG_DONE:
                     bad += 1
                 tuples += st.n_tuples
-                if i in want and not np.array_equal(h.result(), want[i].keys):
-                    bad += 1
-                h.free()
+                pending.append((i, h, st))
                 left -= 1
-        return time.perf_counter() - t0, lat, tuples, bad
+        el = time.perf_counter() - t0
+        for i, h, st in pending:  # checked after the timed region
+            bad += check(i, h, st)
+            h.free()
+        return el, lat, tuples, bad
 
     def plain():
         t0 = time.perf_counter()
-        lat, tuples, launches, bad = [], 0, 0, 0
+        lat, tuples, launches, bad, chk = [], 0, 0, 0, 0.0
         for i, r in enumerate(rels):
             q = ctx.tc(r)
             st = q.wait()
-            lat.append((time.perf_counter() - t0) * 1e3)
+            lat.append((time.perf_counter() - t0 - chk) * 1e3)
             tuples += st.n_tuples
             launches += st.gpu_launches
-            if i in want and not np.array_equal(q.result(), want[i].keys):
-                bad += 1
+            c0 = time.perf_counter()  # the check is not part of the loop's time
+            bad += check(i, q, st)
+            chk += time.perf_counter() - c0
             q.free()
-        return time.perf_counter() - t0, lat, tuples, bad, launches
+        return time.perf_counter() - t0 - chk, lat, tuples, bad, launches
 
     # each arm: its own context, warmed up (engines, graphs, pools), then timed
     open_ctx()
@@ -425,14 +448,20 @@ def run_batch(args):
         h.free()
     ctx.take_completed()
     torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
     tb, lb, nb, bad_b = batched()
+    clk_b = clocks.stop()
     open_ctx()
     for r in rels[:4]:
         q = ctx.tc(r)
         q.wait()
         q.free()
     torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
     tp, lp, npl, bad_p, launches = plain()
+    clk_p = clocks.stop()
     n = len(rels)
     line = {"metric": "batched TC fixpoints: queries/s", "value": n / tb, "unit": "queries/s",
             "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(tb * 1e3, 1),
@@ -444,11 +473,14 @@ def run_batch(args):
                        "iterations_per_launch": args.batch_iters,
                        "tiles": tuned or "compiled defaults"},
             "batched": {"seconds": round(tb, 3), "queries_per_s": n / tb, "tuples_per_s": nb / tb,
-                        "p50_ms": _pct(lb, 50), "p99_ms": _pct(lb, 99), "parity_failures": bad_b},
+                        "p50_ms": _pct(lb, 50), "p99_ms": _pct(lb, 99), "parity_failures": bad_b,
+                        "clocks": clk_b},
             "plain_loop": {"seconds": round(tp, 3), "queries_per_s": n / tp,
                            "tuples_per_s": npl / tp, "p50_ms": _pct(lp, 50), "p99_ms": _pct(lp, 99),
-                           "parity_failures": bad_p, "gpu_launches": launches},
-            "parity_sample": len(want), "same_total": nb == npl}
+                           "parity_failures": bad_p, "gpu_launches": launches, "clocks": clk_p},
+            "parity_checked": f"{len(want)} of {n} queries: closure size, iterations and "
+                              "result digest against the oracle",
+            "same_total": nb == npl, "clocks": clk_b}
     print(json.dumps(line))
     for r in rels:
         r.free()
@@ -654,7 +686,11 @@ def run_serve(args):
     inputs.serve_request), served under a fixed device-memory budget: the
     continuous-batching server (requests join the running set at iteration
     boundaries) against the plain loop that runs one query at a time in
-    arrival order.  The same request pool is replayed at every rate."""
+    arrival order.  Each rate offers --n-arrivals arrivals; arrival a asks
+    for request a % pool of a pool of --n-requests distinct seeded requests
+    (relations resident); each arm stops after --arm-seconds.  Every completed
+    request is checked against the oracle's figures (closure size,
+    iterations, result digest), outside the timed region."""
     import torch
 
     from paper_2607_17571_gb300 import inputs as I
@@ -662,10 +698,22 @@ def run_serve(args):
 
     torch.cuda.set_device(0)
     rates = [float(x) for x in args.rates.split(",")]
-    reqs = [I.serve_request(r) for r in range(args.n_requests)]
+    reqs = [I.serve_request(r) for r in range(args.n_requests)]  # the pool
     kinds = [wg.WG_TC if k == "tc" else wg.WG_SG for k, _ in reqs]
     small = sorted(range(len(reqs)), key=lambda i: len(reqs[i][1]))[:6]
+    # every completed request is checked against the oracle's closure size,
+    # iteration count and result digest (tests/golden/serve_pool.json, written
+    # by tests/golden/make_mix_golden.py, which calls only oracle/)
+    want = load_mix_golden("serve_pool.json", len(reqs))
+    npool = len(reqs)
     ctx, rels = None, None
+
+    def check(i, h, st):
+        g = want.get(i)
+        if g is None:
+            return 0
+        return int(st.n_tuples != g["n_tuples"] or st.iterations != g["iterations"]
+                   or h.digest() != int(g["digest"]))
 
     def single(i):
         return (ctx.tc if kinds[i] == wg.WG_TC else ctx.sg)(rels[i])
@@ -692,81 +740,98 @@ def run_serve(args):
                 q.free()
 
     def served(arr):
+        # arrival a asks for pool request a % npool
         n = len(arr)
-        lat, ok, rej, tuples = [None] * n, 0, 0, 0
+        lat, ok, rej, tuples, bad, chk = [None] * n, 0, 0, 0, 0, 0.0
         idx, nxt, done = {}, 0, 0
         t0 = time.perf_counter()
-        while done < n and time.perf_counter() - t0 < args.arm_seconds:
-            now = time.perf_counter() - t0
+        while done < n and time.perf_counter() - t0 - chk < args.arm_seconds:
+            now = time.perf_counter() - t0 - chk
             new = []
             while nxt < n and arr[nxt] <= now:
                 new.append(nxt)
                 nxt += 1
             if new:
-                for i, h in zip(new, ctx.submit([(kinds[i], rels[i]) for i in new])):
-                    idx[h.id] = (i, h)
+                for a, h in zip(new, ctx.submit([(kinds[a % npool], rels[a % npool]) for a in new])):
+                    idx[h.id] = (a, h)
             running = ctx.serve_step(args.serve_iters)
-            t = time.perf_counter() - t0
+            t = time.perf_counter() - t0 - chk
             for qid in ctx.take_completed():
-                i, h = idx.pop(qid)
+                a, h = idx.pop(qid)
                 st = h.poll()
-                lat[i] = (t - arr[i]) * 1e3
+                lat[a] = (t - arr[a]) * 1e3
                 if st.state == wg.WG_DONE:
                     ok += 1
                     tuples += st.n_tuples
+                    c0 = time.perf_counter()  # the check is not part of the served time
+                    bad += check(a % npool, h, st)
+                    chk += time.perf_counter() - c0
                 else:
                     rej += 1
                 h.free()
                 done += 1
             if running == 0 and nxt < n:
-                time.sleep(max(0.0, min(0.002, arr[nxt] - (time.perf_counter() - t0))))
-        el = time.perf_counter() - t0
+                time.sleep(max(0.0, min(0.002, arr[nxt] - (time.perf_counter() - t0 - chk))))
+        el = time.perf_counter() - t0 - chk
         good = [x for x in lat if x is not None]
         unfinished = n - done  # closing the context waits only for the launch in flight
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
                     p50_ms=_pct(good, 50), p99_ms=_pct(good, 99), completed=ok, rejected=rej,
-                    unfinished_in_time=unfinished)
+                    unfinished_in_time=unfinished, parity_failures=bad)
 
     def plain(arr):
         n = len(arr)
-        lat, ok, rej, tuples = [], 0, 0, 0
+        lat, ok, rej, tuples, bad, chk = [], 0, 0, 0, 0, 0.0
         t0 = time.perf_counter()
-        for i in range(n):
-            if time.perf_counter() - t0 > args.arm_seconds:
+        for a in range(n):
+            if time.perf_counter() - t0 - chk > args.arm_seconds:
                 break
-            wait = arr[i] - (time.perf_counter() - t0)
+            wait = arr[a] - (time.perf_counter() - t0 - chk)
             if wait > 0:
                 time.sleep(wait)
             q = None
             try:  # a query whose first pools do not fit fails at the call
-                q = single(i)
+                q = single(a % npool)
                 st = q.wait()
                 ok += 1
                 tuples += st.n_tuples
             except wg.WgError:
                 rej += 1
-            lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
+            lat.append((time.perf_counter() - t0 - chk - arr[a]) * 1e3)
             if q is not None:
+                c0 = time.perf_counter()
+                bad += check(a % npool, q, st)
+                chk += time.perf_counter() - c0
                 q.free()
-        el = time.perf_counter() - t0
+        el = time.perf_counter() - t0 - chk
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
                     p50_ms=_pct(lat, 50), p99_ms=_pct(lat, 99), completed=ok, rejected=rej,
-                    unfinished_in_time=n - ok - rej)
+                    unfinished_in_time=n - ok - rej, parity_failures=bad)
 
     points = []
     for rate in rates:
-        arr = I.poisson_arrivals(len(reqs), rate, seed=5)
+        arr = I.poisson_arrivals(args.n_arrivals, rate, seed=5)
         open_ctx(True)
+        clocks = Clocks(0)
+        clocks.start()
         b = served(arr)
+        b["clocks"] = clocks.stop()
         open_ctx(False)
+        clocks = Clocks(0)
+        clocks.start()
         p = plain(arr)
+        p["clocks"] = clocks.stop()
         points.append({"rate_qps": rate, "served": b, "plain_loop": p})
     best = max(points, key=lambda x: x["served"]["queries_per_s"])
     line = {"metric": "served TC/SG queries/s (p50/p99 latency)",
             "value": best["served"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
             "steps": len(rates), "warmup": 1, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64", "data": "synthetic",
-            "config": {"workload": "serve", "requests_per_rate": len(reqs),
+            "config": {"workload": "serve", "arrivals_per_rate": args.n_arrivals,
+                       "request_pool": npool, "arm_seconds_cap": args.arm_seconds,
+                       "parity": f"every completed request: closure size, iterations and result "
+                                 f"digest against the oracle ({len(want)} of {npool} pool "
+                                 f"requests have oracle figures)",
                        "mix": "TC 75% (70% ER batch-mix sizes, 30% R-MAT DAG 1e4..1e6 edges), "
                               "SG 25% (forests, batch-mix sizes)",
                        "budget_gb": args.budget_gb, "iterations_per_round": args.serve_iters},
@@ -793,7 +858,10 @@ def main():
     ap.add_argument("--n-queries", type=int, default=4096)
     ap.add_argument("--batch-iters", type=int, default=4)
     ap.add_argument("--rates", default="100,200,500,1000,2000,5000")
-    ap.add_argument("--n-requests", type=int, default=80)
+    ap.add_argument("--n-requests", type=int, default=500,
+                    help="served mix: distinct requests in the pool")
+    ap.add_argument("--n-arrivals", type=int, default=10000,
+                    help="served mix: arrivals per rate (arrival a asks for pool request a %% pool)")
     ap.add_argument("--budget-gb", type=float, default=60.0)
     ap.add_argument("--serve-iters", type=int, default=4)
     ap.add_argument("--arm-seconds", type=float, default=60.0,

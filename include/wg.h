@@ -222,6 +222,15 @@ int wg_wait(wg_ctx* ctx, wg_query q, uint64_t timeout_us);
 int wg_result_copy(wg_ctx* ctx, wg_query q, uint64_t* keys, size_t cap, size_t* n_out);
 /* Same into a DEVICE buffer (stream-ordered; synchronises the stream). */
 int wg_result_copy_device(wg_ctx* ctx, wg_query q, uint64_t* d_keys, size_t cap, size_t* n_out);
+/* Digest of the result without copying it: sum over i of
+ * mix64(keys[i] + i * 0x9E3779B97F4A7C15) mod 2^64, keys[i] the i-th sorted
+ * packed tuple as wg_result_copy returns it and mix64 the output function of
+ * SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).  Computed on the device; a
+ * caller compares it with the same sum over a reference result (the
+ * benchmarks check every batched and served result this way).  The paper has
+ * no counterpart.  Synchronous.  Errors: WG_E_INVAL, WG_E_NOT_READY or the
+ * query's own error, WG_E_NOMEM / WG_E_BUDGET, WG_E_CUDA. */
+int wg_result_digest(wg_ctx* ctx, wg_query q, uint64_t* digest);
 /* Per-iteration delta sizes |Delta^0|, ..., |Delta^iterations| (last entry 0
  * at the fixpoint) into a HOST buffer; WG_E_CAPACITY when cap is too small. */
 int wg_result_iters(wg_ctx* ctx, wg_query q, uint64_t* delta_sizes, size_t cap, size_t* n_out);

@@ -1553,10 +1553,16 @@ static int batch_round(wg_ctx* c, int cls, uint32_t iters, bool wait_launch, boo
   }
   if (E->grow_wait) return WG_OK;
   TRY(batch_admit<K>(c, cls));
-  bool any = false;
-  for (const Inst& I : E->hi) any |= I.state == INST_ACTIVE;
-  if (any) {
-    TRY(E->launch(iters, WG_LOOP_DEVICE));
+  uint32_t active = 0;
+  for (const Inst& I : E->hi) active += I.state == INST_ACTIVE;
+  if (active) {
+    // a lone query (nothing queued, nothing else running anywhere) runs to
+    // its fixpoint in this one launch, as the plain loop would: capping its
+    // iterations only adds host round trips while nobody waits to join
+    bool lone = active == 1 && c->pending.empty() && !solo_running(c);
+    for (auto& kv : c->batch)
+      if (lone && kv.first != cls && batch_holds_work_any(c, kv.first)) lone = false;
+    TRY(E->launch(lone ? 0xFFFFFFFFu : iters, WG_LOOP_DEVICE));
     *progressed = true;
   }
   return WG_OK;
@@ -2157,6 +2163,38 @@ static int result_common(wg_ctx* c, wg_query id, uint64_t* keys, size_t cap, siz
   if (q->n_tuples && !keys) return set_err(WG_E_INVAL, "keys is NULL");
   return q->rel->kb == 4 ? copy_result<uint32_t>(c, q, (unsigned long long*)keys, host)
                          : copy_result<unsigned long long>(c, q, (unsigned long long*)keys, host);
+}
+
+int wg_result_digest(wg_ctx* c, wg_query id, uint64_t* digest) {
+  if (!c || !digest) return set_err(WG_E_INVAL, "bad argument");
+  Query* q = find_q(c, id);
+  if (!q) return set_err(WG_E_INVAL, "no such query");
+  if (q->state != WG_DONE) return set_err(q->state == WG_FAILED ? q->error : WG_E_NOT_READY, "result not ready");
+  *digest = 0;
+  if (!q->n_tuples) return WG_OK;
+  DBuf acc;
+  TRY(acc.get(c, 8));
+  int rc = WG_OK;
+  unsigned long long h = 0;
+  if (cudaMemsetAsync(acc.p, 0, 8, c->stream) != cudaSuccess) {
+    rc = set_err(WG_E_CUDA, "digest clear");
+  } else {
+    const uint32_t* V = (const uint32_t*)q->rel->V.p;
+    if (q->rel->kb == 4)
+      launch_result_digest<uint32_t>((const uint32_t*)q->res_ptr, q->n_tuples, q->rel->w, V,
+                                     (unsigned long long*)acc.p, grid_of(c, 8), c->stream);
+    else
+      launch_result_digest<unsigned long long>((const unsigned long long*)q->res_ptr, q->n_tuples,
+                                               q->rel->w, V, (unsigned long long*)acc.p,
+                                               grid_of(c, 8), c->stream);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, acc.p, 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      rc = set_err(WG_E_CUDA, "digest");
+  }
+  acc.release(c);
+  *digest = h;
+  return rc;
 }
 
 int wg_result_copy(wg_ctx* c, wg_query q, uint64_t* keys, size_t cap, size_t* n_out) {

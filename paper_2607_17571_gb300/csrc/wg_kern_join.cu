@@ -977,6 +977,33 @@ __global__ void k_result_map(const K* F, unsigned long long n, uint32_t w, const
   }
 }
 
+// Digest of a result: sum over i of mix64(key_i + i * phi) mod 2^64, key_i =
+// (id(x) << 32) | id(y) of the i-th sorted tuple, mix64 = the SplitMix64
+// output function (Steele, Lea, Flood 2014).  `first` is the index of F[0] in
+// the whole result (results are digested in chunks).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+template <typename K>
+__global__ void __launch_bounds__(256) k_result_digest(const K* F, unsigned long long n,
+                                                       unsigned long long first, uint32_t w,
+                                                       const uint32_t* V, unsigned long long* out) {
+  __shared__ unsigned long long sh[kWarps];
+  const K mask = (K)(((K)1 << w) - 1);
+  unsigned long long acc = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const K k = F[i];
+    const unsigned long long key = ((unsigned long long)V[(uint32_t)(k >> w)] << 32) | V[(uint32_t)(k & mask)];
+    acc += mix64(key + (first + i) * 0x9E3779B97F4A7C15ull);
+  }
+  unsigned long long tot;
+  block_excl_scan(acc, sh, &tot);
+  if (threadIdx.x == 0 && tot) atomicAdd(out, tot);
+}
+
 // ------------------------------------------------------------------ launchers
 // Self-test of the bounded device wait: one warp looks back, as every scan
 // stage does, for a predecessor tile whose status word is never published
@@ -1052,6 +1079,11 @@ void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint3
                        unsigned long long* out, int grid, cudaStream_t s) {
   k_result_map<K><<<grid, 256, 0, s>>>(F, n, w, V, out);
 }
+template <typename K>
+void launch_result_digest(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
+                          unsigned long long* out, int grid, cudaStream_t s) {
+  if (n) k_result_digest<K><<<grid, 256, 0, s>>>(F, n, 0ull, w, V, out);
+}
 
 #define WG_INST(K)                                                                          \
   template void launch_join_count<K>(Stage*, int, cudaStream_t, uint32_t);                  \
@@ -1068,7 +1100,9 @@ void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint3
   template void launch_csr<K>(const K*, unsigned long long, uint32_t, uint32_t, uint32_t*,  \
                               uint32_t*, int, cudaStream_t);                                \
   template void launch_result_map<K>(const K*, unsigned long long, uint32_t, const uint32_t*, \
-                                     unsigned long long*, int, cudaStream_t);
+                                     unsigned long long*, int, cudaStream_t);                  \
+  template void launch_result_digest<K>(const K*, unsigned long long, uint32_t, const uint32_t*, \
+                                        unsigned long long*, int, cudaStream_t);
 WG_INST(uint32_t)
 WG_INST(unsigned long long)
 #undef WG_INST

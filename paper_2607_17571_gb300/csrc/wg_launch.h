@@ -70,5 +70,9 @@ void launch_csr(const K* E, unsigned long long ne, uint32_t nv, uint32_t w, uint
 template <typename K>
 void launch_result_map(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
                        unsigned long long* out, int grid, cudaStream_t s);
+// adds the digest of the n tuples F (ranks mapped to ids through V) to *out
+template <typename K>
+void launch_result_digest(const K* F, unsigned long long n, uint32_t w, const uint32_t* V,
+                          unsigned long long* out, int grid, cudaStream_t s);
 
 }  // namespace wg

@@ -350,6 +350,8 @@ def workload(name: str) -> EdgeList:
         return sg_forest(60_000, 40, 2.0, 0.01, seed=3)
     if name == "tc_rmat15_100k":  # a smaller skewed case (profiling captures)
         return rmat_dag(15, 100_000, seed=2)
+    if name == "tc_rmat19_400k":  # the same recipe on 2^19 nodes: ranks need 17 bits (64-bit keys)
+        return rmat_dag(19, 400_000, seed=2)
     if name == "tri_rmat16_800k":  # triangle counting: undirected, 800k directed edges
         return rmat_sym(16, 400_000, seed=6)
     raise KeyError(name)

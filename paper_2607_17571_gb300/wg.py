@@ -81,6 +81,7 @@ SIGNATURES = {
     "wg_result_copy": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_copy_device": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
     "wg_result_iters": (c_int, [c_void_p, c_uint64, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "wg_result_digest": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
     "wg_autotune": (c_int, [c_void_p, c_uint64, c_int, POINTER(wg_tune)]),
     "wg_selftest_wait_timeout": (c_int, [c_void_p]),
     "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32]),
@@ -201,6 +202,12 @@ class Query:
         _check(self.ctx.lib.wg_result_copy_device(self.ctx.h, self.id, c_void_p(out_ptr), cap,
                                                   byref(n)), "wg_result_copy_device")
         return n.value
+
+    def digest(self) -> int:
+        """wg_result_digest: the device-side digest of the sorted result."""
+        d = c_uint64()
+        _check(self.ctx.lib.wg_result_digest(self.ctx.h, self.id, byref(d)), "wg_result_digest")
+        return int(d.value)
 
     def delta_sizes(self) -> list:
         n = c_size_t()

@@ -241,3 +241,34 @@ def test_repeated_regrowth_from_tiny_pools(separate):
         for gg in (I.er_graph(900, 2700, 31), I.rmat_dag(11, 6000, 32)):
             check(c, "tc", gg.src, gg.dst, separate_stages=separate, reserve_cand=1,
                   reserve_full=1)
+
+
+def test_result_digest_matches_the_oracle(ctx):
+    # the device digest of a result equals the digest of the oracle's sorted
+    # closure (semi-naive and reachability forms), for both key widths
+    from oracle import digest_keys, oracle_tc_reach
+    for g in (I.er_graph(500, 1500, 21), I.rmat_dag(11, 5000, 22), I.cycle(40)):
+        rel = ctx.load(g.src, g.dst)
+        q = ctx.tc(rel)
+        q.wait()
+        want = oracle_tc(g.src, g.dst)
+        n, iters, log, dg = oracle_tc_reach(g.src, g.dst, n_threads=2)
+        assert q.digest() == digest_keys(want.keys) == dg
+        assert q.digest() == digest_keys(q.result())
+        q.free()
+        rel.free()
+    wide = I.er_graph(100_000, 90_000, 23)  # > 2^16 vertices: 17-bit ranks, 64-bit keys
+    rel = ctx.load(wide.src, wide.dst)
+    assert rel.info()["field_bits"] > 16
+    q = ctx.tc(rel)
+    q.wait()
+    assert q.digest() == digest_keys(oracle_tc(wide.src, wide.dst).keys)
+    q.free()
+    rel.free()
+    f = I.sg_forest(2500, 5, 2.0, 0.01, 24)
+    rel = ctx.load(f.src, f.dst)
+    q = ctx.sg(rel)
+    q.wait()
+    assert q.digest() == digest_keys(oracle_sg(f.src, f.dst).keys)
+    q.free()
+    rel.free()
