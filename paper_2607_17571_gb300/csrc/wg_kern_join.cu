@@ -227,36 +227,69 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
 }
 
 // ------------------------------------------------------------------ join emit
-// Load-balanced over output positions: a tile is kTileC consecutive
-// candidates of one instance.  The delta tuples whose slabs cover the tile --
-// from the slab owner of the tile's first candidate to that of the next
-// tile's first -- are taken in chunks of EmitWin<K>::n:
+// Load-balanced over output positions: a tile holds at most kTileC
+// consecutive candidates of one instance (plus at most kEmitGroup * kTileC
+// delta tuples, however many of their slabs are empty).  The delta tuples
+// whose slabs cover the tile -- from the slab owner of the tile's first
+// candidate to that of the next tile's first -- are taken in chunks of
+// EmitWin<K>::n:
 //  1. a chunk becomes a slab table in shared memory: tile-relative slab
 //     start and the CSR offsets the slab reads (every load of the round in
 //     flight at once);
-//  2. thread t walks the table for those of its kItemsC consecutive
-//     candidates that the chunk covers (shared memory only), then issues all
-//     their adjacency loads at once and stages the candidates.
+//  2. every non-empty slab marks its first position in an owner array of
+//     the tile's positions, and one block-wide max-scan fills in the slab of
+//     every position (slab indices grow with their starts);
+//  3. each thread takes positions tile_start + e * kThreads + lane order, so a
+//     warp reads consecutive adjacency entries of a slab and stores 32
+//     consecutive candidates: coalesced, without a staging copy.
 // Most tiles take one chunk; a long run of empty slabs (sinks) takes more.
-// The staged tile leaves with coalesced stores.
 template <typename K> struct EmitWin {
-  static constexpr int n = sizeof(K) == 4 ? 1536 : 512;  // table + staging < 48 KB
+  static constexpr int n = sizeof(K) == 4 ? 1536 : 1024;
 };
+
+// Block-wide inclusive max-scan of the owner array over [0, kTileC): each
+// thread scans its kItemsC consecutive entries, then the threads' maxima.
+__device__ __forceinline__ void owner_max_scan(uint16_t* own, uint32_t* s_w) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t b = threadIdx.x * kItemsC;
+  uint32_t v[kItemsC];
+  uint32_t m = 0;
+#pragma unroll
+  for (int e = 0; e < kItemsC; ++e) {
+    m = max(m, (uint32_t)own[b + e]);
+    v[e] = m;
+  }
+  uint32_t x = m;  // inclusive warp max-scan of the thread maxima
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= (uint32_t)o) x = max(x, y);
+  }
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  uint32_t before = 0;  // max over the earlier warps and the earlier lanes
+  for (uint32_t w = 0; w < warp; ++w) before = max(before, s_w[w]);
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, x, 1);
+  if (lane) before = max(before, prev);
+#pragma unroll
+  for (int e = 0; e < kItemsC; ++e) own[b + e] = (uint16_t)max(before, v[e]);
+}
 
 // kProbe (triangle counting, Sec. Generalization "Triangle Counting"): the
 // delta is E itself and every candidate (a, b, c) of E(a,b), E(b,c) is tested
 // for E(c,a) by binary search in c's sorted adjacency -- the binary-search
 // join probe -- and only the number of hits is kept.
 template <typename K, bool kProbe>
-__global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
+__global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
   constexpr int W = EmitWin<K>::n;
   __shared__ uint32_t s_start[W];  // slab's first candidate, relative to the tile
   __shared__ uint32_t s_x[W];      // TC: x            SG: off[x]
   __shared__ uint32_t s_a[W];      // TC: adj index of the slab's candidate 0 of the tile
                                    // SG: off[y] (recursive rule)
   __shared__ uint32_t s_d[W];      // SG: divisor that splits a slab index in two
-  __shared__ K sout[kProbe ? 1 : Padded<kTileC>::n];
+  __shared__ uint16_t s_own[kTileC];  // slab (chunk index) of each position
   __shared__ unsigned long long s_scan[kWarps];
+  __shared__ uint32_t s_w[kWarps];
   __shared__ unsigned long long s_i0, s_i1;
   __shared__ uint32_t s_r0, s_ce, s_t;
   Ctl* ctl = stp->ctl;
@@ -291,16 +324,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
     // delta tuples i0..i1: every slab before i0 ends at or before o0 and
     // every slab after i1 starts after o1
     if (stp->splits) {
-      const bool last = t == sg.tile0 + sg.ntiles - 1;
       if (threadIdx.x == 0) s_i0 = stp->splits[t];
-      if (threadIdx.x == 32) s_i1 = last ? sg.n - 1 : stp->splits[t + 1];
+      if (threadIdx.x == 32) s_i1 = last_tile ? sg.n - 1 : stp->splits[t + 1];
     } else {
       if (threadIdx.x == 0) s_i0 = upper_bound_k(P, sg.n, o0) - 1;
       if (threadIdx.x == 32) s_i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
     }
     __syncthreads();
     const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
-    const uint32_t q0 = threadIdx.x * kItemsC;
+    K* Cq = C + sg.out_off + o0;
     unsigned long long hits = 0;  // triangle mode
     for (unsigned long long c0 = 0; c0 < m; c0 += W) {
       const uint32_t mc = (uint32_t)min((unsigned long long)W, m - c0);
@@ -344,61 +376,37 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
             }
           }
         }
+        // (positions cleared for the owner marks of this chunk)
+#pragma unroll
+        for (int e = 0; e < kItemsC; ++e) s_own[threadIdx.x * kItemsC + e] = 0;
       }
       __syncthreads();
-      // round 2: this thread's candidates inside the chunk's range
-      const uint32_t cs = s_start[0], ce = s_ce;
-      const uint32_t j0 = max(q0, cs), j1 = min(q0 + kItemsC, ce);
-      if (j0 < j1) {
-        uint32_t u[kItemsC], v[kItemsC];  // TC: x, adj index; SG: two adj indices
-        uint32_t lo = 0, hi = mc;         // largest i with s_start[i] <= j0
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) >> 1;
-          if (s_start[mid] <= j0) lo = mid; else hi = mid;
+      const uint32_t cs = s_start[0], ce = s_ce;  // this chunk's candidates [cs, ce)
+      if (cs < ce) {  // (a chunk of empty slabs only has none)
+        // round 2: each non-empty slab marks its first position
+        for (uint32_t i = threadIdx.x; i < mc; i += kThreads) {
+          const uint32_t st = s_start[i], nx = i + 1 < mc ? s_start[i + 1] : ce;
+          if (st < nx) s_own[st] = (uint16_t)i;
         }
-        uint32_t i = lo;
-        uint32_t nxt = i + 1 < mc ? s_start[i + 1] : 0xFFFFFFFFu;
-#pragma unroll
-        for (int e = 0; e < kItemsC; ++e) {
-          const uint32_t j = q0 + e;
-          u[e] = 0;
-          v[e] = 0;
-          if (j >= j0 && j < j1) {
-            while (j >= nxt) {  // skip to the slab holding j (empty slabs share a start)
-              ++i;
-              nxt = i + 1 < mc ? s_start[i + 1] : 0xFFFFFFFFu;
-            }
-            const uint32_t r = j - s_start[i];
-            if (tc) {
-              u[e] = s_x[i];
-              v[e] = s_a[i] + r;
-            } else {
-              const uint32_t rr = r + (c0 == 0 && i == 0 ? s_r0 : 0u), d = s_d[i];
-              const uint32_t qa = rr / d;
-              uint32_t qb = rr - qa * d;
-              if (iter == 0) {
-                qb += qb >= qa;
-                u[e] = s_x[i] + qa;
-                v[e] = s_x[i] + qb;
-              } else {
-                u[e] = s_x[i] + qa;
-                v[e] = s_a[i] + qb;
-              }
-            }
-          }
-        }
+        __syncthreads();
+        owner_max_scan(s_own, s_w);
+        __syncthreads();
+        // round 3: positions in lane order, every load of a thread in flight
         if constexpr (kProbe) {
-          // candidate (a = u, b, c = adj[v]): is (c, a) an edge?  Four binary
-          // searches at a time, in lockstep, so their loads overlap
 #pragma unroll
           for (int h = 0; h < kItemsC; h += 4) {
             uint32_t a[4], lo[4], hi[4], end[4];
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
-              const uint32_t j = q0 + h + g;
-              const bool ok = j >= j0 && j < j1;
-              const uint32_t c = ok ? adj[v[h + g]] : 0u;
-              a[g] = u[h + g];
+              const uint32_t q = (h + g) * kThreads + threadIdx.x;
+              const bool ok = q >= cs && q < ce;
+              uint32_t c = 0;
+              a[g] = 0;
+              if (ok) {
+                const uint32_t i = s_own[q];
+                c = adj[s_a[i] + q - s_start[i]];
+                a[g] = s_x[i];
+              }
               lo[g] = ok ? off[c] : 0u;
               end[g] = ok ? off[c + 1] : 0u;
               hi[g] = end[g];
@@ -418,25 +426,62 @@ __global__ void __launch_bounds__(kThreads, 4) k_join_emit(Stage* stp) {
 #pragma unroll
             for (int g = 0; g < 4; ++g) hits += lo[g] < end[g] && adj[lo[g]] == a[g];
           }
-        } else {
+        } else if (tc) {
+          constexpr int kB = kItemsC / 2;  // positions whose loads are in flight together
 #pragma unroll
-          for (int e = 0; e < kItemsC; ++e) {
-            const uint32_t j = q0 + e;
-            if (j >= j0 && j < j1)
-              sout[pad32(j)] = tc ? (((K)u[e] << w) | (K)adj[v[e]])
-                                  : (((K)adj[u[e]] << w) | (K)adj[v[e]]);
+          for (int h = 0; h < kItemsC; h += kB) {
+            uint32_t u[kB], z[kB];
+#pragma unroll
+            for (int e = 0; e < kB; ++e) {
+              const uint32_t q = (h + e) * kThreads + threadIdx.x;
+              u[e] = 0;
+              z[e] = 0;
+              if (q >= cs && q < ce) {
+                const uint32_t i = s_own[q];
+                u[e] = s_x[i];
+                z[e] = adj[s_a[i] + q - s_start[i]];
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < kB; ++e) {
+              const uint32_t q = (h + e) * kThreads + threadIdx.x;
+              if (q >= cs && q < ce) Cq[q] = ((K)u[e] << w) | (K)z[e];
+            }
+          }
+        } else {
+          constexpr int kB = kItemsC / 2;
+#pragma unroll
+          for (int h = 0; h < kItemsC; h += kB) {
+            uint32_t u[kB], z[kB];
+#pragma unroll
+            for (int e = 0; e < kB; ++e) {
+              const uint32_t q = (h + e) * kThreads + threadIdx.x;
+              u[e] = 0;
+              z[e] = 0;
+              if (q >= cs && q < ce) {
+                const uint32_t i = s_own[q];
+                const uint32_t rr = q - s_start[i] + (c0 == 0 && i == 0 ? s_r0 : 0u), d = s_d[i];
+                const uint32_t qa = rr / d;
+                uint32_t qb = rr - qa * d;
+                if (iter == 0) qb += qb >= qa;
+                u[e] = adj[s_x[i] + qa];
+                z[e] = adj[(iter == 0 ? s_x[i] : s_a[i]) + qb];
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < kB; ++e) {
+              const uint32_t q = (h + e) * kThreads + threadIdx.x;
+              if (q >= cs && q < ce) Cq[q] = ((K)u[e] << w) | (K)z[e];
+            }
           }
         }
       }
-      __syncthreads();  // the table is read; the next chunk may overwrite it
+      __syncthreads();  // the table and owners are read; the next chunk may overwrite them
     }
     if constexpr (kProbe) {
       unsigned long long tot;
       block_excl_scan(hits, s_scan, &tot);
       if (threadIdx.x == 0 && tot) atomicAdd(stp->probe, tot);
-    } else {
-      K* Cq = C + sg.out_off + o0;
-      for (uint32_t q = threadIdx.x; q < nout; q += kThreads) Cq[q] = sout[pad32(q)];
     }
   }
 }
