@@ -351,13 +351,18 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
 #pragma unroll
         for (int e = 0; e < kPer; ++e) {
           const uint32_t i = threadIdx.x + e * kThreads;
-          if (i < mc) {
+          // slab i0 starts at or before o0; slabs after it start inside (o0, o1]
+          if (i < mc) s_start[i] = c0 == 0 && i == 0 ? 0u : (uint32_t)(p[e] - o0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+          const uint32_t i = threadIdx.x + e * kThreads;
+          // an empty slab (sink of the join) needs no CSR offsets
+          if (i < mc && s_start[i] < (i + 1 < mc ? s_start[i + 1] : s_ce)) {
             const bool head = c0 == 0 && i == 0;  // the slab owning the tile's first candidate
             const uint32_t x = (uint32_t)(key[e] >> w), y = (uint32_t)(key[e] & mask);
-            // slab i0 starts at or before o0 (r0 of its candidates precede the
-            // tile); slabs after it start inside (o0, o1]
-            const uint32_t r0 = head ? (uint32_t)(o0 - p[e]) : 0u;
-            s_start[i] = head ? 0u : (uint32_t)(p[e] - o0);
+            const uint32_t r0 = head ? (uint32_t)(o0 - p[e]) : 0u;  // its candidates before the tile
             if (tc) {
               s_x[i] = x;
               s_a[i] = off[y] + r0;                                 // T(x,y), E(y,z)
@@ -376,14 +381,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
             }
           }
         }
-        // (positions cleared for the owner marks of this chunk)
-#pragma unroll
-        for (int e = 0; e < kItemsC; ++e) s_own[threadIdx.x * kItemsC + e] = 0;
       }
       __syncthreads();
       const uint32_t cs = s_start[0], ce = s_ce;  // this chunk's candidates [cs, ce)
       if (cs < ce) {  // (a chunk of empty slabs only has none)
         // round 2: each non-empty slab marks its first position
+#pragma unroll
+        for (int e = 0; e < kItemsC; ++e) s_own[threadIdx.x * kItemsC + e] = 0;
+        __syncthreads();
         for (uint32_t i = threadIdx.x; i < mc; i += kThreads) {
           const uint32_t st = s_start[i], nx = i + 1 < mc ? s_start[i + 1] : ce;
           if (st < nx) s_own[st] = (uint16_t)i;
