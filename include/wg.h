@@ -249,9 +249,9 @@ void wg_query_free(wg_ctx* ctx, wg_query q);
  *
  * wg_autotune: time each candidate on a profiled fixpoint of `edges` (kind
  * WG_TC or WG_SG; one warm-up run and one timed run per candidate, the join
- * count and the fused stage timed with CUDA events) and keep the faster
- * shape of each stage in the context for the relation's key width: every
- * engine created afterwards (single, batched, served) uses it.  `out` may be
+ * count, the radix sort and the fused stage timed with CUDA events) and keep
+ * the fastest choice of each stage in the context for the relation's key
+ * width: every engine created afterwards (single, batched, served) uses it.  `out` may be
  * NULL.  Synchronous; runs on the context stream.  Errors: WG_E_INVAL (bad
  * handle or kind), WG_E_NOMEM / WG_E_BUDGET (a run's pools do not fit),
  * WG_E_CUDA.  On an error the context keeps its previous shapes.
@@ -265,11 +265,26 @@ typedef struct wg_tune {
   uint32_t fuse_tile;           /* chosen merged keys per fused-pass tile */
   uint32_t count_cand[2];       /* candidates (default first) */
   uint32_t fuse_cand[2];
+  uint32_t sort_mode;           /* chosen enum wg_sort_mode (TC relations of at most
+                                   2^18 vertices; otherwise the default, untimed) */
   double count_ms[2];           /* join-count time per fixpoint, per candidate */
   double fuse_ms[2];            /* fused-stage time per fixpoint, per candidate */
+  double sort_ms[3];            /* radix sort (histogram + passes) per fixpoint, per
+                                   wg_sort_mode; 0 when not timed */
 } wg_tune;
 int wg_autotune(wg_ctx* ctx, wg_rel edges, int kind, wg_tune* out);
 int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_tile);
+
+/* The radix sort of a single TC query's candidates (sorted per source on the
+ * destination field, Sec. Buffer Routing and Adaptive Radix Sort): one CTA
+ * takes a source's whole segment through every pass, with 16 or 8 keys per
+ * thread (used while no source has more than 512K candidates in an
+ * iteration), or the decoupled-lookback passes over all tiles.  The same
+ * result for every mode.  wg_set_sort picks it for engines of key width
+ * key_bytes created afterwards; wg_autotune times all three.
+ * Errors: WG_E_INVAL. */
+enum wg_sort_mode { WG_SORT_SEGMENT16 = 0, WG_SORT_SEGMENT8 = 1, WG_SORT_PASSES = 2 };
+int wg_set_sort(wg_ctx* ctx, int key_bytes, uint32_t mode);
 
 /* ---- self-test of the bounded device wait --------------------------------
  * wg_selftest_wait_timeout: run the wait of the decoupled lookback (the one

@@ -190,6 +190,7 @@ struct Dev {
   uint32_t copyback;                  // single fused engine: copy Full' back into the Full
                                       // buffer each iteration instead of swapping buffers
   uint32_t count_tile;                // delta tuples per join-count tile
+  uint32_t seg_sort;                  // x-grouped: the per-segment sort may take the launch
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
   uint32_t xseg_maxt;                 // x-grouped sort: tiles of the largest source segment

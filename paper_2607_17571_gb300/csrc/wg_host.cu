@@ -88,6 +88,7 @@ struct wg_ctx {
   // tile shapes engines are built with, per key width (index 0: 4-byte keys,
   // 1: 8-byte); 0 = the compiled default.  Set by wg_autotune / wg_set_tiles.
   uint32_t tune_count[2] = {0, 0}, tune_fuse[2] = {0, 0};
+  uint32_t tune_sort[2] = {WG_SORT_SEGMENT16, WG_SORT_SEGMENT16};  // enum wg_sort_mode
   cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
   void* s_tmp = nullptr; size_t s_tmp_bytes = 0;
@@ -449,6 +450,7 @@ struct EngineBase {
   virtual bool hashjoin() const = 0;
   virtual uint32_t count_tile() const = 0;
   virtual uint32_t fuse_tile() const = 0;
+  virtual uint32_t sort_mode() const = 0;
   virtual void release() = 0;
 };
 
@@ -517,16 +519,21 @@ struct Engine : EngineBase {
   cudaEvent_t ev_done = nullptr;
   uint64_t launches_issued = 0;
   uint32_t regrows = 0;
-  int kernels_per_iter() const { return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 3 : 0) - (hash_join ? 1 : 0); }
+  int kernels_per_iter() const {
+    return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 2 : 0) +
+           (xseg && sort_mode_ != WG_SORT_PASSES ? 1 : 0) - (hash_join ? 1 : 0);
+  }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
   uint32_t count_tile_, fuse_tile_;  // delta tuples per join-count tile, keys per fused tile
+  uint32_t sort_mode_;               // enum wg_sort_mode (x-grouped engines)
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
          bool xseg_, bool copy_back_ = false, bool hash_join_ = false)
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
         log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_),
-        count_tile_(count_tile_of<K>(ctx)), fuse_tile_(fuse_tile_of<K>(ctx)) {
+        count_tile_(count_tile_of<K>(ctx)), fuse_tile_(fuse_tile_of<K>(ctx)),
+        sort_mode_(ctx->tune_sort[sizeof(K) == 8]) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
@@ -537,6 +544,7 @@ struct Engine : EngineBase {
   bool hashjoin() const override { return hash_join; }
   uint32_t count_tile() const override { return count_tile_; }
   uint32_t fuse_tile() const override { return fuse_tile_; }
+  uint32_t sort_mode() const override { return sort_mode_; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -588,6 +596,7 @@ struct Engine : EngineBase {
     h.fuse = fuse ? 1 : 0; h.fuse_tile = fuse_tile_; h.xseg = xseg ? 1 : 0;
     h.copyback = copy_back && single && fuse ? 1 : 0;
     h.count_tile = count_tile_;
+    h.seg_sort = xseg && sort_mode_ != WG_SORT_PASSES ? 1 : 0;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
@@ -598,7 +607,7 @@ struct Engine : EngineBase {
     g_emit = grid_of(c, occupancy_join<K>(1));
     g_hist = grid_of(c, occupancy_sort<K>(0));
     g_pass = grid_of(c, occupancy_sort<K>(1));
-    g_seg = grid_of(c, occupancy_sort<K>(6));
+    g_seg = grid_of(c, occupancy_sort<K>(sort_mode_ == WG_SORT_SEGMENT8 ? 7 : 6));
     g_uniq = grid_of(c, occupancy_sort<K>(2));
     g_merge = grid_of(c, occupancy_sort<K>(3));
     g_fuse = grid_of(c, occupancy_sort<K>(fuse_tile_ == (uint32_t)FuseTile<K>::T ? 4 : 5));
@@ -788,7 +797,8 @@ struct Engine : EngineBase {
       // segment is longer than kSegSortMaxTiles tiles, else the lookback
       // passes (each kernel finds out on the device and the other returns)
       mark();
-      launch_sort_seg<K>(dv->st + S_PASS0, g_seg, s, dbits);
+      if (sort_mode_ != WG_SORT_PASSES)
+        launch_sort_seg<K>(dv->st + S_PASS0, g_seg, s, dbits, sort_mode_ == WG_SORT_SEGMENT8 ? 8 : 16);
       for (uint32_t p = 0; p < passes; ++p) launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits);
       mark();
       if (!stage()) return syncs;
@@ -1874,7 +1884,7 @@ static int single_begin(wg_ctx* c, Query* q) {
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
         c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
         c->idle[i]->hashjoin() == hashjoin && c->idle[i]->count_tile() == ct &&
-        c->idle[i]->fuse_tile() == ft) {
+        c->idle[i]->fuse_tile() == ft && c->idle[i]->sort_mode() == c->tune_sort[R->kb == 8]) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
     }
@@ -2274,19 +2284,30 @@ int wg_set_tiles(wg_ctx* c, int key_bytes, uint32_t count_tile, uint32_t fuse_ti
   return WG_OK;
 }
 
-// One profiled fixpoint: the join-count and fused-stage times (ms).
-static int tune_run(wg_ctx* c, wg_rel edges, int kind, double* count_ms, double* fuse_ms) {
+int wg_set_sort(wg_ctx* c, int key_bytes, uint32_t mode) {
+  if (!c || (key_bytes != 4 && key_bytes != 8) || mode > WG_SORT_PASSES)
+    return set_err(WG_E_INVAL, "bad argument");
+  c->tune_sort[key_bytes == 8] = mode;
+  return WG_OK;
+}
+
+// One profiled fixpoint: the join-count, radix-sort and fused-stage times (ms).
+static int tune_run(wg_ctx* c, wg_rel edges, int kind, double* count_ms, double* fuse_ms,
+                    double* sort_ms = nullptr) {
   wg_opts o{};
   o.profile = 1;
   wg_query id = 0;
   TRY(single_query(c, kind, edges, &o, &id));
   const int rc = wg_wait(c, id, 0);
   *count_ms = *fuse_ms = 0;
+  if (sort_ms) *sort_ms = 0;
   if (rc == WG_OK) {
     Query* q = find_q(c, id);
     for (const KStat& k : q->prof) {
       if (!std::strcmp(k.name, "join_count")) *count_ms = k.ms;
       if (!std::strcmp(k.name, "dedup_diff_merge") || !std::strcmp(k.name, "dedup_diff")) *fuse_ms += k.ms;
+      if (sort_ms && (!std::strcmp(k.name, "sort_hist") || !std::strcmp(k.name, "sort_pass")))
+        *sort_ms += k.ms;
     }
   }
   wg_query_free(c, id);
@@ -2321,6 +2342,27 @@ int wg_autotune(wg_ctx* c, wg_rel edges, int kind, wg_tune* out) {
   t.fuse_tile = t.fuse_ms[1] < t.fuse_ms[0] ? t.fuse_cand[1] : t.fuse_cand[0];
   c->tune_count[i] = t.count_tile;
   c->tune_fuse[i] = t.fuse_tile;
+  // the radix sort of the per-source segments (single TC queries that sort
+  // per source): each mode with the chosen tiles
+  const uint32_t keep_sort = c->tune_sort[i];
+  t.sort_mode = keep_sort;
+  if (kind == WG_TC && it->second->nv <= kXSegMaxVertices) {
+    for (uint32_t m = 0; m <= WG_SORT_PASSES; ++m) {
+      c->tune_sort[i] = m;
+      double cm = 0, fm = 0;
+      for (int rep = 0; rep < 2; ++rep) {
+        const int rc = tune_run(c, edges, kind, &cm, &fm, &t.sort_ms[m]);
+        if (rc != WG_OK) {
+          c->tune_sort[i] = keep_sort;
+          return rc;
+        }
+      }
+    }
+    t.sort_mode = 0;
+    for (uint32_t m = 1; m <= WG_SORT_PASSES; ++m)
+      if (t.sort_ms[m] < t.sort_ms[t.sort_mode]) t.sort_mode = m;
+  }
+  c->tune_sort[i] = t.sort_mode;
   if (out) *out = t;
   return WG_OK;
 }

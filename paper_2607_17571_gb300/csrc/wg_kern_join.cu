@@ -610,11 +610,14 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
     const uint32_t ntiles = (uint32_t)(pt + tt);
     dv->st[S_HIST].segs = dv->segX; dv->st[S_HIST].nseg = nv;
     dv->st[S_HIST].ntiles = ntiles; dv->st[S_HIST].tile_seg = dv->tile_seg;
-    dv->st[S_HIST].maxt = &dv->xseg_maxt;  // count every pass's digits
+    // the per-segment sort (and the histogram of every pass's digits it
+    // reads) only when the engine uses it; else the lookback passes
+    const uint32_t* mt = dv->seg_sort ? &dv->xseg_maxt : nullptr;
+    dv->st[S_HIST].maxt = mt;
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
       dv->st[S_PASS0 + p].ntiles = ntiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
-      dv->st[S_PASS0 + p].maxt = &dv->xseg_maxt;
+      dv->st[S_PASS0 + p].maxt = mt;
     }
   }
 }

@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 // claims the segments of at least kSegBig tiles first, then the others, so
 // the longest ones do not start last.  NT threads of IT keys each make a tile.
 constexpr uint32_t kSegBig = 16;
-constexpr int kSegNT = 256, kSegIT = 16, kSegMinBlocks = 4;  // 64 registers, 4 CTAs per SM
+// two compiled shapes (engine setting, wg_set_sort): 256 threads of 16 keys
+// at 4 CTAs per SM (64 registers) or of 8 keys at 6 CTAs per SM (40)
+constexpr int kSegNT = 256;
+template <int IT> struct SegShape { static constexpr int minb = IT == 16 ? 4 : 6; };
 
 template <typename K, int NT, int IT>
 struct SegSmem {
@@ -680,15 +683,15 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
   }
 }
 
-template <typename K, bool kByte>
-__global__ void __launch_bounds__(kSegNT, kSegMinBlocks) k_sort_seg(Stage* st0) {
-  __shared__ SegSmem<K, kSegNT, kSegIT> S;
+template <typename K, bool kByte, int IT>
+__global__ void __launch_bounds__(kSegNT, SegShape<IT>::minb) k_sort_seg(Stage* st0) {
+  __shared__ SegSmem<K, kSegNT, IT> S;
   if (*(volatile uint32_t*)&st0->ctl->abort) return;
   if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;  // the lookback passes sort it
   for (;;) {
     const uint32_t k = seg_claim(st0, &S.s_k);
     if (k == 0xFFFFFFFFu) return;
-    seg_sort<K, kByte, kSegNT, kSegIT>(st0, S, k);
+    seg_sort<K, kByte, kSegNT, IT>(st0, S, k);
   }
 }
 
@@ -1281,9 +1284,14 @@ void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits) {
   else k_sort_pass<K, false><<<grid, kThreads, 0, s>>>(st);
 }
 template <typename K>
-void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits) {
-  if (dbits == 8) k_sort_seg<K, true><<<grid, kSegNT, 0, s>>>(st0);
-  else k_sort_seg<K, false><<<grid, kSegNT, 0, s>>>(st0);
+void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits, int items) {
+  if (items == 8) {
+    if (dbits == 8) k_sort_seg<K, true, 8><<<grid, kSegNT, 0, s>>>(st0);
+    else k_sort_seg<K, false, 8><<<grid, kSegNT, 0, s>>>(st0);
+  } else {
+    if (dbits == 8) k_sort_seg<K, true, 16><<<grid, kSegNT, 0, s>>>(st0);
+    else k_sort_seg<K, false, 16><<<grid, kSegNT, 0, s>>>(st0);
+  }
 }
 template <typename K>
 void launch_unique_diff(Stage* st, int grid, cudaStream_t s) { k_unique_diff<K><<<grid, kThreads, 0, s>>>(st); }
@@ -1329,7 +1337,8 @@ int occupancy_sort(int which) {
     case 3: return occupancy_of(k_merge<K>);
     case 4: return occupancy_of(k_diff_merge<K, FuseTile<K>::T>);
     case 5: return occupancy_of(k_diff_merge<K, FuseTile<K>::T / 2>);
-    case 6: return occupancy_of(k_sort_seg<K, true>, kSegNT);
+    case 6: return occupancy_of(k_sort_seg<K, true, 16>, kSegNT);
+    case 7: return occupancy_of(k_sort_seg<K, true, 8>, kSegNT);
     default: return 0;
   }
 }
@@ -1337,7 +1346,7 @@ int occupancy_sort(int which) {
 #define WG_INST(K)                                              \
   template void launch_sort_hist<K>(Stage*, int, cudaStream_t);  \
   template void launch_sort_pass<K>(Stage*, int, cudaStream_t, uint32_t); \
-  template void launch_sort_seg<K>(Stage*, int, cudaStream_t, uint32_t); \
+  template void launch_sort_seg<K>(Stage*, int, cudaStream_t, uint32_t, int); \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t, uint32_t); \

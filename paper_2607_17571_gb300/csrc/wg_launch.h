@@ -19,7 +19,8 @@ template <typename K> void launch_sort_hist(Stage* st, int grid, cudaStream_t s)
 template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits);
 // every pass of segments of at most kSegSortMaxTiles tiles, one CTA per segment
 // (st0: the first pass's stage; the later passes' stages follow it)
-template <typename K> void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits);
+template <typename K> void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits,
+                                           int items);  // keys per thread: 16 or 8
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
 // tile: merged keys per fused-pass tile, FuseTile<K>::T or half of it
@@ -29,7 +30,8 @@ template <typename K> void launch_diff_merge(Stage* st, int grid, cudaStream_t s
 template <typename K>
 void launch_partition(Stage* consumer, int mode, uint32_t tile, int grid, cudaStream_t s);
 template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq, 3 merge, 4 fused,
-                                                      // 5 fused with half tiles, 6 segment sort
+                                                      // 5 fused with half tiles, 6 / 7 segment sort
+                                                      // of 16 / 8 keys per thread
 
 // join and engine control (wg_kern_join.cu)
 // tile: delta tuples per count tile, kTileD or kTileD / 2

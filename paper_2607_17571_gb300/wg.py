@@ -27,6 +27,7 @@ WG_FLAG_FULL_WIDTH = 2
 WG_FLAG_COPY_BACK = 4
 WG_FLAG_HASH_JOIN = 8
 WG_PENDING, WG_RUNNING, WG_DONE, WG_FAILED = 0, 1, 2, 3
+WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES = 0, 1, 2
 ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPACITY",
           -5: "WG_E_NOT_READY", -6: "WG_E_ITER_CAP", -7: "WG_E_DEVICE_TIMEOUT", -8: "WG_E_CUDA"}
 
@@ -48,8 +49,8 @@ class wg_request(Structure):
 
 class wg_tune(Structure):
     _fields_ = [("key_bytes", c_uint32), ("count_tile", c_uint32), ("fuse_tile", c_uint32),
-                ("count_cand", c_uint32 * 2), ("fuse_cand", c_uint32 * 2),
-                ("count_ms", c_double * 2), ("fuse_ms", c_double * 2)]
+                ("count_cand", c_uint32 * 2), ("fuse_cand", c_uint32 * 2), ("sort_mode", c_uint32),
+                ("count_ms", c_double * 2), ("fuse_ms", c_double * 2), ("sort_ms", c_double * 3)]
 
 
 class wg_kernel_stat(Structure):
@@ -85,6 +86,7 @@ SIGNATURES = {
     "wg_autotune": (c_int, [c_void_p, c_uint64, c_int, POINTER(wg_tune)]),
     "wg_selftest_wait_timeout": (c_int, [c_void_p]),
     "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32]),
+    "wg_set_sort": (c_int, [c_void_p, c_int, c_uint32]),
     "wg_result_profile": (c_int, [c_void_p, c_uint64, POINTER(wg_kernel_stat), c_size_t,
                                   POINTER(c_size_t)]),
     "wg_query_free": (None, [c_void_p, c_uint64]),
@@ -328,9 +330,10 @@ class Context:
         t = wg_tune()
         _check(self.lib.wg_autotune(self.h, rel.id, kind, byref(t)), "wg_autotune")
         return dict(key_bytes=t.key_bytes, count_tile=t.count_tile, fuse_tile=t.fuse_tile,
-                    count_cand=list(t.count_cand), fuse_cand=list(t.fuse_cand),
-                    count_ms=[round(x, 3) for x in t.count_ms],
-                    fuse_ms=[round(x, 3) for x in t.fuse_ms])
+                    sort_mode=t.sort_mode, count_cand=list(t.count_cand),
+                    fuse_cand=list(t.fuse_cand), count_ms=[round(x, 3) for x in t.count_ms],
+                    fuse_ms=[round(x, 3) for x in t.fuse_ms],
+                    sort_ms=[round(x, 3) for x in t.sort_ms])
 
     def selftest_wait_timeout(self) -> int:
         """wg_selftest_wait_timeout: the return code (WG_E_DEVICE_TIMEOUT is
@@ -340,6 +343,10 @@ class Context:
     def set_tiles(self, key_bytes: int, count_tile: int = 0, fuse_tile: int = 0):
         """wg_set_tiles: tile shapes for engines of this key width (0 = default)."""
         _check(self.lib.wg_set_tiles(self.h, key_bytes, count_tile, fuse_tile), "wg_set_tiles")
+
+    def set_sort(self, key_bytes: int, mode: int = WG_SORT_SEGMENT16):
+        """wg_set_sort: radix-sort mode of single TC engines of this key width."""
+        _check(self.lib.wg_set_sort(self.h, key_bytes, mode), "wg_set_sort")
 
     def triangles(self, rel: Relation) -> int:
         """wg_triangles: number of tuples of triangle(a,b,c) <- edge(a,b),

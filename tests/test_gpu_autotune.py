@@ -1,6 +1,6 @@
 """Tile shapes of the join count and of the fused deduplication / set
-difference / merge pass, and the autotuner that picks them (wg_autotune,
-wg_set_tiles).
+difference / merge pass, the radix-sort modes of single TC queries, and the
+autotuner that picks them (wg_autotune, wg_set_tiles, wg_set_sort).
 
 Every compiled shape must give the oracle's result bit for bit -- closure,
 iteration count and per-iteration delta sizes -- for TC and SG, single and
@@ -76,6 +76,36 @@ def test_every_tile_shape_matches_oracle(count_tile, half_fuse):
             _check(h, want)
 
 
+def _hub():
+    # source 0 -> 1..1000, each of them -> 1001..1600: in its first iteration
+    # source 0 has 600,000 candidates (147 tiles), more than the per-segment
+    # sort takes, so its launches fall back to the lookback passes
+    mid = np.arange(1, 1001, dtype=np.uint32)
+    leaf = np.arange(1001, 1601, dtype=np.uint32)
+    src = np.concatenate([np.zeros(1000, np.uint32), np.repeat(mid, 600)])
+    dst = np.concatenate([mid, np.tile(leaf, 1000)])
+    return I.EdgeList(src, dst, dict(recipe="hub"))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])  # WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES
+def test_every_sort_mode_matches_oracle(mode):
+    from paper_2607_17571_gb300 import wg
+    cases = _cases()
+    hub = _hub()
+    want_hub = oracle_tc(hub.src, hub.dst)
+    with wg.Context(0) as c:
+        for kb in (4, 8):
+            c.set_sort(kb, mode)
+        for name in ("tc32", "tc64"):
+            g, want = cases[name]
+            rel = c.load(g.src, g.dst)
+            _check(c.tc(rel), want)
+            _check(c.tc(rel, loop=wg.WG_LOOP_HOST, profile=True), want)
+        _check(c.tc(c.load(hub.src, hub.dst)), want_hub)
+    with wg.Context(0) as c, pytest.raises(wg.WgError):
+        c.set_sort(4, 3)
+
+
 def test_autotune_picks_a_compiled_shape_and_engines_use_it():
     from paper_2607_17571_gb300 import wg
     g, want = _cases()["tc32"]
@@ -89,6 +119,9 @@ def test_autotune_picks_a_compiled_shape_and_engines_use_it():
         # the choice is the faster candidate of each stage
         assert t["count_tile"] == COUNT[int(t["count_ms"][1] < t["count_ms"][0])]
         assert t["fuse_tile"] == FUSE[4][int(t["fuse_ms"][1] < t["fuse_ms"][0])]
+        # the radix sort of the per-source segments: the fastest of the three modes
+        assert all(ms > 0 for ms in t["sort_ms"])
+        assert t["sort_mode"] == int(np.argmin(t["sort_ms"]))
         _check(c.tc(rel), want)
         h, = c.submit([(wg.WG_TC, rel)])
         _check(h, want)
