@@ -802,19 +802,21 @@ def run_serve(args):
             wait = arr[a] - (time.perf_counter() - t0 - chk)
             if wait > 0:
                 time.sleep(wait)
-            q = None
-            try:  # a query whose first pools do not fit fails at the call
+            q, st = None, None
+            try:  # a query whose pools do not fit fails at the call or at the wait
                 q = single(a % npool)
                 st = q.wait()
                 ok += 1
                 tuples += st.n_tuples
             except wg.WgError:
                 rej += 1
+                st = None
             lat.append((time.perf_counter() - t0 - chk - arr[a]) * 1e3)
             if q is not None:
-                c0 = time.perf_counter()
-                bad += check(a % npool, q, st)
-                chk += time.perf_counter() - c0
+                if st is not None:
+                    c0 = time.perf_counter()
+                    bad += check(a % npool, q, st)
+                    chk += time.perf_counter() - c0
                 q.free()
         el = time.perf_counter() - t0 - chk
         return dict(seconds=round(el, 3), queries_per_s=ok / el, tuples_per_s=tuples / el,
