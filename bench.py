@@ -44,6 +44,9 @@ WORKLOADS = {
     "tc_rmat19_400k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^19 nodes, 400k distinct "
                                            "DAG edges, seed 2 (124,568 vertices: 17-bit ranks, "
                                            "64-bit keys)"),
+    "tc_rmat19_150k": dict(kind="tc", desc="TC, R-MAT(.57,.19,.19,.05) 2^19 nodes, 150k distinct "
+                                           "DAG edges, seed 2 (76,647 vertices: 64-bit keys; "
+                                           "profiling-size case)"),
 }
 FALLBACK_HBM_GBS = 6800.0
 
@@ -341,7 +344,8 @@ def autotune_ctx(ctx, rels, kind=None):
     out = {}
     for kb, (i, _) in sorted(best.items()):
         t = ctx.autotune(rels[i], wg.WG_TC if kind is None else kind)
-        out[f"{kb}B_keys"] = {k: t[k] for k in ("count_tile", "fuse_tile", "count_ms", "fuse_ms")}
+        out[f"{kb}B_keys"] = {k: t[k] for k in ("count_tile", "fuse_tile", "sort_mode", "count_ms",
+                                                 "fuse_ms", "sort_ms")}
     return out
 
 

@@ -352,6 +352,8 @@ def workload(name: str) -> EdgeList:
         return rmat_dag(15, 100_000, seed=2)
     if name == "tc_rmat19_400k":  # the same recipe on 2^19 nodes: ranks need 17 bits (64-bit keys)
         return rmat_dag(19, 400_000, seed=2)
+    if name == "tc_rmat19_150k":  # 64-bit keys at profiling size (76,647 vertices)
+        return rmat_dag(19, 150_000, seed=2)
     if name == "tri_rmat16_800k":  # triangle counting: undirected, 800k directed edges
         return rmat_sym(16, 400_000, seed=6)
     raise KeyError(name)
