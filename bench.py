@@ -637,6 +637,7 @@ def run_ablations(args):
                 ("host_loop", dict(loop=wg.WG_LOOP_HOST)),
                 ("host_staged", dict(loop=wg.WG_LOOP_HOST_STAGED)),
                 ("full_width", dict(full_width=True)),
+                ("merge_every_iter", dict(side_run="never")),
                 ("copy_back", dict(copy_back=True)), ("hash_join", dict(hash_join=True))]
     ref, out = None, []
     clocks = Clocks(0)

@@ -93,6 +93,21 @@ enum wg_loop {
                                       thread, instead of the CSR range lookup and the
                                       load-balanced emit (Sec. Data Skew in Hash-Based Join);
                                       same result.  Ignored by SG queries and by wg_submit */
+#define WG_FLAG_MERGE_EVERY_ITER 16u /* ablation (single queries, fused stages): merge the new
+                                      tuples into the full relation at every iteration (the
+                                      disjoint merge of Sec. Disjoint Merge after each pass).
+                                      By default the full relation is kept as a main run and
+                                      a small side run of the newest tuples: an iteration
+                                      whose candidates are at most 1/8 of the main run finds
+                                      its new tuples against both runs and merges them into
+                                      the side run only, so the main run is not rewritten;
+                                      the side run is folded back when it outgrows its pool
+                                      (an eighth of the full relation's) or when the
+                                      candidates grow again, and the final relation is the
+                                      two runs merged.  Same result either way */
+#define WG_FLAG_SIDE_RUN_ALWAYS 32u /* testing (single queries, fused stages): take the side run
+                                      in every iteration it fits, however many candidates;
+                                      same result */
 
 typedef struct wg_opts {
   uint32_t max_iters;    /* iteration cap; 0 = 1<<20 */

@@ -125,11 +125,22 @@ struct Inst {
   unsigned long long* log;     // |Delta^0|, |Delta^1|, ...
   uint32_t log_cap;
   uint32_t fresh;              // admitted, delta not yet initialised
+  // Full kept as two sorted runs (single-query fused engines): the main run
+  // (n_full - n_side keys in pool F at f_off) and a side run of the newest
+  // tuples (n_side keys in pool G[gphase] at 0), disjoint.  An iteration with
+  // few candidates (side_iter) takes its new tuples against both runs and
+  // merges them into the side run only; the main run is rewritten only when
+  // the side run is folded back (a pre-merge, or the final merge).
+  unsigned long long n_side;
+  unsigned long long n_new0;   // side iteration: candidates not in the main run (deduplicated)
+  uint32_t gphase, side_iter;
 };
 
 // Stage slots of an engine (one Stage record per kernel of the iteration).
+// S_FUSE2: the side run's fused pass; S_PREM: folding the side run into the main run.
+// The radix sort alone uses the stages below S_SORT_END.
 enum StageId : int { S_COUNT = 0, S_EMIT, S_HIST, S_UNIQ, S_MERGE, S_FUSE, S_PASS0,
-                     S_NUM = S_PASS0 + kMaxPasses };
+                     S_SORT_END = S_PASS0 + kMaxPasses, S_FUSE2 = S_SORT_END, S_PREM, S_NUM };
 
 // Full-relation window staged by dedup + diff (separate-stage mode).
 template <typename K> struct FWin { static constexpr int n = sizeof(K) == 4 ? 2048 : 1024; };
@@ -140,6 +151,11 @@ template <typename K> struct FuseTile {
   static constexpr int T = sizeof(K) == 4 ? 4096 : 2048;
   static constexpr int E = T / kThreads;
 };
+
+// Side-run iterations: taken when the candidates are at most 1/kSideRatio of
+// the main run (the main run then is mostly copied, not merged) and the side
+// run plus the candidates fit its pool.
+constexpr unsigned long long kSideRatio = 8;
 
 // Per-segment radix sort (k_sort_seg): used when no segment has more tiles.
 constexpr uint32_t kSegSortMaxTiles = 128;
@@ -163,6 +179,7 @@ struct Dev {
   Seg* segU;  // dedup + diff
   Seg* segM;  // merge (separate mode) / retire copy (fused mode)
   Seg* segF;  // fused dedup + diff + merge
+  Seg* segF2; // the side run's fused pass
   void* D[2];  // delta / new-delta pools (swap every iteration)
   void* C[2];  // candidate pools (radix ping-pong)
   void* F[2];  // full relation pools (swap every iteration)
@@ -183,6 +200,9 @@ struct Dev {
   uint32_t* mixl;                     // fused pass: mixed tile list [tiles]
   uint32_t* mixc;                     // mixed tiles before each tile [tiles + 1]
   uint32_t* mixs;                     // mixed tiles per chunk of kThreads tiles
+  void* G[2];                         // side-run pools (swap at every side iteration)
+  unsigned long long capG;            // keys each side-run pool holds
+  unsigned long long mix_cap;         // tiles the per-tile arrays hold
   unsigned long long r_used;
   unsigned long long cond;            // cudaGraphConditionalHandle
   uint32_t n_inst, single, use_cond, fuse, fuse_tile;
@@ -194,6 +214,8 @@ struct Dev {
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
   uint32_t xseg_maxt;                 // x-grouped sort: tiles of the largest source segment
+  uint32_t side;                      // side run: 0 never, 1 when the candidates are few,
+                                      // 2 whenever it fits (tests)
 };
 
 // Shared-memory index with one pad word per 32: threads that walk their own

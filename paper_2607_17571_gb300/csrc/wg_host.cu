@@ -451,6 +451,9 @@ struct EngineBase {
   virtual uint32_t count_tile() const = 0;
   virtual uint32_t fuse_tile() const = 0;
   virtual uint32_t sort_mode() const = 0;
+  virtual uint32_t side_mode() const = 0;
+  virtual size_t held() const = 0;       // device bytes of the engine's buffers
+  virtual size_t grow_peak() const = 0;  // held() at the peak of the growth the last run asked for
   virtual void release() = 0;
 };
 
@@ -507,7 +510,8 @@ struct Engine : EngineBase {
   std::vector<Inst> hi;
   DBuf b_dev, b_inst, b_seg, b_log;
   DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b, xsum_b, mix_b;
-  unsigned long long capC = 0, capF = 0, capR = 0;
+  DBuf G[2];  // side-run pools (single-query fused engines)
+  unsigned long long capC = 0, capF = 0, capR = 0, capG = 0;
   size_t mix_tiles = 0;  // tiles the per-tile arrays (st_s, spl, mix_b) hold
   uint32_t log_cap = 0;
   cudaGraph_t graph = nullptr;
@@ -521,19 +525,22 @@ struct Engine : EngineBase {
   uint32_t regrows = 0;
   int kernels_per_iter() const {
     return 10 + (fuse ? 3 : 0) + (int)passes + (xseg ? 2 : 0) +
-           (xseg && sort_mode_ != WG_SORT_PASSES ? 1 : 0) - (hash_join ? 1 : 0);
+           (xseg && sort_mode_ != WG_SORT_PASSES ? 1 : 0) - (hash_join ? 1 : 0) +
+           (side_ ? 6 : 0);
   }
 
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
   uint32_t count_tile_, fuse_tile_;  // delta tuples per join-count tile, keys per fused tile
   uint32_t sort_mode_;               // enum wg_sort_mode (x-grouped engines)
+  uint32_t side_;                    // side run of Full: 0 never, 1 with few candidates, 2 always
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
-         bool xseg_, bool copy_back_ = false, bool hash_join_ = false)
+         bool xseg_, bool copy_back_ = false, bool hash_join_ = false, uint32_t side = 0)
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
         log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_),
         count_tile_(count_tile_of<K>(ctx)), fuse_tile_(fuse_tile_of<K>(ctx)),
-        sort_mode_(ctx->tune_sort[sizeof(K) == 8]) {
+        sort_mode_(ctx->tune_sort[sizeof(K) == 8]),
+        side_(single_ && fuse_ && n == 1 && !copy_back_ ? side : 0u) {
     pass_plan(bits, &passes, &dbits);
   }
   ~Engine() override { release(); }
@@ -545,6 +552,7 @@ struct Engine : EngineBase {
   uint32_t count_tile() const override { return count_tile_; }
   uint32_t fuse_tile() const override { return fuse_tile_; }
   uint32_t sort_mode() const override { return sort_mode_; }
+  uint32_t side_mode() const override { return side_; }
   uint32_t bits() const override { return bits_; }
   uint32_t slots() const override { return n_slots; }
 
@@ -557,9 +565,9 @@ struct Engine : EngineBase {
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
                    &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b, &xsum_b,
-                   &mix_b};
+                   &mix_b, &G[0], &G[1]};
     for (DBuf* b : all) b->release(c);
-    capC = capF = capR = 0;
+    capC = capF = capR = capG = 0;
     mix_tiles = 0;
     nv_cap = 0;
     if (own_st && st) {
@@ -582,7 +590,7 @@ struct Engine : EngineBase {
     AllocScope scope(c, st);
     TRY(b_dev.get(c, sizeof(Dev)));
     TRY(b_inst.get(c, sizeof(Inst) * n_slots));
-    TRY(b_seg.get(c, sizeof(Seg) * n_slots * 6));
+    TRY(b_seg.get(c, sizeof(Seg) * n_slots * 7));
     TRY(b_log.get(c, sizeof(unsigned long long) * (size_t)n_slots * log_cap));
     TRY(hist.get(c, sizeof(unsigned long long) * (size_t)n_slots * passes * kRadix));
     dv = (Dev*)b_dev.p;
@@ -592,15 +600,21 @@ struct Engine : EngineBase {
     h.inst = (Inst*)b_inst.p;
     Seg* s = (Seg*)b_seg.p;
     h.segD = s; h.segE = s + n_slots; h.segS = s + 2 * n_slots; h.segU = s + 3 * n_slots;
-    h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots;
+    h.segM = s + 4 * n_slots; h.segF = s + 5 * n_slots; h.segF2 = s + 6 * n_slots;
+    h.side = side_;
     h.fuse = fuse ? 1 : 0; h.fuse_tile = fuse_tile_; h.xseg = xseg ? 1 : 0;
     h.copyback = copy_back && single && fuse ? 1 : 0;
     h.count_tile = count_tile_;
-    h.seg_sort = xseg && sort_mode_ != WG_SORT_PASSES ? 1 : 0;
+    // (the per-segment sort counts up to three passes' digits: fields of <= 24 bits)
+    h.seg_sort = xseg && sort_mode_ != WG_SORT_PASSES && passes <= 3 ? 1 : 0;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
     h.ctl.iter_budget = 0xFFFFFFFFu;
+    // Every stage kernel first reads its record's control block: a run whose
+    // first plan kernel stops on an overflow launches the later stages with
+    // records no plan kernel has written yet -- no tiles, but a valid block.
+    for (int i = 0; i < S_NUM; ++i) h.st[i].ctl = (Ctl*)((char*)dv + offsetof(Dev, ctl));
     CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, st));
     CK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
     g_count = grid_of(c, occupancy_join<K>(count_tile_ == (uint32_t)kTileD ? 0 : 3));
@@ -633,6 +647,8 @@ struct Engine : EngineBase {
     h.mixl = (uint32_t*)mix_b.p;
     h.mixc = mix_b.p ? h.mixl + mix_tiles : nullptr;
     h.mixs = mix_b.p ? h.mixc + mix_tiles + 1 : nullptr;
+    h.G[0] = G[0].p; h.G[1] = G[1].p; h.capG = capG;
+    h.mix_cap = mix_tiles;
     const size_t a = offsetof(Dev, D), b = offsetof(Dev, r_used);
     CK(cudaMemcpyAsync((char*)dv + a, (char*)&h + a, b - a, cudaMemcpyHostToDevice, st));
     return WG_OK;
@@ -650,12 +666,13 @@ struct Engine : EngineBase {
     wantC = std::max<unsigned long long>(wantC, 1ull << 16);
     wantF = std::max<unsigned long long>(wantF, 1ull << 16);
     wantR = single ? 0 : std::max<unsigned long long>(wantR, 1ull << 16);
-    uint64_t liveD = 0, liveF = 0;
+    uint64_t liveD = 0, liveF = 0, liveG = 0;
     if (keep) {
       for (const Inst& I : hi)
         if (I.state == INST_ACTIVE) {
           liveD = std::max<uint64_t>(liveD, I.d_off + I.n_delta);
-          liveF = std::max<uint64_t>(liveF, I.f_off + I.n_full);
+          liveF = std::max<uint64_t>(liveF, I.f_off + I.n_full - I.n_side);  // the main run
+          liveG = std::max<uint64_t>(liveG, I.n_side);
         }
     }
     bool clear = false;  // lookback words must start over (a status array is new)
@@ -729,6 +746,25 @@ struct Engine : EngineBase {
                            cudaMemcpyDeviceToDevice, st));
       for (int i = 0; i < 2; ++i) { F[i].release(c); F[i] = nf[i]; }
       capF = wantF;
+    }
+    if (side_) {  // side-run pools: an eighth of the Full pools
+      const unsigned long long wantG = std::max<unsigned long long>(capF / 8, 1ull << 16);
+      if (wantG > capG) {
+        // optional: without room the iterations keep merging into the main run
+        DBuf ng[2];
+        int rc = ng[0].get(c, wantG * sizeof(K));
+        if (rc == WG_OK) rc = ng[1].get(c, wantG * sizeof(K));
+        if (rc != WG_OK) {
+          ng[0].release(c); ng[1].release(c);
+          cudaGetLastError();
+        } else {
+          const uint32_t gp = hi.empty() ? 0u : hi[0].gphase & 1u;
+          if (liveG)
+            CK(cudaMemcpyAsync(ng[gp].p, G[gp].p, liveG * sizeof(K), cudaMemcpyDeviceToDevice, st));
+          for (int i = 0; i < 2; ++i) { G[i].release(c); G[i] = ng[i]; }
+          capG = wantG;
+        }
+      }
     }
     if (!single && wantR > capR) {
       DBuf nr;
@@ -809,20 +845,39 @@ struct Engine : EngineBase {
       }
     }
     if (fuse) {
+      // timed together as the fused stage: folding the side run back into
+      // the main run (when the plan asked for it), the merge-path partition,
+      // mixed tiles through the fused kernel, Full-only tiles by a plain
+      // copy, and in a side iteration the side run's pass
+      mark();
+      if (side_) {
+        launch_partition<K>(dv->st + S_PREM, 0, kTileM, c->num_sms * 4, s);
+        launch_merge<K>(dv->st + S_PREM, g_merge, s);
+        if (!stage()) return syncs;
+      }
       launch_partition<K>(dv->st + S_FUSE, 0, fuse_tile_, c->num_sms * 4, s);
       if (!stage()) return syncs;
-      // mixed tiles through the fused kernel, Full-only tiles by a plain copy
-      // (timed together as the fused stage)
-      mark();
       launch_fuse_mark(dv, c->num_sms * 2, s);
       launch_fuse_list(dv, c->num_sms * 2, s);
       launch_diff_merge<K>(dv->st + S_FUSE, g_fuse, s, fuse_tile_);
       launch_fuse_copy<K>(dv->st + S_FUSE, c->num_sms * 8, s, fuse_tile_);
+      if (side_) {
+        if (!stage()) return syncs;
+        launch_plan_side(dv, s);
+        if (!stage()) return syncs;
+        launch_partition<K>(dv->st + S_FUSE2, 0, fuse_tile_, c->num_sms * 4, s);
+        if (!stage()) return syncs;
+        launch_diff_merge<K>(dv->st + S_FUSE2, g_fuse, s, fuse_tile_);
+      }
       mark();
       if (!stage()) return syncs;
       launch_plan_post(dv, s);
       if (!stage()) return syncs;
-      mark(); launch_merge<K>(dv->st + S_MERGE, g_merge, s); mark();  // retire copy
+      // retire copy, or with a side run the final merge of both runs
+      mark();
+      if (side_) launch_partition<K>(dv->st + S_MERGE, 0, kTileM, c->num_sms * 4, s);
+      launch_merge<K>(dv->st + S_MERGE, g_merge, s);
+      mark();
     } else {
       mark(); launch_unique_diff<K>(dv->st + S_UNIQ, g_uniq, s); mark();
       if (!stage()) return syncs;
@@ -990,11 +1045,54 @@ struct Engine : EngineBase {
   }
 
   // Grow the pools to what the aborted run asked for (plus headroom).
-  int grow() {
+  void grow_target(unsigned long long* wc, unsigned long long* wf, unsigned long long* wr) const {
     const unsigned long long nc = h.ctl.need_cand ? h.ctl.need_cand + h.ctl.need_cand / 4 + 4096 : 0;
     const unsigned long long nf = h.ctl.need_full ? h.ctl.need_full + h.ctl.need_full / 4 + 4096 : 0;
     const unsigned long long nr = h.ctl.need_res ? h.ctl.need_res + h.ctl.need_res / 2 + 4096 : 0;
-    return ensure(std::max(capC, nc), std::max(capF, nf), std::max(capR, nr), true);
+    *wc = std::max(capC, nc); *wf = std::max(capF, nf); *wr = std::max(capR, nr);
+  }
+  int grow() {
+    unsigned long long wc, wf, wr;
+    grow_target(&wc, &wf, &wr);
+    return ensure(wc, wf, wr, true);
+  }
+  size_t held() const override {
+    const DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
+                         &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b,
+                         &xsum_b, &mix_b, &G[0], &G[1]};
+    size_t b = 0;
+    for (const DBuf* x : all) b += x->bytes;
+    return b;
+  }
+  // The bytes grow() would make the engine hold at its peak: ensure()
+  // allocates each group of buffers before it releases the group it replaces
+  // (the optional side-run pools are left out).
+  size_t grow_peak() const override {
+    unsigned long long wantC, wantF, wantR;
+    grow_target(&wantC, &wantF, &wantR);
+    wantC = std::max<unsigned long long>(wantC, 1ull << 16);
+    wantF = std::max<unsigned long long>(wantF, 1ull << 16);
+    wantR = single ? 0 : std::max<unsigned long long>(wantR, 1ull << 16);
+    size_t cur = held(), peak = cur;
+    auto step = [&](size_t add, size_t drop) {
+      peak = std::max(peak, cur + add);
+      cur = cur + add - drop;
+    };
+    const unsigned long long nC = std::max(capC, wantC), nF = std::max(capF, wantF);
+    const size_t tiles = std::max<size_t>(nC / count_tile_, nF / fuse_tile_) + n_slots + 2;
+    if (tiles > mix_tiles)
+      step(round_up(tiles * 8) + round_up(2 * (tiles + 1) * 8) +
+               round_up((2 * tiles + 1 + tiles / kThreads + 2) * 4),
+           st_s.bytes + spl.bytes + mix_b.bytes);
+    if (wantC > capC)
+      step(4 * round_up(wantC * sizeof(K)) + round_up(wantC * 8) +
+               round_up((wantC / kTileC + std::max(n_slots, nv_cap) + 2) * kRadix * 8) +
+               (xseg ? round_up((wantC / kTileC + nv_cap + 2) * 4) : 0),
+           D[0].bytes + D[1].bytes + C[0].bytes + C[1].bytes + pos.bytes + st_k.bytes +
+               (xseg ? tseg_b.bytes : 0));
+    if (wantF > capF) step(2 * round_up(wantF * sizeof(K)), F[0].bytes + F[1].bytes);
+    if (!single && wantR > capR) step(round_up(wantR * sizeof(K)), R.bytes);
+    return peak;
   }
   // Take instance `slot` out of the running set (its state is dropped).
   int evict(uint32_t slot) {
@@ -1050,15 +1148,16 @@ static void drop_idle_engines(wg_ctx* c, size_t bytes) {
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
                               uint32_t logcap, bool fuse, bool xseg, int* rc,
-                              bool copyback = false, bool hashjoin = false) {
+                              bool copyback = false, bool hashjoin = false, uint32_t side = 0) {
   EngineBase* e;
   if (kb == 4) {
-    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback, hashjoin);
+    auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback, hashjoin,
+                                   side);
     *rc = x->init();
     e = x;
   } else {
     auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg, copyback,
-                                             hashjoin);
+                                             hashjoin, side);
     *rc = x->init();
     e = x;
   }
@@ -1117,8 +1216,18 @@ static int single_start(wg_ctx* c, Query* q) {
           else
             for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
           if (E->fuse) {
-            names.push_back({"dedup_diff_merge", (nc + 2 * nf + 2 * nn) * kb});
-            names.push_back({"retire_copy", E->copyback() ? 2 * (nf + nn) * kb : 0.0});
+            const double ns = (double)before.n_side, n0 = (double)after.n_new0;
+            const bool side = after.side_iter != 0;
+            const bool prem = !side && before.n_side > 0;
+            const bool fmerge = side && after.state != INST_ACTIVE && ns + nn > 0;
+            // side iteration: C and the main run read, the new candidates
+            // written, then the side run's pass (side run and those read, the
+            // new delta and the merged side run written); a pre-merge reads
+            // both runs and writes them merged
+            const double fused = side ? nc + (nf - ns) + 2 * n0 + 2 * ns + 2 * nn
+                                      : nc + 2 * nf + 2 * nn + (prem ? 2 * nf : 0.0);
+            names.push_back({"dedup_diff_merge", fused * kb});
+            names.push_back({"retire_copy", E->copyback() || fmerge ? 2 * (nf + nn) * kb : 0.0});
           } else {
             names.push_back({"dedup_diff", (nc + nn) * kb});
             names.push_back({"merge", 2 * (nf + nn) * kb});
@@ -1295,12 +1404,36 @@ static bool held_elsewhere(wg_ctx* c, int cls) {
   return solo_running(c);
 }
 
+// Whether the growth engine e's last run asked for could fit the budget once
+// the other engines' pools are released (the batch engines drained and
+// dropped, the idle engines freed, the served request running on a single
+// engine finished).  When it could not, waiting for them as the exclusive
+// query would only stall every other request before failing.
+static bool growth_could_fit(wg_ctx* c, const EngineBase* e) {
+  size_t others = 0;
+  for (auto& kv : c->batch)
+    if (kv.second && kv.second.get() != e) others += kv.second->held();
+  for (auto& x : c->idle)
+    if (x.get() != e) others += x->held();
+  if (c->solo_run) {
+    auto it = c->queries.find(c->solo_run);
+    if (it != c->queries.end() && it->second->eng && it->second->eng != e)
+      others += it->second->eng->held();
+  }
+  const size_t mine = e->held();
+  const size_t fixed = c->used > mine + others ? c->used - mine - others : 0;
+  return fixed + e->grow_peak() <= c->budget;
+}
+
 // Query q of class cls does not fit in its engine although it runs there
 // alone: while other engines hold pools it becomes the exclusive query (if
-// there is none yet) and stays queued; with the whole budget it fails.
+// there is none yet) and stays queued; with the whole budget it fails, and so
+// it does at once when the growth its engine's last run asked for (grown:
+// the failure came from that growth) could not fit even the whole budget.
 // True when it failed.
-static bool alone_too_large(wg_ctx* c, int cls, Query* q, int why) {
-  const bool others = held_elsewhere(c, cls);
+static bool alone_too_large(wg_ctx* c, int cls, Query* q, int why, bool grown = false) {
+  const bool others =
+      held_elsewhere(c, cls) && !(grown && !growth_could_fit(c, c->batch[cls].get()));
   if (c->excl == q->id || !others) {
     if (c->excl == q->id) c->excl = 0;
     q->state = WG_FAILED;
@@ -1417,7 +1550,7 @@ static int batch_preempt(wg_ctx* c, int cls, int why) {
   auto it = c->queries.find(qid);
   if (it == c->queries.end()) return WG_OK;
   Query* q = it->second.get();
-  if (active == 1 && alone_too_large(c, cls, q, why)) return WG_OK;
+  if (active == 1 && alone_too_large(c, cls, q, why, true)) return WG_OK;
   q->state = WG_PENDING;
   q->regrows += 1;
   c->pending.insert(c->pending.begin(), qid);
@@ -1520,7 +1653,8 @@ static int batch_grow(wg_ctx* c, int cls) {
   const bool others = held_elsewhere(c, cls);  // (idle engines were dropped above)
   const uint64_t qid = active == 1 ? g_binfo[c][cls].slot_q[slot] : 0;
   Query* x = excl_query(c);
-  if (qid && others && c->queries.count(qid) && (!x || x->id == qid)) {
+  // (a growth that could not fit even the whole budget fails in batch_preempt)
+  if (qid && others && growth_could_fit(c, E) && c->queries.count(qid) && (!x || x->id == qid)) {
     c->excl = qid;
     E->grow_wait = true;
     E->wait_used = c->used;
@@ -1853,6 +1987,10 @@ static int single_begin(wg_ctx* c, Query* q) {
   const bool full_width = (q->opts.flags & WG_FLAG_FULL_WIDTH) != 0;
   const bool copyback = fuse && (q->opts.flags & WG_FLAG_COPY_BACK) != 0;
   const bool hashjoin = kind == WG_TC && (q->opts.flags & WG_FLAG_HASH_JOIN) != 0;
+  // Full as a main run plus a side run of the newest tuples (fused stages,
+  // no copy-back): unless the query asks for the merge every iteration
+  const uint32_t side = !fuse || copyback || (q->opts.flags & WG_FLAG_MERGE_EVERY_ITER) ? 0u
+                        : (q->opts.flags & WG_FLAG_SIDE_RUN_ALWAYS) ? 2u : 1u;
   if (hashjoin && !R->htab.p) {
     // the table of E, built once per relation like its CSR: at most half full
     unsigned long long cap = 1024;
@@ -1884,14 +2022,15 @@ static int single_begin(wg_ctx* c, Query* q) {
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
         c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
         c->idle[i]->hashjoin() == hashjoin && c->idle[i]->count_tile() == ct &&
-        c->idle[i]->fuse_tile() == ft && c->idle[i]->sort_mode() == c->tune_sort[R->kb == 8]) {
+        c->idle[i]->fuse_tile() == ft && c->idle[i]->sort_mode() == c->tune_sort[R->kb == 8] &&
+        c->idle[i]->side_mode() == side) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
     }
   int rc = WG_OK;
   if (!q->own) {
     EngineBase* e = new_engine(c, R->kb, true, 1, bits, 1u << 16, fuse, xseg, &rc, copyback,
-                               hashjoin);
+                               hashjoin, side);
     if (!e) return rc;
     q->own.reset(e);
   }
@@ -2002,6 +2141,11 @@ static int solo_round(wg_ctx* c, bool* progressed, bool* busy) {
     }
     const int rc = k4 ? single_progress<uint32_t>(c, q, false, true)
                       : single_progress<unsigned long long>(c, q, false, true);
+    if (q->solo_wait && !growth_could_fit(c, q->eng)) {  // hopeless: fail now
+      solo_finish(c, q, set_err(WG_E_BUDGET, "the request does not fit the memory budget"));
+      *progressed = true;
+      return WG_OK;
+    }
     if (q->solo_wait) {  // paused: exclusive from now on, unless another query is
       Query* x = excl_query(c);
       if (x && x != q) solo_requeue(c, q);

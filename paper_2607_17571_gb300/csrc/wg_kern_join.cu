@@ -624,11 +624,12 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
 
 __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
   __shared__ unsigned long long sh[32];
-  __shared__ unsigned long long s_cc, s_ct, s_fc, s_ft, s_et;
+  __shared__ unsigned long long s_cc, s_ct, s_fc, s_ft, s_et, s_pt;
+  __shared__ uint32_t s_side;
   Ctl& ctl = dv->ctl;
   if (ctl.abort) return;
   const uint32_t N = dv->n_inst;
-  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; s_fc = 0; s_ft = 0; s_et = 0; }
+  if (threadIdx.x == 0) { s_cc = 0; s_ct = 0; s_fc = 0; s_ft = 0; s_et = 0; s_pt = 0; s_side = 0; }
   __syncthreads();
   for (uint32_t base = 0; base < N; base += kPlanThreads) {
     const uint32_t q = base + threadIdx.x;
@@ -668,17 +669,37 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     if (dv->fuse) {
       // fused dedup + diff + merge: Full' of q at an upper bound |Full| + |C|
       const unsigned long long nf = act ? I->n_full : 0ull, tf = dv->fuse_tile;
-      const unsigned long long ft = (nf + nc + tf - 1) / tf;
+      // Full as a main run and a side run (single-query engines, see Inst):
+      // with few candidates the pass reads the main run only and writes no
+      // Full' (k_plan_side then takes the side run); otherwise a side run
+      // left from earlier iterations is first merged into the main run
+      const unsigned long long ns = act ? I->n_side : 0ull, nf0 = nf - ns;
+      const bool side = dv->side && act && ns + nc <= dv->capG &&
+                        (ns + nc + tf - 1) / tf <= dv->mix_cap &&
+                        (dv->side == 2 || nc * kSideRatio <= nf0);
+      const bool prem = dv->side && act && !side && ns > 0;
+      const unsigned long long nfa = side ? nf0 : nf;  // keys of the run the pass reads
+      const unsigned long long ft = (nfa + nc + tf - 1) / tf;
       unsigned long long totf, totft;
       const unsigned long long exf = scan1024(nf + nc, sh, &totf);
       const unsigned long long exft = scan1024(ft, sh, &totft);
       if (valid) {
         Seg f{};
-        f.in_off = I->f_off; f.n = nf; f.aux_off = s_cc + exc; f.aux_n = nc;
+        f.in_off = I->f_off; f.n = nfa; f.aux_off = s_cc + exc; f.aux_n = nc;
         f.out_off = s_cc + exc; f.out2_off = s_fc + exf; f.res = 0;
         f.tile0 = (uint32_t)(s_ft + exft); f.ntiles = (uint32_t)ft; f.inst = q; f.flags = 0;
         dv->segF[q] = f;
+        if (act) I->side_iter = side ? 1u : 0u;
       }
+      if (prem) {  // both runs into the other Full pool at the same offset (one instance)
+        Seg m{};
+        m.in_off = I->f_off; m.n = nf0; m.aux_off = 0; m.aux_n = ns; m.out_off = I->f_off;
+        m.res = 0; m.tile0 = 0; m.ntiles = (uint32_t)((nf + kTileM - 1) / kTileM); m.inst = q;
+        m.flags = 0;
+        dv->segM[q] = m;
+        s_pt = m.ntiles;  // capacity: the merged run is the nf of the check below
+      }
+      if (side) s_side = 1;
       __syncthreads();
       if (threadIdx.x == 0) { s_fc += totf; s_ft += totft; }
     }
@@ -720,9 +741,25 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
       dv->st[S_PASS0 + p] = s;
     }
     if (dv->fuse) {
+      uint32_t fph = dv->fphase;
+      Stage pm = base;
+      pm.segs = dv->segM; pm.ntiles = 0;
+      if (s_pt) {  // fold the side run into the main run before the pass (one instance)
+        const Inst& I0 = dv->inst[0];
+        pm.in = dv->F[fph]; pm.aux = dv->G[I0.gphase]; pm.out = dv->F[fph ^ 1];
+        pm.ntiles = (uint32_t)s_pt; pm.splits = dv->splits;  // k_partition finds the tile splits
+        dv->inst[0].n_side = 0;
+        fph ^= 1u;
+        dv->fphase = fph;
+      }
+      dv->st[S_PREM] = pm;
       Stage f = base;
-      f.in = dv->F[dv->fphase]; f.aux = dv->C[dv->passes & 1];
-      f.out = dv->D[dv->dphase ^ 1]; f.out2 = dv->F[dv->fphase ^ 1];
+      f.in = dv->F[fph]; f.aux = dv->C[dv->passes & 1];
+      if (s_side) {  // new w.r.t. the main run into the spare candidate pool; no Full'
+        f.out = dv->C[(dv->passes & 1) ^ 1]; f.out2 = nullptr;
+      } else {
+        f.out = dv->D[dv->dphase ^ 1]; f.out2 = dv->F[fph ^ 1];
+      }
       f.segs = dv->segF; f.status = dv->status_scalar; f.epoch = ++ctl.epoch;
       f.ntiles = (uint32_t)s_ft; f.splits = dv->splits;
       f.mixl = dv->mixl; f.mixc = dv->mixc;
@@ -866,12 +903,44 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_merge(Dev* dv) {
   }
 }
 
+// Side iteration (single-query engines, one instance), after the main run's
+// pass: its output -- the candidates new with respect to the main run,
+// deduplicated and sorted, in the spare candidate pool -- against the side
+// run.  One more fused pass over (side run, that output) keeps what the side
+// run lacks (the new delta) and writes the merged side run to the other side
+// pool.  Every tile is classified (no mixed-tile list: the runs are small).
+__global__ void k_plan_side(Dev* dv) {
+  Ctl& ctl = dv->ctl;
+  if (ctl.abort || threadIdx.x != 0) return;
+  Inst* I = dv->inst;
+  const bool act = I->state == INST_ACTIVE && I->side_iter;
+  const unsigned long long n0 = act ? dv->segF[0].res : 0ull, ns = act ? I->n_side : 0ull;
+  const unsigned long long tf = dv->fuse_tile;
+  Seg f{};
+  f.in_off = 0; f.n = ns; f.aux_off = I->c_off; f.aux_n = n0; f.out_off = I->c_off;
+  f.out2_off = 0; f.res = 0; f.tile0 = 0; f.inst = 0; f.flags = 0;
+  f.ntiles = act ? (uint32_t)((ns + n0 + tf - 1) / tf) : 0u;
+  dv->segF2[0] = f;
+  if (act) I->n_new0 = n0;
+  Stage s{};
+  s.segs = dv->segF2; s.inst = dv->inst; s.ctl = &dv->ctl; s.nseg = 1; s.ntiles = f.ntiles;
+  s.ctr = 0; s.in = dv->G[I->gphase]; s.aux = dv->C[(dv->passes & 1) ^ 1];
+  s.out = dv->D[dv->dphase ^ 1]; s.out2 = dv->G[I->gphase ^ 1];
+  s.status = dv->status_scalar; s.epoch = ++ctl.epoch; s.splits = dv->splits;
+  s.mixl = nullptr; s.mixc = nullptr;
+  dv->st[S_FUSE2] = s;
+}
+
 // After the fused stage: commit the iteration (log, termination, new delta,
 // Full' as the full relation) and schedule the copy of finished batch
-// instances into the retire pool.
+// instances into the retire pool.  After a side iteration the main run stays
+// where it is and the merged side run becomes the side run; when that
+// iteration ends the fixpoint, the final relation is the merge of both runs
+// (scheduled here as the S_MERGE stage) unless the side run is empty.
 __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
   __shared__ unsigned long long sh[32];
   __shared__ unsigned long long s_r, s_t, s_act;
+  __shared__ uint32_t s_keep, s_fmerge;
   Ctl& ctl = dv->ctl;
   if (ctl.abort) {
     if (threadIdx.x == 0) set_continue(dv, 0);
@@ -907,35 +976,48 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
   }
   const uint32_t fph = dv->fphase, dph = dv->dphase;
   __syncthreads();
-  if (threadIdx.x == 0) { s_r = dv->r_used; s_t = 0; s_act = 0; }
+  if (threadIdx.x == 0) { s_r = dv->r_used; s_t = 0; s_act = 0; s_keep = 0; s_fmerge = 0; }
   __syncthreads();
   for (uint32_t base = 0; base < N; base += kPlanThreads) {
     const uint32_t q = base + threadIdx.x;
     const bool valid = q < N;
     Inst* I = valid ? dv->inst + q : nullptr;
     const bool act = valid && I->state == INST_ACTIVE;
-    unsigned long long nn = 0, nf = 0, rsz = 0, mt = 0;
-    bool fin = false, done = false, toR = false;
+    unsigned long long nn = 0, nf = 0, rsz = 0, mt = 0, ns1 = 0;
+    bool fin = false, done = false, toR = false, side = false, fmerge = false;
     if (act) {
-      nn = dv->segF[q].res;
+      side = I->side_iter != 0;
+      nn = side ? dv->segF2[q].res : dv->segF[q].res;
       nf = I->n_full + nn;
       done = I->iter >= 1 && nn == 0;
       fin = done || I->iter >= I->max_iters;
       toR = fin && !single;
       if (toR || dv->copyback) { rsz = nf; mt = (nf + kTileM - 1) / kTileM; }
+      if (side) {  // single-query engine: neither toR nor copyback
+        ns1 = I->n_side + nn;
+        fmerge = fin && ns1 > 0;
+        if (fmerge) mt = (nf + kTileM - 1) / kTileM;
+      }
     }
     unsigned long long tr, tt, ta;
     const unsigned long long exr = scan1024(rsz, sh, &tr);
     const unsigned long long ext = scan1024(mt, sh, &tt);
     scan1024((act && !fin) ? 1ull : 0ull, sh, &ta);
     if (valid) {
-      const unsigned long long fo = dv->segF[q].out2_off;
+      const unsigned long long fo = side ? I->f_off : dv->segF[q].out2_off;
       Seg m{};
-      m.in_off = fo; m.n = rsz; m.aux_off = 0; m.aux_n = 0; m.res = 0; m.out2_off = 0;
-      // the retire copy (batch: to the result pool) or, copying back, Full'
-      // onto the same offsets of the Full buffer
-      m.out_off = dv->copyback ? fo : s_r + exr; m.tile0 = (uint32_t)(s_t + ext);
-      m.ntiles = (uint32_t)mt; m.inst = q; m.flags = 1u;
+      if (fmerge) {  // the final relation: main run and side run, merged
+        m.in_off = fo; m.n = nf - ns1; m.aux_off = 0; m.aux_n = ns1; m.out_off = fo;
+        m.flags = 0;
+      } else {
+        // the retire copy (batch: to the result pool) or, copying back,
+        // Full' onto the same offsets of the Full buffer
+        m.in_off = fo; m.n = rsz; m.aux_off = 0; m.aux_n = 0;
+        m.out_off = dv->copyback ? fo : s_r + exr;
+        m.flags = 1u;
+      }
+      m.res = 0; m.out2_off = 0; m.tile0 = (uint32_t)(s_t + ext);
+      m.ntiles = (uint32_t)mt; m.inst = q;
       dv->segM[q] = m;
       if (act) {
         const uint32_t it = I->iter;
@@ -947,15 +1029,27 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
         if (fin) {
           I->state = done ? INST_DONE : INST_ITERCAP;
           I->iters_done = it;
-          I->res_pool = toR ? 2u : dv->copyback ? fph : (fph ^ 1u);
-          I->res_off = toR ? s_r + exr : fo;
+          if (side) {  // in place when nothing is in the side run
+            I->res_pool = fmerge ? (fph ^ 1u) : fph;
+            I->res_off = fo;
+            I->n_side = 0;
+          } else {
+            I->res_pool = toR ? 2u : dv->copyback ? fph : (fph ^ 1u);
+            I->res_off = toR ? s_r + exr : fo;
+          }
           I->n_delta = 0;
         } else {
+          if (side) {
+            I->n_side = ns1;
+            I->gphase ^= 1u;
+          }
           I->d_off = I->c_off;
           I->n_delta = nn;
           I->iter = it + 1;
         }
       }
+      if (side && !fmerge) s_keep = 1;  // the main run stays in pool fph
+      if (fmerge) s_fmerge = 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) { s_r += tr; s_t += tt; s_act += ta; }
@@ -965,11 +1059,15 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_post(Dev* dv) {
     Stage m{};
     m.in = dv->F[fph ^ 1]; m.aux = nullptr; m.out = dv->R;
     m.out2 = dv->copyback ? dv->F[fph] : dv->R;
+    if (s_fmerge) {  // one instance: its side run is in G[gphase ^ 1] (not swapped when final)
+      m.in = dv->F[fph]; m.aux = dv->G[dv->inst[0].gphase ^ 1u]; m.out = dv->F[fph ^ 1];
+      m.out2 = nullptr; m.splits = dv->splits;  // k_partition finds the tile splits
+    }
     m.segs = dv->segM; m.inst = dv->inst; m.ctl = &dv->ctl; m.nseg = N;
     m.ntiles = (uint32_t)s_t; m.ctr = 0;
     dv->st[S_MERGE] = m;
     dv->r_used = s_r;
-    dv->fphase = dv->copyback ? fph : fph ^ 1u;
+    dv->fphase = (dv->copyback || s_keep) ? fph : fph ^ 1u;
     dv->dphase = dph ^ 1u;
     ctl.n_active = (uint32_t)s_act;
     ctl.launch_iters += 1;
@@ -1108,6 +1206,7 @@ void launch_plan_delta(Dev* dv, cudaStream_t s) { k_plan_delta<<<1, kPlanThreads
 void launch_plan_cand(Dev* dv, cudaStream_t s) { k_plan_cand<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_merge(Dev* dv, cudaStream_t s) { k_plan_merge<<<1, kPlanThreads, 0, s>>>(dv); }
 void launch_plan_post(Dev* dv, cudaStream_t s) { k_plan_post<<<1, kPlanThreads, 0, s>>>(dv); }
+void launch_plan_side(Dev* dv, cudaStream_t s) { k_plan_side<<<1, 32, 0, s>>>(dv); }
 void launch_xseg_build(Dev* dv, cudaStream_t s) {
   k_xseg_sum<<<kXChunks, kXChunk, 0, s>>>(dv);
   k_xseg_fill<<<kXChunks, kXChunk, 0, s>>>(dv);

@@ -1067,11 +1067,13 @@ __device__ __forceinline__ void fuse_write(Stage* stp, const K* sbuf, const uint
     const uint32_t e = __ffs(nb) - 1;
     *no++ = sbuf[pad32(wk0 + __popc(kept & ((1u << e) - 1u)))];
   }
-  K* fo = Fall + sg.out2_off + m.a0 + exN;
+  if (Fall) {  // no Full' when the pass only finds what the main run lacks (side iteration)
+    K* fo = Fall + sg.out2_off + m.a0 + exN;
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const uint32_t i = threadIdx.x + e * kThreads;
-    if (i < m.totK) fo[i] = sbuf[pad32(i)];
+    for (int e = 0; e < E; ++e) {
+      const uint32_t i = threadIdx.x + e * kThreads;
+      if (i < m.totK) fo[i] = sbuf[pad32(i)];
+    }
   }
   if (threadIdx.x == 0 && m.last) stp->segs[m.k].res = exN + m.totN;
 }
@@ -1196,6 +1198,7 @@ __global__ void __launch_bounds__(kThreads) k_fuse_copy(Stage* stp) {
   const uint32_t ntiles = stp->ntiles;
   const K* Aall = (const K*)stp->in;
   K* Fall = (K*)stp->out2;
+  if (!Fall) return;  // side iteration: no Full' is written
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     if (stp->mixc[t + 1] != stp->mixc[t]) continue;  // mixed: k_diff_merge wrote it
     const uint32_t k = find_seg(stp->segs, stp->nseg, t, stp->tile_seg);

@@ -57,6 +57,7 @@ void launch_plan_delta(Dev* dv, cudaStream_t s);
 void launch_plan_cand(Dev* dv, cudaStream_t s);
 void launch_plan_merge(Dev* dv, cudaStream_t s);
 void launch_plan_post(Dev* dv, cudaStream_t s);
+void launch_plan_side(Dev* dv, cudaStream_t s);
 void launch_xseg_build(Dev* dv, cudaStream_t s);
 template <typename K>
 void launch_init_diag(Inst* inst, uint32_t first, uint32_t count, void* dpool, cudaStream_t s);

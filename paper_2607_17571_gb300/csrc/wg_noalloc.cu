@@ -45,12 +45,12 @@ constexpr size_t kNoAllocMaxKeys = WG_NOALLOC_MAX_KEYS;
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-// Scratch layout: Stage[S_NUM] | Seg | Ctl | sticky error word |
+// Scratch layout: Stage[S_SORT_END] | Seg | Ctl | sticky error word |
 // hist u64[kMaxPasses*kRadix] | status u64[(tiles+1)*kRadix] |
 // ping-pong keys (8-byte keys, kNoAllocMaxKeys)
 constexpr size_t kTiles = (kNoAllocMaxKeys + kTileC - 1) / kTileC;
 constexpr size_t kOffStage = 0;
-constexpr size_t kOffSeg = align_up(kOffStage + sizeof(Stage) * S_NUM);
+constexpr size_t kOffSeg = align_up(kOffStage + sizeof(Stage) * S_SORT_END);
 constexpr size_t kOffCtl = align_up(kOffSeg + sizeof(Seg));
 constexpr size_t kOffSticky = align_up(kOffCtl + sizeof(Ctl));
 constexpr size_t kOffHist = align_up(kOffSticky + sizeof(uint32_t));

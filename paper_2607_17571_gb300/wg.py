@@ -26,6 +26,8 @@ WG_FLAG_SEPARATE_STAGES = 1
 WG_FLAG_FULL_WIDTH = 2
 WG_FLAG_COPY_BACK = 4
 WG_FLAG_HASH_JOIN = 8
+WG_FLAG_MERGE_EVERY_ITER = 16
+WG_FLAG_SIDE_RUN_ALWAYS = 32
 WG_PENDING, WG_RUNNING, WG_DONE, WG_FAILED = 0, 1, 2, 3
 WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES = 0, 1, 2
 ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPACITY",
@@ -132,10 +134,15 @@ def _check(rc, where):
 
 
 def _opts(max_iters=0, loop=WG_LOOP_DEVICE, profile=False, reserve_full=0, reserve_cand=0,
-          separate_stages=False, full_width=False, copy_back=False, hash_join=False):
+          separate_stages=False, full_width=False, copy_back=False, hash_join=False,
+          side_run="auto"):
+    if side_run not in ("auto", "never", "always"):
+        raise ValueError(f"side_run must be 'auto', 'never' or 'always', got {side_run!r}")
     flags = ((WG_FLAG_SEPARATE_STAGES if separate_stages else 0) |
              (WG_FLAG_FULL_WIDTH if full_width else 0) | (WG_FLAG_COPY_BACK if copy_back else 0) |
-             (WG_FLAG_HASH_JOIN if hash_join else 0))
+             (WG_FLAG_HASH_JOIN if hash_join else 0) |
+             (WG_FLAG_MERGE_EVERY_ITER if side_run == "never" else 0) |
+             (WG_FLAG_SIDE_RUN_ALWAYS if side_run == "always" else 0))
     return wg_opts(max_iters, loop, 1 if profile else 0, flags, reserve_full, reserve_cand)
 
 

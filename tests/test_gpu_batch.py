@@ -142,6 +142,30 @@ def test_query_larger_than_budget_fails_cleanly():
         assert np.array_equal(hs.result(), oracle_tc(small.src, small.dst).keys)
 
 
+def test_hopeless_large_request_fails_beside_small_ones():
+    """A served request over 65,536 edges whose closure cannot fit the budget
+    even alone fails with a budget error as soon as its growth is refused
+    (it does not wait for the other engines to drain), and the small requests
+    submitted around it complete with the oracle's results."""
+    from paper_2607_17571_gb300 import wg
+    big = I.er_graph(30000, 70000, 8)  # a giant component: ~5e8 tuples
+    smalls = [I.er_graph(n, 3 * n, 500 + n) for n in (200, 400, 600, 800, 300, 700)]
+    want = [oracle_tc(g.src, g.dst) for g in smalls]
+    with wg.Context(0, mem_budget=256 << 20) as c:
+        rb = c.load(big.src, big.dst)
+        rs = [c.load(g.src, g.dst) for g in smalls]
+        hs = c.submit([(wg.WG_TC, r) for r in rs[:3]] + [(wg.WG_TC, rb)] +
+                      [(wg.WG_TC, r) for r in rs[3:]])
+        with pytest.raises(wg.WgError) as e:
+            hs[3].wait()
+        assert e.value.code in (wg.WG_E_BUDGET, wg.WG_E_NOMEM)
+        hs[3].free()
+        for h, w in zip(hs[:3] + hs[4:], want):
+            h.wait()
+            assert np.array_equal(h.result(), w.keys) and h.delta_sizes() == w.log.tolist()
+            h.free()
+
+
 @functools.lru_cache(maxsize=1)
 def _growth_cases():
     gs = [I.er_graph(n, 3 * n, 90 + n) for n in (800, 1400, 2000, 2600)]  # 0.6 .. 6.0 M tuples

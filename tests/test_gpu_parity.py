@@ -243,6 +243,21 @@ def test_repeated_regrowth_from_tiny_pools(separate):
                   reserve_full=1)
 
 
+def test_overflow_in_the_first_iteration():
+    # SG on a star: the base rule alone makes 1,500 * 1,499 candidates, far
+    # over the first pools, so the very first plan kernel stops the run --
+    # before any later stage record has been written by a plan kernel -- and
+    # the engine grows and starts over (a fresh context: no cached capacities)
+    from paper_2607_17571_gb300 import wg
+    hub = np.zeros(1500, dtype=np.uint32)
+    leaves = np.arange(1, 1501, dtype=np.uint32)
+    with wg.Context(0) as c:
+        for opts in (dict(), dict(separate_stages=True), dict(side_run="never")):
+            st, _ = check(c, "sg", hub, leaves, **opts)
+            assert st.n_tuples == 1500 * 1499 and st.regrows >= 1
+        st, _ = check(c, "sg", hub, leaves, loop=wg.WG_LOOP_HOST_STAGED)
+
+
 def test_result_digest_matches_the_oracle(ctx):
     # the device digest of a result equals the digest of the oracle's sorted
     # closure (semi-naive and reachability forms), for both key widths
