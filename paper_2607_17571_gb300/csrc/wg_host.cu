@@ -1207,12 +1207,18 @@ static int single_start(wg_ctx* c, Query* q) {
           const double nd = (double)before.n_delta, nc = (double)after.n_cand,
                        nn = (double)after.n_new, nf = (double)before.n_full;
           // algorithmic bytes of each kernel (see the kernel headers)
+          // the per-segment sort reads its keys once more to count their
+          // digits (the histogram kernel then returns at once)
+          uint32_t maxt = 0;
+          if (E->xgrouped() && E->h.seg_sort)
+            CK(cudaMemcpy(&maxt, &E->dv->xseg_maxt, 4, cudaMemcpyDeviceToHost));
+          const bool seg = E->xgrouped() && E->h.seg_sort && maxt <= kSegSortMaxTiles;
           std::vector<std::pair<const char*, double>> names = {
               {"join_count", nd * (kb + 8 + 8)},
               {"join_emit", nd * (kb + 8) + nc * (kb + 4)},
-              {"sort_hist", nc * kb}};
+              {"sort_hist", seg ? 0.0 : nc * kb}};
           if (E->xgrouped())  // every pass in one timed region (k_sort_seg or the passes)
-            names.push_back({"sort_pass", E->passes * 2 * nc * kb});
+            names.push_back({"sort_pass", (E->passes * 2 + (seg ? 1 : 0)) * nc * kb});
           else
             for (uint32_t p = 0; p < E->passes; ++p) names.push_back({"sort_pass", 2 * nc * kb});
           if (E->fuse) {

@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(kThreads, 6) k_sort_hist(Stage* stp) {
   __shared__ uint32_t s_t, s_n;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
+  // the per-segment sort counts its segments' digits itself
+  if (stp->maxt && *stp->maxt <= kSegSortMaxTiles) return;
   const K* in = (const K*)stp->in;
   const uint32_t passes = stp->passes, nseg = stp->nseg, ntiles = stp->ntiles;
   const uint32_t np = stp->maxt ? passes : 1u;  // digits counted per key
@@ -450,12 +452,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 // Many segments of at most kSegSortMaxTiles tiles (the per-source segments of
 // the x-grouped sort): one CTA takes a whole segment through every pass, its
 // tiles in order, so each digit's next output offset in the segment is a
-// running count in shared memory -- no lookback and no status words; the
-// histogram kernel counted every pass's digits.  Every pass after the first ranks
-// stably within a tile and takes the tiles in order, so it is stable.  A CTA
-// claims the segments of at least kSegBig tiles first, then the others, so
-// the longest ones do not start last.  NT threads of IT keys each make a tile.
+// running count in shared memory -- no lookback and no status words.  The CTA
+// first counts every pass's digits of its segment in one read (which also
+// brings the segment into L2 for the first pass); the histogram kernel then
+// has nothing to do.  Every pass after the first ranks stably within a tile
+// and takes the tiles in order, so it is stable.  A CTA claims the segments of
+// at least kSegBig tiles first, then the others, so the longest ones do not
+// start last.  NT threads of IT keys each make a tile.
 constexpr uint32_t kSegBig = 16;
+// the per-source segments sort fields of at most 18 bits (kXSegMaxVertices):
+// at most three passes
+constexpr uint32_t kSegMaxPasses = 3;
 // two compiled shapes (engine setting, wg_set_sort): 256 threads of 16 keys
 // at 4 CTAs per SM (64 registers) or of 8 keys at 6 CTAs per SM (40)
 constexpr int kSegNT = 256;
@@ -468,6 +475,7 @@ struct SegSmem {
   uint32_t wbase[NW][kRadix];     // per-warp counters -> tile-local start of (warp, digit)
   uint32_t gdst[kRadix];          // output offset in the segment minus the digit's tile start
   uint32_t run[kRadix];           // next output offset of each digit in the segment
+  uint32_t hc[kSegMaxPasses][kRadix];  // the segment's count of each digit, per pass
   uint32_t s_scan[NW];
   uint32_t s_k;
 };
@@ -626,6 +634,31 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&k
   __syncthreads();
 }
 
+// Every pass's digit counts of a segment of n keys at p, into S.hc (one read).
+template <typename K, bool kByte, int NT, int IT>
+__device__ __forceinline__ void seg_count(SegSmem<K, NT, IT>& S, const K* p, uint32_t n,
+                                          uint32_t passes, uint32_t dbits) {
+  constexpr uint32_t TILE = NT * IT;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t wb = warp * 32 * IT + lane;
+  for (uint32_t i = threadIdx.x; i < kSegMaxPasses * kRadix; i += NT) (&S.hc[0][0])[i] = 0;
+  __syncthreads();
+  for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
+    const uint32_t tn = min(n - t0, TILE);
+    K key[IT];
+    seg_load<K, NT, IT>(p + t0, tn, key);
+#pragma unroll
+    for (uint32_t ps = 0; ps < kSegMaxPasses; ++ps) {
+      if (ps >= passes) break;
+      const Digit dg(ps * dbits, dbits);
+#pragma unroll
+      for (int i = 0; i < IT; ++i)
+        if (wb + i * 32 < tn) atomicAdd(&S.hc[ps][dg.operator()<kByte>(key[i])], 1u);
+    }
+  }
+  __syncthreads();
+}
+
 template <typename K, bool kByte, int NT, int IT>
 __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint32_t k) {
   using D = SegDig<NT>;
@@ -634,6 +667,7 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
   const unsigned long long in_off = sg.in_off, out_off = sg.out_off;
   const uint32_t n = (uint32_t)sg.n, passes = st0->passes, dbits = st0->dbits;
   const uint32_t nt = (n + TILE - 1) / TILE;
+  seg_count<K, kByte, NT, IT>(S, (const K*)st0->in + in_off, n, passes, dbits);
   for (uint32_t p = 0; p < passes; ++p) {
     const Stage* sp = st0 + p;
     const K* in = (const K*)sp->in + in_off;
@@ -641,13 +675,13 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
     const Digit dg(sp->shift, dbits);
     K key[IT];
     seg_load<K, NT, IT>(in, min(n, TILE), key);
-    // the segment's count of each digit in this pass (the histogram kernel
-    // counted every pass); their scan starts the running counts
+    // the segment's count of each digit in this pass; their scan starts
+    // the running counts
     uint32_t c[D::DPT], csum = 0;
     if (D::owns()) {
 #pragma unroll
       for (int j = 0; j < D::DPT; ++j) {
-        c[j] = (uint32_t)st0->hist[((unsigned long long)k * passes + p) * kRadix + D::first() + j];
+        c[j] = S.hc[p][D::first() + j];
         csum += c[j];
       }
     }
