@@ -81,6 +81,10 @@ struct wg_ctx {
   std::map<uint64_t, std::unique_ptr<Query>> queries;
   std::vector<std::unique_ptr<EngineBase>> idle;  // single-query engines ready for reuse
   std::map<int, std::unique_ptr<EngineBase>> batch;  // batch engines by key class
+  // one stream per batch key class, kept across engine rebuilds: an allocator
+  // that caches freed blocks per stream (PyTorch's) can then hand a rebuilt
+  // engine the blocks its predecessor freed instead of allocating anew
+  std::map<int, cudaStream_t> class_st;
   std::vector<uint64_t> pending;                  // submitted, not yet admitted
   std::vector<uint64_t> completed;                // batch queries finished, not yet taken
   uint64_t excl = 0;  // batch query that runs with the whole budget (0: none), see batch_preempt
@@ -578,11 +582,13 @@ struct Engine : EngineBase {
     }
   }
 
-  int init() {
+  int init(cudaStream_t stream = nullptr) {
     if (!st) {
       if (single) {
         st = c->stream;
-      } else {  // batch engines run on their own stream, concurrently with each other
+      } else if (stream) {  // batch engines run on their class's stream, concurrently
+        st = stream;
+      } else {
         CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         own_st = true;
       }
@@ -1148,17 +1154,18 @@ static void drop_idle_engines(wg_ctx* c, size_t bytes) {
 
 static EngineBase* new_engine(wg_ctx* c, int kb, bool single, uint32_t slots, uint32_t bits,
                               uint32_t logcap, bool fuse, bool xseg, int* rc,
-                              bool copyback = false, bool hashjoin = false, uint32_t side = 0) {
+                              bool copyback = false, bool hashjoin = false, uint32_t side = 0,
+                              cudaStream_t stream = nullptr) {
   EngineBase* e;
   if (kb == 4) {
     auto* x = new Engine<uint32_t>(c, single, slots, bits, logcap, fuse, xseg, copyback, hashjoin,
                                    side);
-    *rc = x->init();
+    *rc = x->init(stream);
     e = x;
   } else {
     auto* x = new Engine<unsigned long long>(c, single, slots, bits, logcap, fuse, xseg, copyback,
                                              hashjoin, side);
-    *rc = x->init();
+    *rc = x->init(stream);
     e = x;
   }
   if (*rc != WG_OK) { delete e; return nullptr; }
@@ -1797,8 +1804,10 @@ static int serve_round(wg_ctx* c, uint32_t iters) {
 static int ensure_batch_engine(wg_ctx* c, int cls, Relation* R) {
   if (c->batch[cls]) return WG_OK;
   int rc = WG_OK;
+  cudaStream_t& cs = c->class_st[cls];
+  if (!cs) CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   EngineBase* e = new_engine(c, R->kb, false, kBatchSlots, class_bits(cls), kBatchLogCap, true,
-                             false, &rc);
+                             false, &rc, false, false, 0, cs);
   if (!e) return rc;
   c->batch[cls].reset(e);
   g_binfo[c][cls].slot_q.assign(kBatchSlots, 0);
@@ -1893,6 +1902,11 @@ void wg_destroy(wg_ctx* c) {
   c->idle.clear();
   for (auto& kv : c->batch) if (kv.second) kv.second->release();
   c->batch.clear();
+  for (auto& kv : c->class_st) {
+    cudaStreamSynchronize(kv.second);
+    cudaStreamDestroy(kv.second);
+  }
+  c->class_st.clear();
   g_binfo.erase(c);
   for (auto& kv : c->rels) kv.second->release(c);
   c->rels.clear();
