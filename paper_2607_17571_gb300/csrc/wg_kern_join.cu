@@ -124,11 +124,15 @@ __global__ void __launch_bounds__(kThreads) k_join_emit_hash(Stage* stp) {
 // ------------------------------------------------------------------ join count
 // ITEMS delta tuples per thread: a tile of kThreads * ITEMS (the tile shape
 // is an engine setting the autotuner picks; kItemsD by default).
+// Shared layouts padded against bank conflicts: each thread reads its ITEMS
+// consecutive tuples (one pad word per 32 keys) and writes their 64-bit slab
+// offsets (one pad offset per 16).
+__device__ __forceinline__ uint32_t pad16(uint32_t i) { return i + (i >> 4); }
 template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
   constexpr int kTile = kThreads * ITEMS;
-  __shared__ K sd[kTile];
-  __shared__ unsigned long long sp[kTile];
+  __shared__ K sd[Padded<kTile>::n];
+  __shared__ unsigned long long sp[kTile + kTile / 16];
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ unsigned long long s_excl;
   __shared__ uint32_t s_xprev, s_xnext;  // sources of the delta tuples around the tile
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     const unsigned long long start = (unsigned long long)(t - sg.tile0) * kTile;
     const uint32_t n = (uint32_t)min((unsigned long long)kTile, sg.n - start);
     const K* p = D + sg.in_off + start;
-    tile_to_smem<ITEMS>(sd, p, n, Ident());
+    tile_to_smem<ITEMS>(sd, p, n, Pad32());
     if (threadIdx.x == 0) {
       s_bad = 0;
       s_xprev = start > 0 ? (uint32_t)(p[-1] >> w) : 0xFFFFFFFFu;
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     for (int i = 0; i < ITEMS; ++i) {
       c[i] = 0;
       if (b + i < n) {
-        const K key = sd[b + i];
+        const K key = sd[pad32(b + i)];
         const uint32_t x = (uint32_t)(key >> w), y = (uint32_t)(key & mask);
         if (kind == KIND_TC) {
           c[i] = stp->htab ? hash_count(stp->htab, stp->hmask, y) : deg(off, y);  // T(x,y), E(y,z)
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     unsigned long long run = s_excl + texcl;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
-      if (b + i < n) { sp[b + i] = run; run += c[i]; }
+      if (b + i < n) { sp[pad16(b + i)] = run; run += c[i]; }
     if (stp->xlen) {
       // candidates per source x.  Delta is sorted by x, so x's tuples are one
       // run and its total is (prefix at the run's end) - (prefix at its
@@ -210,9 +214,9 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
 #pragma unroll
       for (int i = 0; i < ITEMS; ++i) {
         if (b + i < n) {
-          const uint32_t x = (uint32_t)(sd[b + i] >> w);
-          const uint32_t xp = b + i > 0 ? (uint32_t)(sd[b + i - 1] >> w) : s_xprev;
-          const uint32_t xn = b + i + 1 < n ? (uint32_t)(sd[b + i + 1] >> w) : s_xnext;
+          const uint32_t x = (uint32_t)(sd[pad32(b + i)] >> w);
+          const uint32_t xp = b + i > 0 ? (uint32_t)(sd[pad32(b + i - 1)] >> w) : s_xprev;
+          const uint32_t xn = b + i + 1 < n ? (uint32_t)(sd[pad32(b + i + 1)] >> w) : s_xnext;
           if (x != xp) atomicAdd(stp->xlen + x, 0ull - r);
           r += c[i];
           if (x != xn) atomicAdd(stp->xlen + x, r);
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 6) k_join_count(Stage* stp) {
     }
     __syncthreads();
     unsigned long long* q = pos + sg.in_off + start;
-    for (uint32_t i = threadIdx.x; i < n; i += kThreads) q[i] = sp[i];
+    for (uint32_t i = threadIdx.x; i < n; i += kThreads) q[i] = sp[pad16(i)];
     if (threadIdx.x == 0 && t == sg.tile0 + sg.ntiles - 1) stp->segs[k].res = s_excl + tot;
   }
 }

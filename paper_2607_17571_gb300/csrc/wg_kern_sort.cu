@@ -555,7 +555,7 @@ __device__ __forceinline__ void seg_load(const K* p, uint32_t n, K (&key)[IT]) {
 // One tile of one pass: rank (unstable for the first pass, stable after),
 // count the next pass's digits, place the keys in digit order, compute their
 // output offsets from the running counts.  The caller writes the tile out.
-template <typename K, bool kByte, int NT, int IT>
+template <typename K, bool kByte, bool kFull, int NT, int IT>
 __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&key)[IT],
                                               uint32_t n, const Digit& dg, bool first_pass) {
   using D = SegDig<NT>;
@@ -576,12 +576,12 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&k
   if (first_pass) {
 #pragma unroll
     for (int i = 0; i < IT; ++i)
-      if (wb + i * 32 < n)
+      if (kFull || wb + i * 32 < n)
         rk[i >> 1] |= atomicAdd(&wc[dg.operator()<kByte>(key[i])], 1u) << (16 * (i & 1));
   } else {
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
-      const bool ok = wb + i * 32 < n;
+      const bool ok = kFull || wb + i * 32 < n;
       const uint32_t d = ok ? dg.operator()<kByte>(key[i]) : 0xFFFFFFFFu;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t before = 0;
@@ -629,7 +629,7 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&k
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < IT; ++i)
-    if (wb + i * 32 < n)
+    if (kFull || wb + i * 32 < n)
       S.sk[wc[dg.operator()<kByte>(key[i])] + ((rk[i >> 1] >> (16 * (i & 1))) & 0xFFFFu)] = key[i];
   __syncthreads();
 }
@@ -651,9 +651,14 @@ __device__ __forceinline__ void seg_count(SegSmem<K, NT, IT>& S, const K* p, uin
     for (uint32_t ps = 0; ps < kSegMaxPasses; ++ps) {
       if (ps >= passes) break;
       const Digit dg(ps * dbits, dbits);
+      if (tn == TILE) {
 #pragma unroll
-      for (int i = 0; i < IT; ++i)
-        if (wb + i * 32 < tn) atomicAdd(&S.hc[ps][dg.operator()<kByte>(key[i])], 1u);
+        for (int i = 0; i < IT; ++i) atomicAdd(&S.hc[ps][dg.operator()<kByte>(key[i])], 1u);
+      } else {
+#pragma unroll
+        for (int i = 0; i < IT; ++i)
+          if (wb + i * 32 < tn) atomicAdd(&S.hc[ps][dg.operator()<kByte>(key[i])], 1u);
+      }
     }
   }
   __syncthreads();
@@ -696,7 +701,8 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
     __syncthreads();
     for (uint32_t j = 0; j < nt; ++j) {
       const uint32_t tn = min(n - j * TILE, TILE);
-      seg_rank_tile<K, kByte, NT, IT>(S, key, tn, dg, p == 0);
+      if (tn == TILE) seg_rank_tile<K, kByte, true, NT, IT>(S, key, tn, dg, p == 0);
+      else seg_rank_tile<K, kByte, false, NT, IT>(S, key, tn, dg, p == 0);
       if (j + 1 < nt)  // the next tile's loads fly during this tile's stores
         seg_load<K, NT, IT>(in + (unsigned long long)(j + 1) * TILE, min(n - (j + 1) * TILE, TILE), key);
       if (tn == TILE) {
