@@ -351,8 +351,8 @@ def autotune_ctx(ctx, rels, kind=None):
     out = {}
     for kb, (i, _) in sorted(best.items()):
         t = ctx.autotune(rels[i], wg.WG_TC if kind is None else kind)
-        out[f"{kb}B_keys"] = {k: t[k] for k in ("count_tile", "fuse_tile", "sort_mode", "count_ms",
-                                                 "fuse_ms", "sort_ms")}
+        out[f"{kb}B_keys"] = {k: t[k] for k in ("count_tile", "emit_tile", "fuse_tile", "sort_mode",
+                                                 "count_ms", "emit_ms", "fuse_ms", "sort_ms")}
     return out
 
 

@@ -255,16 +255,20 @@ int wg_result_profile(wg_ctx* ctx, wg_query q, wg_kernel_stat* stats, size_t cap
 void wg_query_free(wg_ctx* ctx, wg_query q);
 
 /* ---- tile shapes and the autotuner --------------------------------------
- * Two stages have a compiled choice of tile shape: the join count (delta
- * tuples per tile: 2,048 or 1,024) and the fused deduplication / set
- * difference / merge pass (merged keys per tile: 4,096 or 2,048 for 4-byte
- * keys, 2,048 or 1,024 for 8-byte keys).  Sec. Fused Deduplication fixes its
- * own workgroup tile (256 threads x 12 keys) for its hardware; here the
- * shape is an engine setting, the same results for every choice.
+ * Three stages have a compiled choice of tile shape: the join count (delta
+ * tuples per tile: 2,048 or 1,024), the join emit (merged items per tile --
+ * one per group of 8 delta tuples plus the candidates: 4,096 or 2,048) and
+ * the fused deduplication / set difference / merge pass (merged keys per
+ * tile: 4,096 or 2,048 for 4-byte keys, 2,048 or 1,024 for 8-byte keys).
+ * Sec. Fused Deduplication fixes its own workgroup tile (256 threads x 12
+ * keys) for its hardware; here the shape is an engine setting, the same
+ * results for every choice.  The radix-sort mode (wg_sort_mode below, which
+ * includes the digit width) is tuned with them.
  *
  * wg_autotune: time each candidate on a profiled fixpoint of `edges` (kind
  * WG_TC or WG_SG; one warm-up run and one timed run per candidate, the join
- * count, the radix sort and the fused stage timed with CUDA events) and keep
+ * count, the join emit, the radix sort and the fused stage timed with CUDA
+ * events) and keep
  * the fastest choice of each stage in the context for the relation's key
  * width: every engine created afterwards (single, batched, served) uses it.  `out` may be
  * NULL.  Synchronous; runs on the context stream.  Errors: WG_E_INVAL (bad
@@ -282,23 +286,34 @@ typedef struct wg_tune {
   uint32_t fuse_cand[2];
   uint32_t sort_mode;           /* chosen enum wg_sort_mode (TC relations of at most
                                    2^18 vertices; otherwise the default, untimed) */
+  uint32_t emit_tile;           /* chosen merged items (delta groups + candidates) per
+                                   join-emit tile */
+  uint32_t emit_cand[2];
+  uint32_t reserved0;
   double count_ms[2];           /* join-count time per fixpoint, per candidate */
   double fuse_ms[2];            /* fused-stage time per fixpoint, per candidate */
-  double sort_ms[3];            /* radix sort (histogram + passes) per fixpoint, per
+  double sort_ms[4];            /* radix sort (histogram + passes) per fixpoint, per
                                    wg_sort_mode; 0 when not timed */
+  double emit_ms[2];            /* join-emit time per fixpoint, per candidate */
 } wg_tune;
 int wg_autotune(wg_ctx* ctx, wg_rel edges, int kind, wg_tune* out);
-int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_tile);
+int wg_set_tiles(wg_ctx* ctx, int key_bytes, uint32_t count_tile, uint32_t fuse_tile,
+                 uint32_t emit_tile);
 
 /* The radix sort of a single TC query's candidates (sorted per source on the
  * destination field, Sec. Buffer Routing and Adaptive Radix Sort): one CTA
  * takes a source's whole segment through every pass, with 16 or 8 keys per
- * thread (used while no source has more than 512K candidates in an
- * iteration), or the decoupled-lookback passes over all tiles.  The same
- * result for every mode.  wg_set_sort picks it for engines of key width
- * key_bytes created afterwards; wg_autotune times all three.
- * Errors: WG_E_INVAL. */
-enum wg_sort_mode { WG_SORT_SEGMENT16 = 0, WG_SORT_SEGMENT8 = 1, WG_SORT_PASSES = 2 };
+ * thread and digits of at most 8 bits (used while no source has more than
+ * 128 tiles of candidates in an iteration, else the decoupled-lookback
+ * passes over all tiles), or only the lookback passes, or (SEGMENT_WIDE) one
+ * CTA per segment, 8 keys per thread, with digits of up to 9 bits for every
+ * segment -- two passes instead of three for the 17- and 18-bit fields of
+ * relations of 2^16 to 2^18 vertices (the radix digit width of Sec. Buffer
+ * Routing and Adaptive Radix Sort as a tuning choice).  The same result for
+ * every mode.  wg_set_sort picks it for engines of key width key_bytes
+ * created afterwards; wg_autotune times all four.  Errors: WG_E_INVAL. */
+enum wg_sort_mode { WG_SORT_SEGMENT16 = 0, WG_SORT_SEGMENT8 = 1, WG_SORT_PASSES = 2,
+                    WG_SORT_SEGMENT_WIDE = 3 };
 int wg_set_sort(wg_ctx* ctx, int key_bytes, uint32_t mode);
 
 /* ---- self-test of the bounded device wait --------------------------------

@@ -210,12 +210,16 @@ struct Dev {
   uint32_t copyback;                  // single fused engine: copy Full' back into the Full
                                       // buffer each iteration instead of swapping buffers
   uint32_t count_tile;                // delta tuples per join-count tile
+  uint32_t emit_tile;                 // merged items per join-emit tile
   uint32_t seg_sort;                  // x-grouped: the per-segment sort may take the launch
   uint32_t dphase, fphase;
   uint32_t bits, passes, dbits;
   uint32_t xseg_maxt;                 // x-grouped sort: tiles of the largest source segment
   uint32_t side;                      // side run: 0 never, 1 when the candidates are few,
                                       // 2 whenever it fits (tests)
+  uint32_t seg_wide;                  // x-grouped: the per-segment sort with 9-bit digits
+                                      // takes every launch (no lookback passes)
+  uint32_t zero_word;                 // always 0 (the largest segment "size" of seg_wide)
 };
 
 // Shared-memory index with one pad word per 32: threads that walk their own

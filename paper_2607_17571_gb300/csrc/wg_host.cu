@@ -91,7 +91,7 @@ struct wg_ctx {
   uint64_t solo_run = 0;  // the served request running on a single-query engine (0: none)
   // tile shapes engines are built with, per key width (index 0: 4-byte keys,
   // 1: 8-byte); 0 = the compiled default.  Set by wg_autotune / wg_set_tiles.
-  uint32_t tune_count[2] = {0, 0}, tune_fuse[2] = {0, 0};
+  uint32_t tune_count[2] = {0, 0}, tune_fuse[2] = {0, 0}, tune_emit[2] = {0, 0};
   uint32_t tune_sort[2] = {WG_SORT_SEGMENT16, WG_SORT_SEGMENT16};  // enum wg_sort_mode
   cudaStream_t alloc_stream = nullptr;            // stream of allocations in progress (NULL: stream)
   // scratch of the standalone primitives
@@ -454,6 +454,7 @@ struct EngineBase {
   virtual bool hashjoin() const = 0;
   virtual uint32_t count_tile() const = 0;
   virtual uint32_t fuse_tile() const = 0;
+  virtual uint32_t emit_tile() const = 0;
   virtual uint32_t sort_mode() const = 0;
   virtual uint32_t side_mode() const = 0;
   virtual size_t held() const = 0;       // device bytes of the engine's buffers
@@ -469,6 +470,10 @@ template <typename K> static uint32_t count_tile_of(const wg_ctx* c) {
 template <typename K> static uint32_t fuse_tile_of(const wg_ctx* c) {
   const uint32_t v = c->tune_fuse[sizeof(K) == 8];
   return v ? v : (uint32_t)FuseTile<K>::T;
+}
+template <typename K> static uint32_t emit_tile_of(const wg_ctx* c) {
+  const uint32_t v = c->tune_emit[sizeof(K) == 8];
+  return v ? v : (uint32_t)kTileC;
 }
 
 struct Query {
@@ -536,6 +541,7 @@ struct Engine : EngineBase {
   bool copy_back = false;  // copy Full' back every iteration instead of swapping buffers
   bool hash_join = false;  // join through the relation's hash table (ablation)
   uint32_t count_tile_, fuse_tile_;  // delta tuples per join-count tile, keys per fused tile
+  uint32_t emit_tile_;               // merged items per join-emit tile
   uint32_t sort_mode_;               // enum wg_sort_mode (x-grouped engines)
   uint32_t side_;                    // side run of Full: 0 never, 1 with few candidates, 2 always
   Engine(wg_ctx* ctx, bool single_, uint32_t n, uint32_t bits, uint32_t logcap, bool fuse_,
@@ -543,9 +549,13 @@ struct Engine : EngineBase {
       : c(ctx), single(single_), fuse(fuse_), xseg(xseg_), n_slots(n), bits_(bits),
         log_cap(logcap), copy_back(copy_back_), hash_join(hash_join_),
         count_tile_(count_tile_of<K>(ctx)), fuse_tile_(fuse_tile_of<K>(ctx)),
-        sort_mode_(ctx->tune_sort[sizeof(K) == 8]),
+        emit_tile_(emit_tile_of<K>(ctx)), sort_mode_(ctx->tune_sort[sizeof(K) == 8]),
         side_(single_ && fuse_ && n == 1 && !copy_back_ ? side : 0u) {
     pass_plan(bits, &passes, &dbits);
+    if (xseg && sort_mode_ == WG_SORT_SEGMENT_WIDE && bits > 8) {  // digits of up to 9 bits
+      passes = (bits + 8) / 9;
+      dbits = (bits + passes - 1) / passes;
+    }
   }
   ~Engine() override { release(); }
   int kb() const override { return (int)sizeof(K); }
@@ -554,6 +564,7 @@ struct Engine : EngineBase {
   bool copyback() const override { return copy_back; }
   bool hashjoin() const override { return hash_join; }
   uint32_t count_tile() const override { return count_tile_; }
+  uint32_t emit_tile() const override { return emit_tile_; }
   uint32_t fuse_tile() const override { return fuse_tile_; }
   uint32_t sort_mode() const override { return sort_mode_; }
   uint32_t side_mode() const override { return side_; }
@@ -611,8 +622,10 @@ struct Engine : EngineBase {
     h.fuse = fuse ? 1 : 0; h.fuse_tile = fuse_tile_; h.xseg = xseg ? 1 : 0;
     h.copyback = copy_back && single && fuse ? 1 : 0;
     h.count_tile = count_tile_;
+    h.emit_tile = emit_tile_;
     // (the per-segment sort counts up to three passes' digits: fields of <= 24 bits)
     h.seg_sort = xseg && sort_mode_ != WG_SORT_PASSES && passes <= 3 ? 1 : 0;
+    h.seg_wide = h.seg_sort && sort_mode_ == WG_SORT_SEGMENT_WIDE ? 1 : 0;
     h.hist = (unsigned long long*)hist.p;
     h.n_inst = n_slots; h.single = single ? 1 : 0;
     h.bits = bits_; h.passes = passes; h.dbits = dbits;
@@ -624,10 +637,11 @@ struct Engine : EngineBase {
     CK(cudaMemcpyAsync(dv, &h, sizeof(Dev), cudaMemcpyHostToDevice, st));
     CK(cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming));
     g_count = grid_of(c, occupancy_join<K>(count_tile_ == (uint32_t)kTileD ? 0 : 3));
-    g_emit = grid_of(c, occupancy_join<K>(1));
+    g_emit = grid_of(c, occupancy_join<K>(emit_tile_ == (uint32_t)kTileC ? 1 : 4));
     g_hist = grid_of(c, occupancy_sort<K>(0));
     g_pass = grid_of(c, occupancy_sort<K>(1));
-    g_seg = grid_of(c, occupancy_sort<K>(sort_mode_ == WG_SORT_SEGMENT8 ? 7 : 6));
+    g_seg = grid_of(c, occupancy_sort<K>(sort_mode_ == WG_SORT_SEGMENT8 ? 7
+                                         : sort_mode_ == WG_SORT_SEGMENT_WIDE ? 8 : 6));
     g_uniq = grid_of(c, occupancy_sort<K>(2));
     g_merge = grid_of(c, occupancy_sort<K>(3));
     g_fuse = grid_of(c, occupancy_sort<K>(fuse_tile_ == (uint32_t)FuseTile<K>::T ? 4 : 5));
@@ -827,9 +841,9 @@ struct Engine : EngineBase {
     if (hash_join) {
       mark(); launch_join_emit_hash<K>(dv->st + S_EMIT, g_emit, s); mark();
     } else {
-      launch_partition<K>(dv->st + S_EMIT, 2, kTileC, c->num_sms * 4, s);
+      launch_partition<K>(dv->st + S_EMIT, 2, emit_tile_, c->num_sms * 4, s);
       if (!stage()) return syncs;
-      mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s); mark();
+      mark(); launch_join_emit<K>(dv->st + S_EMIT, g_emit, s, emit_tile_); mark();
     }
     if (!stage()) return syncs;
     mark(); launch_sort_hist<K>(dv->st + S_HIST, g_hist, s); mark();
@@ -840,7 +854,8 @@ struct Engine : EngineBase {
       // passes (each kernel finds out on the device and the other returns)
       mark();
       if (sort_mode_ != WG_SORT_PASSES)
-        launch_sort_seg<K>(dv->st + S_PASS0, g_seg, s, dbits, sort_mode_ == WG_SORT_SEGMENT8 ? 8 : 16);
+        launch_sort_seg<K>(dv->st + S_PASS0, g_seg, s, dbits, sort_mode_ == WG_SORT_SEGMENT8 ? 8 : 16,
+                           sort_mode_ == WG_SORT_SEGMENT_WIDE);
       for (uint32_t p = 0; p < passes; ++p) launch_sort_pass<K>(dv->st + S_PASS0 + p, g_pass, s, dbits);
       mark();
       if (!stage()) return syncs;
@@ -1219,7 +1234,7 @@ static int single_start(wg_ctx* c, Query* q) {
           uint32_t maxt = 0;
           if (E->xgrouped() && E->h.seg_sort)
             CK(cudaMemcpy(&maxt, &E->dv->xseg_maxt, 4, cudaMemcpyDeviceToHost));
-          const bool seg = E->xgrouped() && E->h.seg_sort && maxt <= kSegSortMaxTiles;
+          const bool seg = E->xgrouped() && E->h.seg_sort && (E->h.seg_wide || maxt <= kSegSortMaxTiles);
           std::vector<std::pair<const char*, double>> names = {
               {"join_count", nd * (kb + 8 + 8)},
               {"join_emit", nd * (kb + 8) + nc * (kb + 4)},
@@ -2038,11 +2053,13 @@ static int single_begin(wg_ctx* c, Query* q) {
   const uint32_t bits = full_width ? 8u * R->kb : xseg ? R->w : 2 * R->w;
   const uint32_t ct = R->kb == 4 ? count_tile_of<uint32_t>(c) : count_tile_of<unsigned long long>(c);
   const uint32_t ft = R->kb == 4 ? fuse_tile_of<uint32_t>(c) : fuse_tile_of<unsigned long long>(c);
+  const uint32_t et = R->kb == 4 ? emit_tile_of<uint32_t>(c) : emit_tile_of<unsigned long long>(c);
   for (size_t i = 0; i < c->idle.size() && !q->own; ++i)
     if (c->idle[i]->kb() == R->kb && c->idle[i]->bits() == bits && c->idle[i]->fused() == fuse &&
         c->idle[i]->xgrouped() == xseg && c->idle[i]->copyback() == copyback &&
         c->idle[i]->hashjoin() == hashjoin && c->idle[i]->count_tile() == ct &&
         c->idle[i]->fuse_tile() == ft && c->idle[i]->sort_mode() == c->tune_sort[R->kb == 8] &&
+        c->idle[i]->emit_tile() == et &&
         c->idle[i]->side_mode() == side) {
       q->own = std::move(c->idle[i]);
       c->idle.erase(c->idle.begin() + i);
@@ -2436,20 +2453,24 @@ int wg_selftest_wait_timeout(wg_ctx* c) {
   return rc;
 }
 
-int wg_set_tiles(wg_ctx* c, int key_bytes, uint32_t count_tile, uint32_t fuse_tile) {
+int wg_set_tiles(wg_ctx* c, int key_bytes, uint32_t count_tile, uint32_t fuse_tile,
+                 uint32_t emit_tile) {
   if (!c || (key_bytes != 4 && key_bytes != 8)) return set_err(WG_E_INVAL, "bad argument");
   const uint32_t T = key_bytes == 4 ? FuseTile<uint32_t>::T : FuseTile<unsigned long long>::T;
   if (count_tile && count_tile != (uint32_t)kTileD && count_tile != (uint32_t)kTileD / 2)
     return set_err(WG_E_INVAL, "count tile is not a compiled shape");
   if (fuse_tile && fuse_tile != T && fuse_tile != T / 2)
     return set_err(WG_E_INVAL, "fused tile is not a compiled shape");
+  if (emit_tile && emit_tile != (uint32_t)kTileC && emit_tile != (uint32_t)kTileC / 2)
+    return set_err(WG_E_INVAL, "emit tile is not a compiled shape");
   c->tune_count[key_bytes == 8] = count_tile;
   c->tune_fuse[key_bytes == 8] = fuse_tile;
+  c->tune_emit[key_bytes == 8] = emit_tile;
   return WG_OK;
 }
 
 int wg_set_sort(wg_ctx* c, int key_bytes, uint32_t mode) {
-  if (!c || (key_bytes != 4 && key_bytes != 8) || mode > WG_SORT_PASSES)
+  if (!c || (key_bytes != 4 && key_bytes != 8) || mode > WG_SORT_SEGMENT_WIDE)
     return set_err(WG_E_INVAL, "bad argument");
   c->tune_sort[key_bytes == 8] = mode;
   return WG_OK;
@@ -2457,7 +2478,7 @@ int wg_set_sort(wg_ctx* c, int key_bytes, uint32_t mode) {
 
 // One profiled fixpoint: the join-count, radix-sort and fused-stage times (ms).
 static int tune_run(wg_ctx* c, wg_rel edges, int kind, double* count_ms, double* fuse_ms,
-                    double* sort_ms = nullptr) {
+                    double* sort_ms = nullptr, double* emit_ms = nullptr) {
   wg_opts o{};
   o.profile = 1;
   wg_query id = 0;
@@ -2465,10 +2486,12 @@ static int tune_run(wg_ctx* c, wg_rel edges, int kind, double* count_ms, double*
   const int rc = wg_wait(c, id, 0);
   *count_ms = *fuse_ms = 0;
   if (sort_ms) *sort_ms = 0;
+  if (emit_ms) *emit_ms = 0;
   if (rc == WG_OK) {
     Query* q = find_q(c, id);
     for (const KStat& k : q->prof) {
       if (!std::strcmp(k.name, "join_count")) *count_ms = k.ms;
+      if (emit_ms && !std::strcmp(k.name, "join_emit")) *emit_ms = k.ms;
       if (!std::strcmp(k.name, "dedup_diff_merge") || !std::strcmp(k.name, "dedup_diff")) *fuse_ms += k.ms;
       if (sort_ms && (!std::strcmp(k.name, "sort_hist") || !std::strcmp(k.name, "sort_pass")))
         *sort_ms += k.ms;
@@ -2488,30 +2511,37 @@ int wg_autotune(wg_ctx* c, wg_rel edges, int kind, wg_tune* out) {
   t.key_bytes = (uint32_t)kb;
   t.count_cand[0] = kTileD; t.count_cand[1] = kTileD / 2;
   t.fuse_cand[0] = T; t.fuse_cand[1] = T / 2;
-  const uint32_t keep_count = c->tune_count[i], keep_fuse = c->tune_fuse[i];
+  t.emit_cand[0] = kTileC; t.emit_cand[1] = kTileC / 2;
+  const uint32_t keep_count = c->tune_count[i], keep_fuse = c->tune_fuse[i],
+                 keep_emit = c->tune_emit[i];
   for (int v = 0; v < 2; ++v) {
-    // the two stages are separate kernels: one run per candidate pair times both
+    // the three stages are separate kernels: one run per candidate triple times all
     c->tune_count[i] = t.count_cand[v];
     c->tune_fuse[i] = t.fuse_cand[v];
+    c->tune_emit[i] = t.emit_cand[v];
     for (int rep = 0; rep < 2; ++rep) {  // the first run grows the engine's pools
-      const int rc = tune_run(c, edges, kind, &t.count_ms[v], &t.fuse_ms[v]);
+      const int rc = tune_run(c, edges, kind, &t.count_ms[v], &t.fuse_ms[v], nullptr,
+                              &t.emit_ms[v]);
       if (rc != WG_OK) {
         c->tune_count[i] = keep_count;
         c->tune_fuse[i] = keep_fuse;
+        c->tune_emit[i] = keep_emit;
         return rc;
       }
     }
   }
   t.count_tile = t.count_ms[1] < t.count_ms[0] ? t.count_cand[1] : t.count_cand[0];
   t.fuse_tile = t.fuse_ms[1] < t.fuse_ms[0] ? t.fuse_cand[1] : t.fuse_cand[0];
+  t.emit_tile = t.emit_ms[1] < t.emit_ms[0] ? t.emit_cand[1] : t.emit_cand[0];
   c->tune_count[i] = t.count_tile;
   c->tune_fuse[i] = t.fuse_tile;
+  c->tune_emit[i] = t.emit_tile;
   // the radix sort of the per-source segments (single TC queries that sort
   // per source): each mode with the chosen tiles
   const uint32_t keep_sort = c->tune_sort[i];
   t.sort_mode = keep_sort;
   if (kind == WG_TC && it->second->nv <= kXSegMaxVertices) {
-    for (uint32_t m = 0; m <= WG_SORT_PASSES; ++m) {
+    for (uint32_t m = 0; m <= WG_SORT_SEGMENT_WIDE; ++m) {
       c->tune_sort[i] = m;
       double cm = 0, fm = 0;
       for (int rep = 0; rep < 2; ++rep) {
@@ -2523,7 +2553,7 @@ int wg_autotune(wg_ctx* c, wg_rel edges, int kind, wg_tune* out) {
       }
     }
     t.sort_mode = 0;
-    for (uint32_t m = 1; m <= WG_SORT_PASSES; ++m)
+    for (uint32_t m = 1; m <= WG_SORT_SEGMENT_WIDE; ++m)
       if (t.sort_ms[m] < t.sort_ms[t.sort_mode]) t.sort_mode = m;
   }
   c->tune_sort[i] = t.sort_mode;

@@ -251,15 +251,17 @@ template <typename K> struct EmitWin {
   static constexpr int n = sizeof(K) == 4 ? 1536 : 1024;
 };
 
-// Block-wide inclusive max-scan of the owner array over [0, kTileC): each
-// thread scans its kItemsC consecutive entries, then the threads' maxima.
+// Block-wide inclusive max-scan of the owner array over the tile's IE *
+// kThreads positions: each thread scans its IE consecutive entries, then the
+// threads' maxima.
+template <int IE>
 __device__ __forceinline__ void owner_max_scan(uint16_t* own, uint32_t* s_w) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t b = threadIdx.x * kItemsC;
-  uint32_t v[kItemsC];
+  const uint32_t b = threadIdx.x * IE;
+  uint32_t v[IE];
   uint32_t m = 0;
 #pragma unroll
-  for (int e = 0; e < kItemsC; ++e) {
+  for (int e = 0; e < IE; ++e) {
     m = max(m, (uint32_t)own[b + e]);
     v[e] = m;
   }
@@ -276,22 +278,24 @@ __device__ __forceinline__ void owner_max_scan(uint16_t* own, uint32_t* s_w) {
   const uint32_t prev = __shfl_up_sync(0xffffffffu, x, 1);
   if (lane) before = max(before, prev);
 #pragma unroll
-  for (int e = 0; e < kItemsC; ++e) own[b + e] = (uint16_t)max(before, v[e]);
+  for (int e = 0; e < IE; ++e) own[b + e] = (uint16_t)max(before, v[e]);
 }
 
 // kProbe (triangle counting, Sec. Generalization "Triangle Counting"): the
 // delta is E itself and every candidate (a, b, c) of E(a,b), E(b,c) is tested
 // for E(c,a) by binary search in c's sorted adjacency -- the binary-search
 // join probe -- and only the number of hits is kept.
-template <typename K, bool kProbe>
+// TE: items per tile (an engine setting the autotuner picks; kTileC by default).
+template <typename K, bool kProbe, int TE = kTileC>
 __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
   constexpr int W = EmitWin<K>::n;
+  constexpr int IE = TE / kThreads;  // positions per thread
   __shared__ uint32_t s_start[W];  // slab's first candidate, relative to the tile
   __shared__ uint32_t s_x[W];      // TC: x            SG: off[x]
   __shared__ uint32_t s_a[W];      // TC: adj index of the slab's candidate 0 of the tile
                                    // SG: off[y] (recursive rule)
   __shared__ uint32_t s_d[W];      // SG: divisor that splits a slab index in two
-  __shared__ uint16_t s_own[kTileC];  // slab (chunk index) of each position
+  __shared__ uint16_t s_own[TE];      // slab (chunk index) of each position
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ uint32_t s_w[kWarps];
   __shared__ unsigned long long s_i0, s_i1;
@@ -317,12 +321,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
     const K* Dq = D + sg.in_off;
     const bool last_tile = t == sg.tile0 + sg.ntiles - 1;
     unsigned long long o0, o1;  // the tile's candidates: [o0, o1) of the instance
-    if (stp->splits2) {         // merged tiles (at most kTileC candidates each)
+    if (stp->splits2) {         // merged tiles (at most TE candidates each)
       o0 = stp->splits2[t];
       o1 = last_tile ? sg.aux_n : stp->splits2[t + 1];
     } else {
-      o0 = (unsigned long long)(t - sg.tile0) * kTileC;
-      o1 = min(o0 + kTileC, sg.aux_n);
+      o0 = (unsigned long long)(t - sg.tile0) * TE;
+      o1 = min(o0 + (unsigned long long)TE, sg.aux_n);
     }
     const uint32_t nout = (uint32_t)(o1 - o0);
     // delta tuples i0..i1: every slab before i0 ends at or before o0 and
@@ -391,19 +395,19 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
       if (cs < ce) {  // (a chunk of empty slabs only has none)
         // round 2: each non-empty slab marks its first position
 #pragma unroll
-        for (int e = 0; e < kItemsC; ++e) s_own[threadIdx.x * kItemsC + e] = 0;
+        for (int e = 0; e < IE; ++e) s_own[threadIdx.x * IE + e] = 0;
         __syncthreads();
         for (uint32_t i = threadIdx.x; i < mc; i += kThreads) {
           const uint32_t st = s_start[i], nx = i + 1 < mc ? s_start[i + 1] : ce;
           if (st < nx) s_own[st] = (uint16_t)i;
         }
         __syncthreads();
-        owner_max_scan(s_own, s_w);
+        owner_max_scan<IE>(s_own, s_w);
         __syncthreads();
         // round 3: positions in lane order, every load of a thread in flight
         if constexpr (kProbe) {
 #pragma unroll
-          for (int h = 0; h < kItemsC; h += 4) {
+          for (int h = 0; h < IE; h += 4) {
             uint32_t a[4], lo[4], hi[4], end[4];
 #pragma unroll
             for (int g = 0; g < 4; ++g) {
@@ -436,9 +440,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
             for (int g = 0; g < 4; ++g) hits += lo[g] < end[g] && adj[lo[g]] == a[g];
           }
         } else if (tc) {
-          constexpr int kB = kItemsC / 2;  // positions whose loads are in flight together
+          constexpr int kB = IE / 2;  // positions whose loads are in flight together
 #pragma unroll
-          for (int h = 0; h < kItemsC; h += kB) {
+          for (int h = 0; h < IE; h += kB) {
             uint32_t u[kB], z[kB];
 #pragma unroll
             for (int e = 0; e < kB; ++e) {
@@ -458,9 +462,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
             }
           }
         } else {
-          constexpr int kB = kItemsC / 2;
+          constexpr int kB = IE / 2;
 #pragma unroll
-          for (int h = 0; h < kItemsC; h += kB) {
+          for (int h = 0; h < IE; h += kB) {
             uint32_t u[kB], z[kB];
 #pragma unroll
             for (int e = 0; e < kB; ++e) {
@@ -614,9 +618,10 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
     const uint32_t ntiles = (uint32_t)(pt + tt);
     dv->st[S_HIST].segs = dv->segX; dv->st[S_HIST].nseg = nv;
     dv->st[S_HIST].ntiles = ntiles; dv->st[S_HIST].tile_seg = dv->tile_seg;
-    // the per-segment sort (and the histogram of every pass's digits it
-    // reads) only when the engine uses it; else the lookback passes
-    const uint32_t* mt = dv->seg_sort ? &dv->xseg_maxt : nullptr;
+    // the per-segment sort when the engine uses it, for segments of at most
+    // kSegSortMaxTiles tiles (with 9-bit digits for every segment: the
+    // lookback passes take 8-bit digits only); else the lookback passes
+    const uint32_t* mt = dv->seg_sort ? (dv->seg_wide ? &dv->zero_word : &dv->xseg_maxt) : nullptr;
     dv->st[S_HIST].maxt = mt;
     for (uint32_t p = 0; p < dv->passes; ++p) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
@@ -647,7 +652,8 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_cand(Dev* dv) {
     // tuples, then their slabs' candidates), so long runs of empty slabs are
     // spread over tiles too
     const unsigned long long ng = (nd + kEmitGroup - 1) >> kEmitGroupShift;
-    const unsigned long long net = nc ? (nc + ng + kTileC - 1) / kTileC : 0ull;
+    const unsigned long long te = dv->emit_tile;
+    const unsigned long long net = nc ? (nc + ng + te - 1) / te : 0ull;
     unsigned long long totc, tott, tote;
     const unsigned long long exc = scan1024(nc, sh, &totc);
     const unsigned long long ext = scan1024(nt, sh, &tott);
@@ -1179,7 +1185,10 @@ void launch_join_count(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
   else k_join_count<K, kItemsD><<<grid, kThreads, 0, s>>>(st);
 }
 template <typename K>
-void launch_join_emit(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, false><<<grid, kThreads, 0, s>>>(st); }
+void launch_join_emit(Stage* st, int grid, cudaStream_t s, uint32_t tile) {
+  if (tile == kTileC / 2) k_join_emit<K, false, kTileC / 2><<<grid, kThreads, 0, s>>>(st);
+  else k_join_emit<K, false><<<grid, kThreads, 0, s>>>(st);
+}
 template <typename K>
 void launch_tri_probe(Stage* st, int grid, cudaStream_t s) { k_join_emit<K, true><<<grid, kThreads, 0, s>>>(st); }
 template <typename K>
@@ -1203,6 +1212,7 @@ int occupancy_join(int which) {
     case 0: return one(k_join_count<K, kItemsD>);
     case 1: return one(k_join_emit<K, false>);
     case 2: return one(k_join_emit<K, true>);
+    case 4: return one(k_join_emit<K, false, kTileC / 2>);
     default: return one(k_join_count<K, kItemsD / 2>);
   }
 }
@@ -1243,7 +1253,7 @@ void launch_result_digest(const K* F, unsigned long long n, uint32_t w, const ui
 
 #define WG_INST(K)                                                                          \
   template void launch_join_count<K>(Stage*, int, cudaStream_t, uint32_t);                  \
-  template void launch_join_emit<K>(Stage*, int, cudaStream_t);                             \
+  template void launch_join_emit<K>(Stage*, int, cudaStream_t, uint32_t);                   \
   template void launch_tri_probe<K>(Stage*, int, cudaStream_t);                             \
   template void launch_join_emit_hash<K>(Stage*, int, cudaStream_t);                        \
   template void launch_hash_build<K>(const K*, unsigned long long, uint32_t,                 \

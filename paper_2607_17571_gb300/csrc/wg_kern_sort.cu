@@ -463,19 +463,23 @@ constexpr uint32_t kSegBig = 16;
 // the per-source segments sort fields of at most 18 bits (kXSegMaxVertices):
 // at most three passes
 constexpr uint32_t kSegMaxPasses = 3;
-// two compiled shapes (engine setting, wg_set_sort): 256 threads of 16 keys
-// at 4 CTAs per SM (64 registers) or of 8 keys at 6 CTAs per SM (40)
+// three compiled shapes (engine setting, wg_set_sort): 256 threads of 16 keys
+// at 4 CTAs per SM (64 registers) or of 8 keys at 6 CTAs per SM (40), with
+// digits of up to 8 bits (RB = 256 buckets); and 8 keys with digits of up to
+// 9 bits (RB = 512), so that the 17- and 18-bit fields of relations of up to
+// 2^18 vertices take two passes instead of three.
 constexpr int kSegNT = 256;
+constexpr int kWideRadix = 512;
 template <int IT> struct SegShape { static constexpr int minb = IT == 16 ? 4 : 6; };
 
-template <typename K, int NT, int IT>
+template <typename K, int NT, int IT, int RB>
 struct SegSmem {
   static constexpr int NW = NT / 32, TILE = NT * IT;
   K sk[TILE];                     // a ranked tile in digit order
-  uint32_t wbase[NW][kRadix];     // per-warp counters -> tile-local start of (warp, digit)
-  uint32_t gdst[kRadix];          // output offset in the segment minus the digit's tile start
-  uint32_t run[kRadix];           // next output offset of each digit in the segment
-  uint32_t hc[kSegMaxPasses][kRadix];  // the segment's count of each digit, per pass
+  uint32_t wbase[NW][RB];         // per-warp counters -> tile-local start of (warp, digit)
+  uint32_t gdst[RB];              // output offset in the segment minus the digit's tile start
+  uint32_t run[RB];               // next output offset of each digit in the segment
+  uint32_t hc[kSegMaxPasses][RB]; // the segment's count of each digit, per pass
   uint32_t s_scan[NW];
   uint32_t s_k;
 };
@@ -510,10 +514,10 @@ __device__ __forceinline__ uint32_t cta_excl_scan32(uint32_t v, uint32_t* sh) {
 }
 
 // Digits owned by a thread in the per-digit steps: DPT consecutive digits
-// (CTAs of fewer than kRadix threads), else digit threadIdx.x (if < kRadix).
-template <int NT> struct SegDig {
-  static constexpr int DPT = NT >= kRadix ? 1 : kRadix / NT;
-  __device__ static bool owns() { return NT <= kRadix || threadIdx.x < (uint32_t)kRadix; }
+// (CTAs of fewer than RB threads), else digit threadIdx.x (if < RB).
+template <int NT, int RB> struct SegDig {
+  static constexpr int DPT = NT >= RB ? 1 : RB / NT;
+  __device__ static bool owns() { return NT <= RB || threadIdx.x < (uint32_t)RB; }
   __device__ static uint32_t first() { return threadIdx.x * DPT; }
 };
 
@@ -555,10 +559,10 @@ __device__ __forceinline__ void seg_load(const K* p, uint32_t n, K (&key)[IT]) {
 // One tile of one pass: rank (unstable for the first pass, stable after),
 // count the next pass's digits, place the keys in digit order, compute their
 // output offsets from the running counts.  The caller writes the tile out.
-template <typename K, bool kByte, bool kFull, int NT, int IT>
-__device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&key)[IT],
+template <typename K, bool kByte, bool kFull, int NT, int IT, int RB>
+__device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT, RB>& S, const K (&key)[IT],
                                               uint32_t n, const Digit& dg, bool first_pass) {
-  using D = SegDig<NT>;
+  using D = SegDig<NT, RB>;
   constexpr int NW = NT / 32;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -568,7 +572,7 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&k
   // are behind a barrier already, and only this warp touches its row until
   // the next barrier
 #pragma unroll
-  for (int j = 0; j < kRadix / 32; ++j) wc[lane + 32 * j] = 0;
+  for (int j = 0; j < RB / 32; ++j) wc[lane + 32 * j] = 0;
   __syncwarp();
   uint32_t rk[(IT + 1) / 2];
 #pragma unroll
@@ -635,13 +639,13 @@ __device__ __forceinline__ void seg_rank_tile(SegSmem<K, NT, IT>& S, const K (&k
 }
 
 // Every pass's digit counts of a segment of n keys at p, into S.hc (one read).
-template <typename K, bool kByte, int NT, int IT>
-__device__ __forceinline__ void seg_count(SegSmem<K, NT, IT>& S, const K* p, uint32_t n,
+template <typename K, bool kByte, int NT, int IT, int RB>
+__device__ __forceinline__ void seg_count(SegSmem<K, NT, IT, RB>& S, const K* p, uint32_t n,
                                           uint32_t passes, uint32_t dbits) {
   constexpr uint32_t TILE = NT * IT;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t wb = warp * 32 * IT + lane;
-  for (uint32_t i = threadIdx.x; i < kSegMaxPasses * kRadix; i += NT) (&S.hc[0][0])[i] = 0;
+  for (uint32_t i = threadIdx.x; i < kSegMaxPasses * RB; i += NT) (&S.hc[0][0])[i] = 0;
   __syncthreads();
   for (uint32_t t0 = 0; t0 < n; t0 += TILE) {
     const uint32_t tn = min(n - t0, TILE);
@@ -664,15 +668,15 @@ __device__ __forceinline__ void seg_count(SegSmem<K, NT, IT>& S, const K* p, uin
   __syncthreads();
 }
 
-template <typename K, bool kByte, int NT, int IT>
-__device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint32_t k) {
-  using D = SegDig<NT>;
+template <typename K, bool kByte, int NT, int IT, int RB>
+__device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT, RB>& S, uint32_t k) {
+  using D = SegDig<NT, RB>;
   constexpr uint32_t TILE = NT * IT;
   const Seg& sg = st0->segs[k];
   const unsigned long long in_off = sg.in_off, out_off = sg.out_off;
   const uint32_t n = (uint32_t)sg.n, passes = st0->passes, dbits = st0->dbits;
   const uint32_t nt = (n + TILE - 1) / TILE;
-  seg_count<K, kByte, NT, IT>(S, (const K*)st0->in + in_off, n, passes, dbits);
+  seg_count<K, kByte, NT, IT, RB>(S, (const K*)st0->in + in_off, n, passes, dbits);
   for (uint32_t p = 0; p < passes; ++p) {
     const Stage* sp = st0 + p;
     const K* in = (const K*)sp->in + in_off;
@@ -701,8 +705,8 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
     __syncthreads();
     for (uint32_t j = 0; j < nt; ++j) {
       const uint32_t tn = min(n - j * TILE, TILE);
-      if (tn == TILE) seg_rank_tile<K, kByte, true, NT, IT>(S, key, tn, dg, p == 0);
-      else seg_rank_tile<K, kByte, false, NT, IT>(S, key, tn, dg, p == 0);
+      if (tn == TILE) seg_rank_tile<K, kByte, true, NT, IT, RB>(S, key, tn, dg, p == 0);
+      else seg_rank_tile<K, kByte, false, NT, IT, RB>(S, key, tn, dg, p == 0);
       if (j + 1 < nt)  // the next tile's loads fly during this tile's stores
         seg_load<K, NT, IT>(in + (unsigned long long)(j + 1) * TILE, min(n - (j + 1) * TILE, TILE), key);
       if (tn == TILE) {
@@ -723,15 +727,17 @@ __device__ __forceinline__ void seg_sort(Stage* st0, SegSmem<K, NT, IT>& S, uint
   }
 }
 
-template <typename K, bool kByte, int IT>
+template <typename K, bool kByte, int IT, int RB = kRadix>
 __global__ void __launch_bounds__(kSegNT, SegShape<IT>::minb) k_sort_seg(Stage* st0) {
-  __shared__ SegSmem<K, kSegNT, IT> S;
+  __shared__ SegSmem<K, kSegNT, IT, RB> S;
   if (*(volatile uint32_t*)&st0->ctl->abort) return;
-  if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;  // the lookback passes sort it
+  // the lookback passes sort it (never for wide digits: their stages point
+  // maxt at a zero word)
+  if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;
   for (;;) {
     const uint32_t k = seg_claim(st0, &S.s_k);
     if (k == 0xFFFFFFFFu) return;
-    seg_sort<K, kByte, kSegNT, IT>(st0, S, k);
+    seg_sort<K, kByte, kSegNT, IT, RB>(st0, S, k);
   }
 }
 
@@ -1327,8 +1333,11 @@ void launch_sort_pass(Stage* st, int grid, cudaStream_t s, uint32_t dbits) {
   else k_sort_pass<K, false><<<grid, kThreads, 0, s>>>(st);
 }
 template <typename K>
-void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits, int items) {
-  if (items == 8) {
+void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits, int items, bool wide) {
+  if (wide) {  // digits of up to 9 bits, 8 keys per thread
+    if (dbits == 8) k_sort_seg<K, true, 8, kWideRadix><<<grid, kSegNT, 0, s>>>(st0);
+    else k_sort_seg<K, false, 8, kWideRadix><<<grid, kSegNT, 0, s>>>(st0);
+  } else if (items == 8) {
     if (dbits == 8) k_sort_seg<K, true, 8><<<grid, kSegNT, 0, s>>>(st0);
     else k_sort_seg<K, false, 8><<<grid, kSegNT, 0, s>>>(st0);
   } else {
@@ -1382,6 +1391,7 @@ int occupancy_sort(int which) {
     case 5: return occupancy_of(k_diff_merge<K, FuseTile<K>::T / 2>);
     case 6: return occupancy_of(k_sort_seg<K, true, 16>, kSegNT);
     case 7: return occupancy_of(k_sort_seg<K, true, 8>, kSegNT);
+    case 8: return occupancy_of(k_sort_seg<K, false, 8, kWideRadix>, kSegNT);
     default: return 0;
   }
 }
@@ -1389,7 +1399,7 @@ int occupancy_sort(int which) {
 #define WG_INST(K)                                              \
   template void launch_sort_hist<K>(Stage*, int, cudaStream_t);  \
   template void launch_sort_pass<K>(Stage*, int, cudaStream_t, uint32_t); \
-  template void launch_sort_seg<K>(Stage*, int, cudaStream_t, uint32_t, int); \
+  template void launch_sort_seg<K>(Stage*, int, cudaStream_t, uint32_t, int, bool); \
   template void launch_unique_diff<K>(Stage*, int, cudaStream_t); \
   template void launch_merge<K>(Stage*, int, cudaStream_t);      \
   template void launch_diff_merge<K>(Stage*, int, cudaStream_t, uint32_t); \

@@ -20,7 +20,7 @@ template <typename K> void launch_sort_pass(Stage* st, int grid, cudaStream_t s,
 // every pass of segments of at most kSegSortMaxTiles tiles, one CTA per segment
 // (st0: the first pass's stage; the later passes' stages follow it)
 template <typename K> void launch_sort_seg(Stage* st0, int grid, cudaStream_t s, uint32_t dbits,
-                                           int items);  // keys per thread: 16 or 8
+                                           int items, bool wide);  // keys per thread: 16 or 8
 template <typename K> void launch_unique_diff(Stage* st, int grid, cudaStream_t s);
 template <typename K> void launch_merge(Stage* st, int grid, cudaStream_t s);
 // tile: merged keys per fused-pass tile, FuseTile<K>::T or half of it
@@ -36,7 +36,7 @@ template <typename K> int occupancy_sort(int which);  // 0 hist, 1 pass, 2 uniq,
 // join and engine control (wg_kern_join.cu)
 // tile: delta tuples per count tile, kTileD or kTileD / 2
 template <typename K> void launch_join_count(Stage* st, int grid, cudaStream_t s, uint32_t tile);
-template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s);
+template <typename K> void launch_join_emit(Stage* st, int grid, cudaStream_t s, uint32_t tile);
 template <typename K> void launch_tri_probe(Stage* st, int grid, cudaStream_t s);
 void launch_fuse_mark(Dev* dv, int grid, cudaStream_t s);
 void launch_fuse_list(Dev* dv, int grid, cudaStream_t s);

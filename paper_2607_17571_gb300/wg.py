@@ -29,7 +29,7 @@ WG_FLAG_HASH_JOIN = 8
 WG_FLAG_MERGE_EVERY_ITER = 16
 WG_FLAG_SIDE_RUN_ALWAYS = 32
 WG_PENDING, WG_RUNNING, WG_DONE, WG_FAILED = 0, 1, 2, 3
-WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES = 0, 1, 2
+WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES, WG_SORT_SEGMENT_WIDE = 0, 1, 2, 3
 ERRORS = {-1: "WG_E_INVAL", -2: "WG_E_NOMEM", -3: "WG_E_BUDGET", -4: "WG_E_CAPACITY",
           -5: "WG_E_NOT_READY", -6: "WG_E_ITER_CAP", -7: "WG_E_DEVICE_TIMEOUT", -8: "WG_E_CUDA"}
 
@@ -52,7 +52,9 @@ class wg_request(Structure):
 class wg_tune(Structure):
     _fields_ = [("key_bytes", c_uint32), ("count_tile", c_uint32), ("fuse_tile", c_uint32),
                 ("count_cand", c_uint32 * 2), ("fuse_cand", c_uint32 * 2), ("sort_mode", c_uint32),
-                ("count_ms", c_double * 2), ("fuse_ms", c_double * 2), ("sort_ms", c_double * 3)]
+                ("emit_tile", c_uint32), ("emit_cand", c_uint32 * 2), ("reserved0", c_uint32),
+                ("count_ms", c_double * 2), ("fuse_ms", c_double * 2), ("sort_ms", c_double * 4),
+                ("emit_ms", c_double * 2)]
 
 
 class wg_kernel_stat(Structure):
@@ -87,7 +89,7 @@ SIGNATURES = {
     "wg_result_digest": (c_int, [c_void_p, c_uint64, POINTER(c_uint64)]),
     "wg_autotune": (c_int, [c_void_p, c_uint64, c_int, POINTER(wg_tune)]),
     "wg_selftest_wait_timeout": (c_int, [c_void_p]),
-    "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32]),
+    "wg_set_tiles": (c_int, [c_void_p, c_int, c_uint32, c_uint32, c_uint32]),
     "wg_set_sort": (c_int, [c_void_p, c_int, c_uint32]),
     "wg_result_profile": (c_int, [c_void_p, c_uint64, POINTER(wg_kernel_stat), c_size_t,
                                   POINTER(c_size_t)]),
@@ -331,15 +333,17 @@ class Context:
         return Query(self, q.value)
 
     def autotune(self, rel: Relation, kind: int = WG_TC) -> dict:
-        """wg_autotune: time the compiled tile shapes of the join count and the
-        fused pass on profiled fixpoints of `rel` and keep the faster ones for
-        engines of its key width."""
+        """wg_autotune: time the compiled tile shapes of the join count, the
+        join emit and the fused pass (and the radix-sort modes) on profiled
+        fixpoints of `rel` and keep the fastest for engines of its key width."""
         t = wg_tune()
         _check(self.lib.wg_autotune(self.h, rel.id, kind, byref(t)), "wg_autotune")
         return dict(key_bytes=t.key_bytes, count_tile=t.count_tile, fuse_tile=t.fuse_tile,
-                    sort_mode=t.sort_mode, count_cand=list(t.count_cand),
-                    fuse_cand=list(t.fuse_cand), count_ms=[round(x, 3) for x in t.count_ms],
+                    emit_tile=t.emit_tile, sort_mode=t.sort_mode, count_cand=list(t.count_cand),
+                    fuse_cand=list(t.fuse_cand), emit_cand=list(t.emit_cand),
+                    count_ms=[round(x, 3) for x in t.count_ms],
                     fuse_ms=[round(x, 3) for x in t.fuse_ms],
+                    emit_ms=[round(x, 3) for x in t.emit_ms],
                     sort_ms=[round(x, 3) for x in t.sort_ms])
 
     def selftest_wait_timeout(self) -> int:
@@ -347,9 +351,11 @@ class Context:
         the expected outcome: the bounded device wait gave up)."""
         return int(self.lib.wg_selftest_wait_timeout(self.h))
 
-    def set_tiles(self, key_bytes: int, count_tile: int = 0, fuse_tile: int = 0):
+    def set_tiles(self, key_bytes: int, count_tile: int = 0, fuse_tile: int = 0,
+                  emit_tile: int = 0):
         """wg_set_tiles: tile shapes for engines of this key width (0 = default)."""
-        _check(self.lib.wg_set_tiles(self.h, key_bytes, count_tile, fuse_tile), "wg_set_tiles")
+        _check(self.lib.wg_set_tiles(self.h, key_bytes, count_tile, fuse_tile, emit_tile),
+               "wg_set_tiles")
 
     def set_sort(self, key_bytes: int, mode: int = WG_SORT_SEGMENT16):
         """wg_set_sort: radix-sort mode of single TC engines of this key width."""

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 COUNT = (2048, 1024)
 FUSE = {4: (4096, 2048), 8: (2048, 1024)}
+EMIT = (4096, 2048)
 
 
 def _components(k, n, m, seed):
@@ -53,12 +54,13 @@ def _check(q, want):
 
 @pytest.mark.parametrize("count_tile", COUNT)
 @pytest.mark.parametrize("half_fuse", [False, True])
-def test_every_tile_shape_matches_oracle(count_tile, half_fuse):
+@pytest.mark.parametrize("emit_tile", EMIT)
+def test_every_tile_shape_matches_oracle(count_tile, half_fuse, emit_tile):
     from paper_2607_17571_gb300 import wg
     cases = _cases()
     with wg.Context(0) as c:
         for kb in (4, 8):
-            c.set_tiles(kb, count_tile, FUSE[kb][1 if half_fuse else 0])
+            c.set_tiles(kb, count_tile, FUSE[kb][1 if half_fuse else 0], emit_tile)
         g, want = cases["tc32"]
         rel = c.load(g.src, g.dst)
         _check(c.tc(rel), want)
@@ -79,7 +81,8 @@ def test_every_tile_shape_matches_oracle(count_tile, half_fuse):
 def _hub():
     # source 0 -> 1..1000, each of them -> 1001..1600: in its first iteration
     # source 0 has 600,000 candidates (147 tiles), more than the per-segment
-    # sort takes, so its launches fall back to the lookback passes
+    # sort takes, so its launches fall back to the lookback passes (with
+    # 9-bit digits the per-segment sort takes it all the same)
     mid = np.arange(1, 1001, dtype=np.uint32)
     leaf = np.arange(1001, 1601, dtype=np.uint32)
     src = np.concatenate([np.zeros(1000, np.uint32), np.repeat(mid, 600)])
@@ -87,7 +90,8 @@ def _hub():
     return I.EdgeList(src, dst, dict(recipe="hub"))
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])  # WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES
+# WG_SORT_SEGMENT16, WG_SORT_SEGMENT8, WG_SORT_PASSES, WG_SORT_SEGMENT_WIDE
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_every_sort_mode_matches_oracle(mode):
     from paper_2607_17571_gb300 import wg
     cases = _cases()
@@ -103,7 +107,24 @@ def test_every_sort_mode_matches_oracle(mode):
             _check(c.tc(rel, loop=wg.WG_LOOP_HOST, profile=True), want)
         _check(c.tc(c.load(hub.src, hub.dst)), want_hub)
     with wg.Context(0) as c, pytest.raises(wg.WgError):
-        c.set_sort(4, 3)
+        c.set_sort(4, 4)
+
+
+# 8, 9, 15, 17 and 18-bit fields (mean degree 0.9: small closures)
+@pytest.mark.parametrize("n", [150, 300, 20_000, 100_000, 200_000])
+def test_wide_digit_sort_field_widths(n):
+    """The per-segment sort with digits of up to 9 bits: one pass for fields
+    of at most 8 bits, two passes of ceil(w/2) bits for 9..18-bit fields
+    (17 and 18 bits: two passes instead of three)."""
+    from paper_2607_17571_gb300 import wg
+    g = I.er_graph(n, int(n * 0.9), 300 + n % 97)
+    want = oracle_tc(g.src, g.dst)
+    with wg.Context(0) as c:
+        c.set_sort(4, wg.WG_SORT_SEGMENT_WIDE)
+        c.set_sort(8, wg.WG_SORT_SEGMENT_WIDE)
+        rel = c.load(g.src, g.dst)
+        _check(c.tc(rel), want)
+        _check(c.tc(rel, side_run="never"), want)
 
 
 def test_autotune_picks_a_compiled_shape_and_engines_use_it():
@@ -114,12 +135,14 @@ def test_autotune_picks_a_compiled_shape_and_engines_use_it():
         t = c.autotune(rel, wg.WG_TC)
         assert t["key_bytes"] == 4
         assert t["count_cand"] == list(COUNT) and t["fuse_cand"] == list(FUSE[4])
-        assert t["count_tile"] in COUNT and t["fuse_tile"] in FUSE[4]
-        assert all(ms > 0 for ms in t["count_ms"] + t["fuse_ms"])
+        assert t["emit_cand"] == list(EMIT)
+        assert t["count_tile"] in COUNT and t["fuse_tile"] in FUSE[4] and t["emit_tile"] in EMIT
+        assert all(ms > 0 for ms in t["count_ms"] + t["fuse_ms"] + t["emit_ms"])
         # the choice is the faster candidate of each stage
         assert t["count_tile"] == COUNT[int(t["count_ms"][1] < t["count_ms"][0])]
         assert t["fuse_tile"] == FUSE[4][int(t["fuse_ms"][1] < t["fuse_ms"][0])]
-        # the radix sort of the per-source segments: the fastest of the three modes
+        assert t["emit_tile"] == EMIT[int(t["emit_ms"][1] < t["emit_ms"][0])]
+        # the radix sort of the per-source segments: the fastest of the four modes
         assert all(ms > 0 for ms in t["sort_ms"])
         assert t["sort_mode"] == int(np.argmin(t["sort_ms"]))
         _check(c.tc(rel), want)
@@ -130,7 +153,7 @@ def test_autotune_picks_a_compiled_shape_and_engines_use_it():
 def test_set_tiles_rejects_shapes_that_are_not_compiled():
     from paper_2607_17571_gb300 import wg
     with wg.Context(0) as c:
-        for args in ((4, 3000, 0), (4, 0, 1000), (8, 0, 4096), (2, 0, 0)):
+        for args in ((4, 3000, 0), (4, 0, 1000), (8, 0, 4096), (2, 0, 0), (4, 0, 0, 1024)):
             with pytest.raises(wg.WgError) as e:
                 c.set_tiles(*args)
             assert e.value.code == wg.WG_E_INVAL
