@@ -298,18 +298,55 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
   __shared__ uint16_t s_own[TE];      // slab (chunk index) of each position
   __shared__ unsigned long long s_scan[kWarps];
   __shared__ uint32_t s_w[kWarps];
-  __shared__ unsigned long long s_i0, s_i1;
-  __shared__ uint32_t s_r0, s_ce, s_t;
+  __shared__ unsigned long long s_i0, s_i1, s_o0, s_o1;
+  __shared__ uint32_t s_r0, s_ce, s_t, s_k;
   Ctl* ctl = stp->ctl;
   if (*(volatile uint32_t*)&ctl->abort) return;
   const K* D = (const K*)stp->in;
   K* C = (K*)stp->out;
   const unsigned long long* pos_all = stp->pos;
   const uint32_t nseg = stp->nseg, ntiles = stp->ntiles;
-  for (;;) {
-    const uint32_t t = claim_tile(stp, &s_t);
+  // Thread 0 claims a tile and reads where it lies (segment, candidate range,
+  // delta range) into shared memory.  It does so for the next tile while the
+  // CTA works on the current one, so that chain of dependent loads is off the
+  // critical path (tiles are independent: no lookback orders them).
+  auto fetch = [&]() {
+    const uint32_t t = atomicAdd(&stp->ctr, 1u);
+    s_t = t;
     if (t >= ntiles) return;
     const uint32_t k = find_seg(stp->segs, nseg, t);
+    const Seg& sg = stp->segs[k];
+    const bool last_tile = t == sg.tile0 + sg.ntiles - 1;
+    unsigned long long o0, o1;
+    if (stp->splits2) {         // merged tiles (at most TE candidates each)
+      o0 = stp->splits2[t];
+      o1 = last_tile ? sg.aux_n : stp->splits2[t + 1];
+    } else {
+      o0 = (unsigned long long)(t - sg.tile0) * TE;
+      o1 = min(o0 + (unsigned long long)TE, sg.aux_n);
+    }
+    // delta tuples i0..i1: every slab before i0 ends at or before o0 and
+    // every slab after i1 starts after o1
+    const unsigned long long* P = pos_all + sg.in_off;
+    unsigned long long i0, i1;
+    if (stp->splits) {
+      i0 = stp->splits[t];
+      i1 = last_tile ? sg.n - 1 : stp->splits[t + 1];
+    } else {
+      i0 = upper_bound_k(P, sg.n, o0) - 1;
+      i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
+    }
+    s_k = k; s_o0 = o0; s_o1 = o1; s_i0 = i0; s_i1 = i1;
+  };
+  if (threadIdx.x == 0) fetch();
+  __syncthreads();
+  for (;;) {
+    const uint32_t t = s_t;
+    if (t >= ntiles) return;
+    const uint32_t k = s_k;
+    const unsigned long long o0 = s_o0, o1 = s_o1, i0 = s_i0, m = s_i1 - i0 + 1;
+    __syncthreads();  // every thread has the tile; thread 0 fetches the next one
+    if (threadIdx.x == 0) fetch();
     const Seg sg = stp->segs[k];
     const Inst* I = stp->inst + sg.inst;
     const uint32_t* off = I->off;
@@ -319,27 +356,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
     const K mask = (K)(((K)1 << w) - 1);
     const unsigned long long* P = pos_all + sg.in_off;
     const K* Dq = D + sg.in_off;
-    const bool last_tile = t == sg.tile0 + sg.ntiles - 1;
-    unsigned long long o0, o1;  // the tile's candidates: [o0, o1) of the instance
-    if (stp->splits2) {         // merged tiles (at most TE candidates each)
-      o0 = stp->splits2[t];
-      o1 = last_tile ? sg.aux_n : stp->splits2[t + 1];
-    } else {
-      o0 = (unsigned long long)(t - sg.tile0) * TE;
-      o1 = min(o0 + (unsigned long long)TE, sg.aux_n);
-    }
     const uint32_t nout = (uint32_t)(o1 - o0);
-    // delta tuples i0..i1: every slab before i0 ends at or before o0 and
-    // every slab after i1 starts after o1
-    if (stp->splits) {
-      if (threadIdx.x == 0) s_i0 = stp->splits[t];
-      if (threadIdx.x == 32) s_i1 = last_tile ? sg.n - 1 : stp->splits[t + 1];
-    } else {
-      if (threadIdx.x == 0) s_i0 = upper_bound_k(P, sg.n, o0) - 1;
-      if (threadIdx.x == 32) s_i1 = upper_bound_k(P, sg.n, o1 - 1) - 1;
-    }
-    __syncthreads();
-    const unsigned long long i0 = s_i0, m = s_i1 - i0 + 1;
     K* Cq = C + sg.out_off + o0;
     unsigned long long hits = 0;  // triangle mode
     for (unsigned long long c0 = 0; c0 < m; c0 += W) {
@@ -496,6 +513,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
       block_excl_scan(hits, s_scan, &tot);
       if (threadIdx.x == 0 && tot) atomicAdd(stp->probe, tot);
     }
+    __syncthreads();  // thread 0's fetch of the next tile is visible
   }
 }
 

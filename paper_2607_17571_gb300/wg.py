@@ -271,6 +271,12 @@ class Context:
             import torch
             self.torch_stream = stream or torch.cuda.Stream(device=device)
             sptr = self.torch_stream.cuda_stream
+            if not mem_budget:
+                # the library's default is 90% of the free device memory; blocks
+                # PyTorch's cache holds unused will serve this context too
+                free, _ = torch.cuda.mem_get_info(device)
+                cached = torch.cuda.memory_reserved(device) - torch.cuda.memory_allocated(device)
+                mem_budget = int(0.9 * (free + max(0, cached)))
 
             def _alloc(nbytes, stream_, user):
                 try:
