@@ -97,6 +97,11 @@ struct Stage {
   // kSegSortMaxTiles: one CTA per segment sorts the launch (k_sort_seg) and
   // the lookback passes have nothing to do; otherwise the reverse.
   const uint32_t* maxt;
+  // per-segment sort: the non-empty segments in claim order -- those of at
+  // least kSegBig tiles from the front (order_n[0] of them), the others from
+  // the back (order_n[1]) -- or NULL: every segment, claimed by scanning.
+  const uint32_t* order;
+  const uint32_t* order_n;
 };
 
 // Hash-join ablation (the hash-based join the paper's sorted-array join
@@ -159,6 +164,9 @@ constexpr unsigned long long kSideRatio = 8;
 
 // Per-segment radix sort (k_sort_seg): used when no segment has more tiles.
 constexpr uint32_t kSegSortMaxTiles = 128;
+// segments of at least this many tiles are claimed first (the long ones must
+// not start last)
+constexpr uint32_t kSegBig = 16;
 
 // x-grouped sort: relations of up to kXSegMaxVertices vertices, segment
 // records built by chunks of kXChunk source vertices.
@@ -194,6 +202,7 @@ struct Dev {
   unsigned long long* xlen;           // candidates per source vertex (x-grouped sort)
   Seg* segX;                          // one sort segment per source vertex
   uint32_t* tile_seg;                 // tile -> x-segment map of the x-grouped sort
+  uint32_t* xord;                     // x-segments in claim order (see Stage::order)
   unsigned long long* xsum;           // [kXChunks][2]: candidates and tiles per chunk of x
   const unsigned long long* htab;     // hash-join ablation: the relation's table (or NULL)
   unsigned long long hmask;
@@ -217,6 +226,7 @@ struct Dev {
   uint32_t xseg_maxt;                 // x-grouped sort: tiles of the largest source segment
   uint32_t side;                      // side run: 0 never, 1 when the candidates are few,
                                       // 2 whenever it fits (tests)
+  uint32_t xord_n[2];                 // big / small x-segments listed in xord
   uint32_t seg_wide;                  // x-grouped: the per-segment sort with 9-bit digits
                                       // takes every launch (no lookback passes)
   uint32_t zero_word;                 // always 0 (the largest segment "size" of seg_wide)

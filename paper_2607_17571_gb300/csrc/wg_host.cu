@@ -520,6 +520,7 @@ struct Engine : EngineBase {
   DBuf b_dev, b_inst, b_seg, b_log;
   DBuf D[2], C[2], F[2], R, pos, st_s, st_k, hist, spl, xlen_b, segx_b, tseg_b, xsum_b, mix_b;
   DBuf G[2];  // side-run pools (single-query fused engines)
+  DBuf xord_b;  // x-grouped: claim order of the per-source sort segments
   unsigned long long capC = 0, capF = 0, capR = 0, capG = 0;
   size_t mix_tiles = 0;  // tiles the per-tile arrays (st_s, spl, mix_b) hold
   uint32_t log_cap = 0;
@@ -580,7 +581,7 @@ struct Engine : EngineBase {
     ev_done = nullptr;
     DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
                    &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b, &xsum_b,
-                   &mix_b, &G[0], &G[1]};
+                   &mix_b, &G[0], &G[1], &xord_b};
     for (DBuf* b : all) b->release(c);
     capC = capF = capR = capG = 0;
     mix_tiles = 0;
@@ -662,6 +663,7 @@ struct Engine : EngineBase {
     h.xlen = (unsigned long long*)xlen_b.p;
     h.segX = (Seg*)segx_b.p;
     h.tile_seg = (uint32_t*)tseg_b.p;
+    h.xord = (uint32_t*)xord_b.p;
     h.xsum = (unsigned long long*)xsum_b.p;
     // [mix_tiles] list | [mix_tiles + 1] prefix | [mix_tiles / kThreads + 2] chunk counts
     h.mixl = (uint32_t*)mix_b.p;
@@ -1043,20 +1045,22 @@ struct Engine : EngineBase {
   int ensure_nv(uint32_t nv) {
     if (!xseg || nv <= nv_cap) return WG_OK;
     AllocScope scope(c, st);
-    DBuf nx, ns, nh, nk, nt, nz;
+    DBuf nx, ns, nh, nk, nt, nz, no;
     int rc = nx.get(c, (size_t)nv * 8);
     if (rc == WG_OK) rc = ns.get(c, (size_t)nv * sizeof(Seg));
     if (rc == WG_OK) rc = nh.get(c, (size_t)std::max(n_slots, nv) * passes * kRadix * 8);
     if (rc == WG_OK) rc = nk.get(c, (capC / kTileC + std::max(n_slots, nv) + 2) * kRadix * 8);
     if (rc == WG_OK) rc = nt.get(c, (capC / kTileC + nv + 2) * 4);
     if (rc == WG_OK && !xsum_b.p) rc = nz.get(c, (size_t)kXChunks * 2 * 8);
+    if (rc == WG_OK) rc = no.get(c, (size_t)nv * 4);
     if (rc != WG_OK) {
-      DBuf* tmp[] = {&nx, &ns, &nh, &nk, &nt, &nz};
+      DBuf* tmp[] = {&nx, &ns, &nh, &nk, &nt, &nz, &no};
       for (DBuf* b : tmp) b->release(c);
       return rc;  // nothing was replaced: the device block is still current
     }
     xlen_b.release(c); segx_b.release(c); hist.release(c); st_k.release(c); tseg_b.release(c);
-    xlen_b = nx; segx_b = ns; hist = nh; st_k = nk; tseg_b = nt;
+    xord_b.release(c);
+    xlen_b = nx; segx_b = ns; hist = nh; st_k = nk; tseg_b = nt; xord_b = no;
     if (nz.p) xsum_b = nz;
     CK(cudaMemsetAsync(st_k.p, 0, st_k.bytes, st));
     h.ctl.epoch = 0;
@@ -1080,7 +1084,7 @@ struct Engine : EngineBase {
   size_t held() const override {
     const DBuf* all[] = {&b_dev, &b_inst, &b_seg, &b_log, &D[0], &D[1], &C[0], &C[1], &F[0], &F[1],
                          &R, &pos, &st_s, &st_k, &hist, &spl, &xlen_b, &segx_b, &tseg_b,
-                         &xsum_b, &mix_b, &G[0], &G[1]};
+                         &xsum_b, &mix_b, &G[0], &G[1], &xord_b};
     size_t b = 0;
     for (const DBuf* x : all) b += x->bytes;
     return b;

@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan_delta(Dev* dv) {
   }
   const uint32_t nvx = dv->xseg ? dv->inst[0].nv : 0u;
   for (uint32_t x = threadIdx.x; x < nvx; x += kPlanThreads) dv->xlen[x] = 0;
-  if (threadIdx.x == 0) dv->xseg_maxt = 0;
+  if (threadIdx.x == 0) { dv->xseg_maxt = 0; dv->xord_n[0] = 0; dv->xord_n[1] = 0; }
   if (threadIdx.x == 0) {
     Stage& s = dv->st[S_COUNT];
     s.in = dv->D[dv->dphase]; s.out = nullptr; s.aux = nullptr; s.out2 = nullptr;
@@ -616,6 +616,21 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
     const uint32_t wm = __reduce_max_sync(0xffffffffu, (uint32_t)min(nt, 0xFFFFFFFFull));
     if ((threadIdx.x & 31) == 0 && wm) atomicMax(&dv->xseg_maxt, wm);
   }
+  {  // claim order of the per-segment sort: segments of at least kSegBig
+     // tiles from the front of xord, the other non-empty ones from the back
+    const bool big = nt >= kSegBig, small = nt > 0 && nt < kSegBig;  // (x >= nv: nt = 0)
+    const uint32_t lane = threadIdx.x & 31, lt = (1u << lane) - 1u;
+    const uint32_t mb = __ballot_sync(0xffffffffu, big), ms = __ballot_sync(0xffffffffu, small);
+    uint32_t bb = 0, bs = 0;
+    if (lane == 0) {
+      if (mb) bb = atomicAdd(&dv->xord_n[0], (uint32_t)__popc(mb));
+      if (ms) bs = atomicAdd(&dv->xord_n[1], (uint32_t)__popc(ms));
+    }
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+    bs = __shfl_sync(0xffffffffu, bs, 0);
+    if (big) dv->xord[bb + __popc(mb & lt)] = x;
+    if (small) dv->xord[nv - 1 - (bs + __popc(ms & lt))] = x;
+  }
   if (x < nv) {
     const unsigned long long off = I.c_off + pl + el;
     const uint32_t tile0 = (uint32_t)(pt + et);
@@ -645,6 +660,7 @@ __global__ void __launch_bounds__(kXChunk) k_xseg_fill(Dev* dv) {
       dv->st[S_PASS0 + p].segs = dv->segX; dv->st[S_PASS0 + p].nseg = nv;
       dv->st[S_PASS0 + p].ntiles = ntiles; dv->st[S_PASS0 + p].tile_seg = dv->tile_seg;
       dv->st[S_PASS0 + p].maxt = mt;
+      dv->st[S_PASS0 + p].order = dv->xord; dv->st[S_PASS0 + p].order_n = dv->xord_n;
     }
   }
 }

@@ -459,7 +459,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_sort_pass(Stage* stp) {
 // and takes the tiles in order, so it is stable.  A CTA claims the segments of
 // at least kSegBig tiles first, then the others, so the longest ones do not
 // start last.  NT threads of IT keys each make a tile.
-constexpr uint32_t kSegBig = 16;
 // the per-source segments sort fields of at most 18 bits (kXSegMaxVertices):
 // at most three passes
 constexpr uint32_t kSegMaxPasses = 3;
@@ -521,25 +520,26 @@ template <int NT, int RB> struct SegDig {
   __device__ static uint32_t first() { return threadIdx.x * DPT; }
 };
 
-__device__ __forceinline__ uint32_t seg_claim(Stage* st0, uint32_t* s_k) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const uint32_t nseg = st0->nseg;
-    uint32_t k = 0xFFFFFFFFu;
-    for (;;) {
-      const uint32_t v = atomicAdd(&st0->ctr, 1u);
-      if (v >= 2 * nseg) break;
-      const uint32_t kk = v < nseg ? v : v - nseg;
-      const uint32_t nt = st0->segs[kk].ntiles;
-      if (nt != 0 && (v < nseg) == (nt >= kSegBig)) {
-        k = kk;
-        break;
-      }
-    }
-    *s_k = k;
+// The next segment for a CTA (thread 0): from the claim order list when the
+// stage has one (one atomic ticket, one load), else by scanning the segments
+// (the big ones on a first sweep of the tickets, the others on a second).
+// 0xFFFFFFFF when none is left.
+__device__ __forceinline__ uint32_t seg_claim(Stage* st0) {
+  const uint32_t nseg = st0->nseg;
+  if (st0->order) {
+    const uint32_t v = atomicAdd(&st0->ctr, 1u);
+    const uint32_t nb = st0->order_n[0], ns = st0->order_n[1];
+    if (v < nb) return st0->order[v];
+    if (v < nb + ns) return st0->order[nseg - 1 - (v - nb)];
+    return 0xFFFFFFFFu;
   }
-  __syncthreads();
-  return *s_k;
+  for (;;) {
+    const uint32_t v = atomicAdd(&st0->ctr, 1u);
+    if (v >= 2 * nseg) return 0xFFFFFFFFu;
+    const uint32_t kk = v < nseg ? v : v - nseg;
+    const uint32_t nt = st0->segs[kk].ntiles;
+    if (nt != 0 && (v < nseg) == (nt >= kSegBig)) return kk;
+  }
 }
 
 // Load n <= NT*IT keys from p into registers, warp-striped.
@@ -734,10 +734,15 @@ __global__ void __launch_bounds__(kSegNT, SegShape<IT>::minb) k_sort_seg(Stage* 
   // the lookback passes sort it (never for wide digits: their stages point
   // maxt at a zero word)
   if (!st0->maxt || *st0->maxt > kSegSortMaxTiles) return;
+  // thread 0 claims the CTA's next segment while the CTA sorts the current one
+  if (threadIdx.x == 0) S.s_k = seg_claim(st0);
+  __syncthreads();
   for (;;) {
-    const uint32_t k = seg_claim(st0, &S.s_k);
+    const uint32_t k = S.s_k;
     if (k == 0xFFFFFFFFu) return;
-    seg_sort<K, kByte, kSegNT, IT, RB>(st0, S, k);
+    __syncthreads();  // every thread has k
+    if (threadIdx.x == 0) S.s_k = seg_claim(st0);
+    seg_sort<K, kByte, kSegNT, IT, RB>(st0, S, k);  // ends with a barrier
   }
 }
 

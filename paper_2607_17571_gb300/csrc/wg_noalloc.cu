@@ -45,12 +45,15 @@ constexpr size_t kNoAllocMaxKeys = WG_NOALLOC_MAX_KEYS;
 constexpr size_t kAlign = 256;
 constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
 
-// Scratch layout: Stage[S_SORT_END] | Seg | Ctl | sticky error word |
+// Scratch layout: stage records (the histogram's, then one per pass, in a
+// region of fixed size) | Seg | Ctl | sticky error word |
 // hist u64[kMaxPasses*kRadix] | status u64[(tiles+1)*kRadix] |
 // ping-pong keys (8-byte keys, kNoAllocMaxKeys)
 constexpr size_t kTiles = (kNoAllocMaxKeys + kTileC - 1) / kTileC;
 constexpr size_t kOffStage = 0;
-constexpr size_t kOffSeg = align_up(kOffStage + sizeof(Stage) * S_SORT_END);
+constexpr size_t kStageBytes = 2816;
+static_assert(sizeof(Stage) * (1 + kMaxPasses) <= kStageBytes, "stage records fit their region");
+constexpr size_t kOffSeg = align_up(kOffStage + kStageBytes);
 constexpr size_t kOffCtl = align_up(kOffSeg + sizeof(Seg));
 constexpr size_t kOffSticky = align_up(kOffCtl + sizeof(Ctl));
 constexpr size_t kOffHist = align_up(kOffSticky + sizeof(uint32_t));
@@ -94,14 +97,14 @@ __global__ void k_noalloc_setup(unsigned char* base, void* keys, unsigned long l
     Stage h{};
     h.segs = sg; h.ctl = ctl; h.status = status; h.hist = hist;
     h.nseg = 1; h.ntiles = ntiles; h.in = keys; h.passes = passes; h.dbits = dbits;
-    st[S_HIST] = h;
+    st[0] = h;
     void* buf[2] = {keys, base + kOffKeys};
     for (uint32_t p = 0; p < passes; ++p) {
       Stage x = h;
       x.in = buf[p & 1]; x.out = buf[(p + 1) & 1];
       // a distinct epoch per pass; the words were just cleared to epoch 0
       x.shift = p * dbits; x.pass = p; x.epoch = 1 + p;
-      st[S_PASS0 + p] = x;
+      st[1 + p] = x;
     }
   }
 }
@@ -154,9 +157,9 @@ int sort_noalloc(K* keys, size_t n, uint32_t bits, cudaStream_t s, int dev) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_noalloc_setup<<<64, 256, 0, s>>>(base, keys, n, passes, dbits, ntiles);
   Stage* st = (Stage*)(base + kOffStage);
-  launch_sort_hist<K>(st + S_HIST, sms * std::max(1, occupancy_sort<K>(0)), s);
+  launch_sort_hist<K>(st, sms * std::max(1, occupancy_sort<K>(0)), s);
   for (uint32_t p = 0; p < passes; ++p)
-    launch_sort_pass<K>(st + S_PASS0 + p, sms * std::max(1, occupancy_sort<K>(1)), s, dbits);
+    launch_sort_pass<K>(st + 1 + p, sms * std::max(1, occupancy_sort<K>(1)), s, dbits);
   if (passes & 1) {
     const cudaError_t e = cudaMemcpyAsync(keys, base + kOffKeys, n * sizeof(K),
                                           cudaMemcpyDeviceToDevice, s);
