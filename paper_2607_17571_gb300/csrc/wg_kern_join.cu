@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
     const uint32_t w = I->w, kind = I->kind, iter = I->iter;
     const bool tc = kind == KIND_TC;
     const K mask = (K)(((K)1 << w) - 1);
-    const unsigned long long* P = pos_all + sg.in_off;
-    const K* Dq = D + sg.in_off;
+    const unsigned long long* P = pos_all + sg.in_off + i0;  // from the tile's first delta tuple
+    const K* Dq = D + sg.in_off + i0;
     const uint32_t nout = (uint32_t)(o1 - o0);
     K* Cq = C + sg.out_off + o0;
     unsigned long long hits = 0;  // triangle mode
@@ -368,11 +368,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
 #pragma unroll
         for (int e = 0; e < kPer; ++e) {
           const uint32_t i = threadIdx.x + e * kThreads;
-          p[e] = i < mc ? P[i0 + c0 + i] : 0ull;
-          key[e] = i < mc ? Dq[i0 + c0 + i] : (K)0;
+          p[e] = i < mc ? P[c0 + i] : 0ull;
+          key[e] = i < mc ? Dq[c0 + i] : (K)0;
         }
         if (threadIdx.x == 0)  // the chunk covers candidates [its first slab's start, s_ce)
-          s_ce = c0 + mc < m ? (uint32_t)(P[i0 + c0 + mc] - o0) : nout;
+          s_ce = c0 + mc < m ? (uint32_t)(P[c0 + mc] - o0) : nout;
 #pragma unroll
         for (int e = 0; e < kPer; ++e) {
           const uint32_t i = threadIdx.x + e * kThreads;
@@ -507,6 +507,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_join_emit(Stage* stp) {
         }
       }
       __syncthreads();  // the table and owners are read; the next chunk may overwrite them
+      // The range ends at the slab holding the next tile's first candidate,
+      // so it takes in a run of empty slabs that starts exactly at the tile's
+      // end; once the next chunk starts at or past the end, it and every
+      // later one emit nothing here.
+      if (ce >= nout) break;
     }
     if constexpr (kProbe) {
       unsigned long long tot;

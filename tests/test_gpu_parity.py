@@ -97,6 +97,36 @@ def test_forest_sg_small(ctx):
     check(ctx, "sg", g.src, g.dst)
 
 
+@pytest.mark.parametrize("shared", [True, False])
+def test_long_runs_of_sink_slabs(ctx, shared):
+    """Delta tuples into sinks have empty join slabs.  Here they come in runs
+    of 40,000 (longer than the delta tuples of one join-emit tile): one before
+    the first candidate, runs between tuples that do produce candidates, and
+    one after the last.  The tiles next to a run must emit all their own
+    candidates and nothing for the run.  Shared sinks keep 16-bit fields
+    (32-bit keys); one sink set per hub needs 18 (64-bit keys)."""
+    L = 40_000
+    src, dst = [], []
+    for h in range(4):
+        hub = 10 * h
+        src += [hub] * L
+        dst += (np.arange(L) + (1 << 20) + (0 if shared else h * L)).tolist()
+        if h == 0:
+            continue  # sinks only: the leading run
+        for j in range(3):
+            m = hub + 1 + j  # below the sinks in rank: its slab precedes the hub's run
+            src.append(hub)
+            dst.append(m)
+            for z in range(40):
+                t = 1000 + 40 * m + z
+                src += [m, t]
+                dst += [t, 100000 + t]
+    src, dst = np.array(src, np.uint32), np.array(dst, np.uint32)
+    st, info = check(ctx, "tc", src, dst)
+    assert info["field_bits"] == (16 if shared else 18)
+    assert st.iterations == 3
+
+
 def test_full_id_range(ctx):
     big = 0xFFFFFFFF
     check(ctx, "tc", [0, big, 7, 7], [big, 7, 0, 7])
