@@ -221,71 +221,6 @@ static int prim_seg(wg_ctx* c, const Seg& s) {
   return WG_OK;
 }
 
-// ------------------------------------------------------------------ triangle counting
-// triangle(a,b,c) <- edge(a,b), edge(b,c), edge(c,a) (Sec. Generalization,
-// "Triangle Counting"): one pass of the sorted-array join with E as the
-// delta.  The join count gives each edge (a,b) its slab of deg(b) two-paths;
-// the emit kernel in probe mode tests each two-path (a,b,c) for E(c,a) by
-// binary search and counts the hits.
-template <typename K>
-static int tri_count(wg_ctx* c, Relation* R, unsigned long long* count) {
-  *count = 0;
-  const size_t ne = R->ne;
-  if (ne == 0) return WG_OK;
-  const uint32_t ntd = (uint32_t)((ne + kTileD - 1) / kTileD);
-  TRY(prim_scratch(c, 0, ntd));
-  DBuf inst, pos, spl, hits;
-  TRY(inst.get(c, sizeof(Inst)));
-  TRY(pos.get(c, ne * 8));
-  TRY(hits.get(c, 8));
-  Inst I{};
-  I.off = (const uint32_t*)R->off.p; I.adj = (const uint32_t*)R->adj.p;
-  I.nv = R->nv; I.w = R->w; I.kind = KIND_TC; I.state = INST_ACTIVE; I.iter = 1; I.n_delta = ne;
-  CK(cudaMemcpyAsync(inst.p, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
-  Seg sd{};
-  sd.n = ne; sd.ntiles = ntd;
-  TRY(prim_seg(c, sd));
-  Stage k = prim_stage(c, ntd);
-  k.in = R->keys.p; k.inst = (Inst*)inst.p; k.pos = (unsigned long long*)pos.p;
-  k.epoch = prim_epoch(c);
-  TRY(prim_put(c, S_COUNT, k));
-  launch_join_count<K>(c->s_stage + S_COUNT, grid_of(c, occupancy_join<K>(0)), c->stream, kTileD);
-  CK(cudaGetLastError());
-  Seg back{};
-  Ctl ctl{};
-  CK(cudaMemcpyAsync(&back, c->s_seg, sizeof(Seg), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  int rc = WG_OK;
-  const unsigned long long paths = back.res;  // two-paths (a,b,c)
-  if (!ctl.error && paths) {
-    const unsigned long long ntiles = (paths + kTileC - 1) / kTileC;
-    if (ntiles >= (1ull << 32)) return set_err(WG_E_CAPACITY, "too many two-paths");
-    TRY(spl.get(c, (size_t)(ntiles + 1) * 8));  // (the probe has no lookback: no status words)
-    Seg se{};
-    se.n = ne; se.aux_n = paths; se.ntiles = (uint32_t)ntiles;
-    TRY(prim_seg(c, se));
-    CK(cudaMemsetAsync(hits.p, 0, 8, c->stream));
-    Stage e = prim_stage(c, (uint32_t)ntiles);
-    e.in = R->keys.p; e.inst = (Inst*)inst.p; e.pos = (unsigned long long*)pos.p;
-    e.splits = (unsigned long long*)spl.p; e.probe = (unsigned long long*)hits.p;
-    TRY(prim_put(c, S_EMIT, e));
-    launch_partition<K>(c->s_stage + S_EMIT, 1, kTileC, c->num_sms * 4, c->stream);
-    launch_tri_probe<K>(c->s_stage + S_EMIT, grid_of(c, occupancy_join<K>(2)), c->stream);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(count, hits.p, 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-  }
-  if (ctl.error) {
-    cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream);
-    *count = 0;
-    rc = set_err(WG_E_DEVICE_TIMEOUT, "a device lookback wait gave up");
-  }
-  inst.release(c); pos.release(c); spl.release(c); hits.release(c);
-  return rc;
-}
-
 static void pass_plan(uint32_t bits, uint32_t* passes, uint32_t* dbits) {
   bits = std::max(1u, bits);
   *passes = (bits + 7) / 8;
@@ -434,6 +369,71 @@ static int load_relation(wg_ctx* c, const uint32_t* d_src, const uint32_t* d_dst
   R->kb = 2 * R->w <= 32 ? 4 : 8;
   if (R->kb == 4) return build_edges<uint32_t>(c, R, d_src, d_dst, n);
   return build_edges<unsigned long long>(c, R, d_src, d_dst, n);
+}
+
+// ------------------------------------------------------------------ triangle counting
+// triangle(a,b,c) <- edge(a,b), edge(b,c), edge(c,a) (Sec. Generalization,
+// "Triangle Counting"): one pass of the sorted-array join with E as the
+// delta.  The join count gives each edge (a,b) its slab of deg(b) two-paths;
+// the emit kernel in probe mode tests each two-path (a,b,c) for E(c,a) by
+// binary search and counts the hits.
+template <typename K>
+static int tri_count(wg_ctx* c, Relation* R, unsigned long long* count) {
+  *count = 0;
+  const size_t ne = R->ne;
+  if (ne == 0) return WG_OK;
+  const uint32_t ntd = (uint32_t)((ne + kTileD - 1) / kTileD);
+  TRY(prim_scratch(c, 0, ntd));
+  DBuf inst, pos, spl, hits;
+  TRY(inst.get(c, sizeof(Inst)));
+  TRY(pos.get(c, ne * 8));
+  TRY(hits.get(c, 8));
+  Inst I{};
+  I.off = (const uint32_t*)R->off.p; I.adj = (const uint32_t*)R->adj.p;
+  I.nv = R->nv; I.w = R->w; I.kind = KIND_TC; I.state = INST_ACTIVE; I.iter = 1; I.n_delta = ne;
+  CK(cudaMemcpyAsync(inst.p, &I, sizeof(Inst), cudaMemcpyHostToDevice, c->stream));
+  Seg sd{};
+  sd.n = ne; sd.ntiles = ntd;
+  TRY(prim_seg(c, sd));
+  Stage k = prim_stage(c, ntd);
+  k.in = R->keys.p; k.inst = (Inst*)inst.p; k.pos = (unsigned long long*)pos.p;
+  k.epoch = prim_epoch(c);
+  TRY(prim_put(c, S_COUNT, k));
+  launch_join_count<K>(c->s_stage + S_COUNT, grid_of(c, occupancy_join<K>(0)), c->stream, kTileD);
+  CK(cudaGetLastError());
+  Seg back{};
+  Ctl ctl{};
+  CK(cudaMemcpyAsync(&back, c->s_seg, sizeof(Seg), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  int rc = WG_OK;
+  const unsigned long long paths = back.res;  // two-paths (a,b,c)
+  if (!ctl.error && paths) {
+    const unsigned long long ntiles = (paths + kTileC - 1) / kTileC;
+    if (ntiles >= (1ull << 32)) return set_err(WG_E_CAPACITY, "too many two-paths");
+    TRY(spl.get(c, (size_t)(ntiles + 1) * 8));  // (the probe has no lookback: no status words)
+    Seg se{};
+    se.n = ne; se.aux_n = paths; se.ntiles = (uint32_t)ntiles;
+    TRY(prim_seg(c, se));
+    CK(cudaMemsetAsync(hits.p, 0, 8, c->stream));
+    Stage e = prim_stage(c, (uint32_t)ntiles);
+    e.in = R->keys.p; e.inst = (Inst*)inst.p; e.pos = (unsigned long long*)pos.p;
+    e.splits = (unsigned long long*)spl.p; e.probe = (unsigned long long*)hits.p;
+    TRY(prim_put(c, S_EMIT, e));
+    launch_partition<K>(c->s_stage + S_EMIT, 1, kTileC, c->num_sms * 4, c->stream);
+    launch_tri_probe<K>(c->s_stage + S_EMIT, grid_of(c, occupancy_join<K>(2)), c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(count, hits.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&ctl, c->s_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (ctl.error) {
+    cudaMemsetAsync(c->s_ctl, 0, sizeof(Ctl), c->stream);
+    *count = 0;
+    rc = set_err(WG_E_DEVICE_TIMEOUT, "a device lookback wait gave up");
+  }
+  inst.release(c); pos.release(c); spl.release(c); hits.release(c);
+  return rc;
 }
 
 // ------------------------------------------------------------------ engine
